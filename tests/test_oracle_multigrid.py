@@ -1,0 +1,226 @@
+"""Pins of the oracle's hierarchy, pieces, smoothers and cycle (Sec. 3-6)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import discretize, hierarchy, pieces, smoothers, mg
+from paper_1902_01818_gb300 import workloads as W
+from oracle_helpers import full_numbering
+
+
+def _nm(cidx, a):
+    return 4 if (cidx[0] + cidx[1]) % 2 == 0 else 8
+
+
+@pytest.mark.parametrize("coupling", ["conforming", "sipg"])
+def test_galerkin_equals_rediscretisation_affine(coupling):
+    # Eq. a:galerkin: with the penalty frozen at h_L the coarse form is the fine form
+    n = 8 if coupling == "conforming" else _nm
+    prob = W.grid_problem((2, 2), n, 2, coupling, box=(2.0, 1.0), flip_patches=(1,))
+    h = hierarchy.build(prob, levels=3)
+    for l in range(2):
+        Ar = hierarchy.rediscretize(prob, h, l)
+        d = (Ar - h["A"][l]).toarray()
+        assert np.max(np.abs(d)) <= 1e-12 * abs(Ar).max()
+
+
+def test_prolongation_preserves_mass():
+    prob = W.grid_problem((2, 1), 8, 3, "conforming", jitter=0.0)
+    h = hierarchy.build(prob, levels=2)
+    kn = h["knots"]
+    Ms = []
+    for l in range(2):
+        num = h["num"][l]
+        rows, cols, vals = [], [], []
+        for k in range(2):
+            Mk = discretize.patch_mass(prob, k, kn[l][k]).tocoo()
+            g = num["loc2glob"][k]
+            keep = (g[Mk.row] >= 0) & (g[Mk.col] >= 0)
+            rows.append(g[Mk.row][keep]); cols.append(g[Mk.col][keep]); vals.append(Mk.data[keep])
+        Ms.append(sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                                shape=(num["ndof"], num["ndof"])))
+    P = h["P"][1]
+    assert np.max(np.abs((P.T @ Ms[1] @ P - Ms[0]).toarray())) <= 1e-15 * 10
+
+
+def test_auto_levels_of_the_workloads():
+    assert hierarchy.auto_levels(W.sipg_3x3(2)[0]) == 6
+    assert hierarchy.auto_levels(W.sipg_3x3(2, scale=3)[0]) == 6  # 288 -> 9 is odd
+    assert hierarchy.auto_levels(W.cube_2x2x2(3, "sipg")[0]) == 5
+
+
+@pytest.mark.parametrize("coupling", ["conforming", "sipg"])
+def test_pieces_partition_the_dofs_2d(coupling):
+    prob = W.grid_problem((2, 2), 4, 2, coupling, flip_patches=(3,))
+    num = discretize.numbering(prob, prob["knots"])
+    pcs = pieces.decompose(prob, num)
+    allx = np.concatenate([pc["dofs"] for pc in pcs])
+    assert np.array_equal(np.sort(allx), np.arange(num["ndof"]))
+    kinds = [pc["kind"] for pc in pcs]
+    assert kinds.count("interior") == 4 and kinds.count("interface") == 5
+    sizes = sorted(len(pc["dofs"]) for pc in pcs if pc["kind"] == "interface")
+    # conforming: 4 edges of N-2 = 4 DoFs, centre vertex 1; SIPG: edges 2(N-2), vertex 4
+    assert sizes == ([1, 4, 4, 4, 4] if coupling == "conforming" else [4, 8, 8, 8, 8])
+
+
+@pytest.mark.parametrize("coupling", ["conforming", "sipg"])
+def test_pieces_partition_the_dofs_3d(coupling):
+    prob = W.grid_problem((2, 2, 2), 3, 2, coupling, flip_patches=(5,), transpose_patches=(6,))
+    num = discretize.numbering(prob, prob["knots"])
+    pcs = pieces.decompose(prob, num)
+    allx = np.concatenate([pc["dofs"] for pc in pcs])
+    assert np.array_equal(np.sort(allx), np.arange(num["ndof"]))
+    kinds = [pc["kind"] for pc in pcs]
+    # 8 interiors, 12 interior faces, 6 interior edges, 1 centre vertex
+    assert kinds.count("interior") == 8 and kinds.count("interface") == 19
+    sizes = sorted(len(pc["dofs"]) for pc in pcs if pc["kind"] == "interface")
+    m = 3 + 2 - 2  # N - 2 tangential interior DoFs
+    if coupling == "conforming":
+        assert sizes == [1] + [m] * 6 + [m * m] * 12
+    else:
+        assert sizes == [8] + [4 * m] * 6 + [2 * m * m] * 12
+
+
+@pytest.mark.parametrize("coupling,d", [("conforming", 2), ("sipg", 2), ("conforming", 3), ("sipg", 3)])
+def test_colouring_is_valid(coupling, d):
+    cells = (3, 3) if d == 2 else (2, 2, 2)
+    n = (lambda c, a: 3 if sum(c) % 2 == 0 else 4) if coupling == "sipg" else 3
+    prob = W.grid_problem(cells, n, 2, coupling, jitter=0.05, seed=2)
+    num = discretize.numbering(prob, prob["knots"])
+    col = smoothers.colouring(prob, prob["knots"], num)
+    A = discretize.assemble_global(prob, prob["knots"], num).tocoo()
+    off = A.row != A.col
+    assert not np.any(col[A.row[off]] == col[A.col[off]])
+    S = smoothers.structural_pattern(prob, prob["knots"], num).tocoo()
+    off = S.row != S.col
+    assert not np.any(col[S.row[off]] == col[S.col[off]])
+    # the numeric pattern is contained in the structural one
+    Sd = set(zip(S.row.tolist(), S.col.tolist()))
+    assert all((r, c) in Sd for r, c in zip(A.row.tolist(), A.col.tolist()))
+
+
+def test_colouring_conflicts_get_extra_colours():
+    # a non-bipartite patch graph (3 patches around a vertex cannot be
+    # 2-coloured) is emulated by a 2x2 conforming grid: the shared centre
+    # vertex DoF couples DoFs of the diagonal patches, which share a parity
+    prob = W.grid_problem((2, 2), 2, 1, "conforming")
+    num = discretize.numbering(prob, prob["knots"])
+    col = smoothers.colouring(prob, prob["knots"], num)
+    S = smoothers.structural_pattern(prob, prob["knots"], num).tocoo()
+    off = S.row != S.col
+    assert not np.any(col[S.row[off]] == col[S.col[off]])
+
+
+def test_gauss_seidel_equals_pointwise_sweep():
+    prob = W.grid_problem((2, 2), _nm, 2, "sipg", jitter=0.1, seed=1)
+    num = discretize.numbering(prob, prob["knots"])
+    A = discretize.assemble_global(prob, prob["knots"], num)
+    col = smoothers.colouring(prob, prob["knots"], num)
+    order = smoothers.gs_order(col)
+    gs = smoothers.GaussSeidel(A, order)
+    rng = np.random.default_rng(0)
+    f, u = rng.standard_normal(num["ndof"]), rng.standard_normal(num["ndof"])
+    Ad = A.toarray()
+    ref = u.copy()
+    for i in order:  # textbook pointwise update, current values
+        ref[i] += (f[i] - Ad[i] @ ref) / Ad[i, i]
+    assert np.max(np.abs(gs.forward(f, u) - ref)) <= 1e-12 * np.max(np.abs(ref))
+    ref = u.copy()
+    for i in order[::-1]:
+        ref[i] += (f[i] - Ad[i] @ ref) / Ad[i, i]
+    assert np.max(np.abs(gs.backward(f, u) - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_interior_operator_brute_force():
+    # L_T entries from the definition: sum over directions of products of 1D
+    # stiffness/mass entries plus sigma times the mass product
+    p, n, delta = 2, 4, 0.3
+    kn = [W.uniform_knots(n, p), W.uniform_knots(2 * n, p)]
+    L, sigma = smoothers.interior_operator(kn, p, delta)
+    assert abs(sigma - 1.0 / (delta * (1.0 / n) ** 2)) <= 1e-12
+    (K0, M0), (K1, M1) = [discretize.param_matrices_1d(t, p) for t in kn]
+    n0, n1 = K0.shape[0] - 2, K1.shape[0] - 2
+    Ld = L.toarray()
+    for r in range(n0 * n1):
+        i0, i1 = r % n0 + 1, r // n0 + 1
+        for c in range(n0 * n1):
+            j0, j1 = c % n0 + 1, c // n0 + 1
+            ref = K0[i0, j0] * M1[i1, j1] + M0[i0, j0] * K1[i1, j1] + sigma * M0[i0, j0] * M1[i1, j1]
+            assert abs(Ld[r, c] - ref) <= 1e-12 * abs(Ld).max()
+
+
+def test_scms_is_damped_block_jacobi_over_pieces():
+    prob = W.grid_problem((2, 2), 4, 2, "sipg", jitter=0.1, seed=3)
+    M = mg.Multigrid(prob, levels=2, smoother="scms", tau=0.7, delta=0.2)
+    sm = M.scms[1]
+    n = M.ndof
+    A = M.A.toarray()
+    Z = np.zeros((n, n))
+    for pc in M.pieces[1]:
+        dofs = pc["dofs"]
+        if pc["kind"] == "interface":
+            Z[np.ix_(dofs, dofs)] = np.linalg.inv(A[np.ix_(dofs, dofs)])
+        else:
+            k = pc["patch"]
+            L, _ = smoothers.interior_operator(M.h["knots"][1][k], 2, 0.2)
+            shape = M.h["num"][1]["shapes"][k]
+            multi = discretize.unflatten(np.arange(int(np.prod(shape))), shape)
+            inner = (multi[0] >= 1) & (multi[0] <= shape[0] - 2) & (multi[1] >= 1) & (multi[1] <= shape[1] - 2)
+            order = M.h["num"][1]["loc2glob"][k][inner]
+            Z[np.ix_(order, order)] = np.linalg.inv(L.toarray())
+    r = np.random.default_rng(1).standard_normal(n)
+    assert np.max(np.abs(sm.apply(r) - 0.7 * Z @ r)) <= 1e-12 * np.max(np.abs(Z @ r))
+
+
+@pytest.mark.parametrize("smoother", ["scms", "hybrid", "gs"])
+@pytest.mark.parametrize("coupling", ["conforming", "sipg"])
+def test_cycle_converges_and_preconditioner_is_symmetric(smoother, coupling):
+    n = 4 if coupling == "conforming" else _nm
+    prob = W.grid_problem((2, 2), n, 2, coupling, jitter=0.1, seed=8)
+    tau = 1.0 if coupling == "conforming" else 0.5
+    M = mg.Multigrid(prob, levels=3, smoother=smoother, tau=tau, delta=0.2)
+    E = M.error_propagation()
+    rho = max(abs(np.linalg.eigvals(E)))
+    assert rho < 1.0, rho
+    rng = np.random.default_rng(2)
+    x, y = rng.standard_normal(M.ndof), rng.standard_normal(M.ndof)
+    bx, by = M.precondition(x), M.precondition(y)
+    assert abs(y @ bx - x @ by) <= 1e-12 * np.linalg.norm(bx) * np.linalg.norm(y)
+
+
+def _energy_norm(E, A):
+    w, V = np.linalg.eigh(A)
+    Ah = V @ np.diag(np.sqrt(w)) @ V.T
+    Aih = V @ np.diag(1 / np.sqrt(w)) @ V.T
+    return np.linalg.norm(Ah @ E @ Aih, 2)
+
+
+def test_hybrid_no_worse_than_scms_in_energy_norm():
+    # Sec. 6: ||W~||_A <= ||W||_A (Gauss-Seidel is an A-contraction)
+    prob = W.grid_problem((2, 2), _nm, 2, "sipg", jitter=0.1, seed=8)
+    Ms = mg.Multigrid(prob, levels=3, smoother="scms", tau=0.5, delta=0.2)
+    Mh = mg.Multigrid(prob, levels=3, smoother="hybrid", tau=0.5, delta=0.2)
+    A = Ms.A.toarray()
+    assert _energy_norm(Mh.error_propagation(), A) <= _energy_norm(Ms.error_propagation(), A) + 1e-12
+
+
+def test_pcg_reaches_the_stopping_rule_and_the_discrete_solution():
+    prob = W.grid_problem((2, 2), _nm, 3, "sipg", jitter=0.1, seed=8)
+    M = mg.Multigrid(prob, smoother="scms", tau=0.5, delta=0.2)
+    num = M.h["num"][-1]
+    f = discretize.assemble_load(prob, prob["knots"], num, W.source_sinprod)
+    u, it, hist = M.solve_pcg(f)
+    assert np.linalg.norm(f - M.A @ u) / np.linalg.norm(f) <= 1e-8
+    ex = spla.spsolve(M.A.tocsc(), f)
+    assert np.linalg.norm(u - ex) <= 1e-6 * np.linalg.norm(ex)
+    u2, it2, _ = M.solve_pcg(f, max_iter=3)
+    assert it2 == 3
+
+
+def test_coarse_solve_inverts_a0():
+    prob = W.grid_problem((2, 2), 4, 2, "conforming", jitter=0.1, seed=1)
+    M = mg.Multigrid(prob, levels=2)
+    A0 = M.h["A"][0].toarray()
+    f = np.random.default_rng(0).standard_normal(A0.shape[0])
+    assert np.max(np.abs(A0 @ M.coarse_solve(f) - f)) <= 1e-12 * np.max(np.abs(f))

@@ -1,0 +1,324 @@
+"""Benchmark: DoF/s of V-cycle-preconditioned CG solves to 1e-8 relative residual.
+
+Workload (default): [0,3]^2 as 3x3 SIPG-coupled bilinear patches with jittered
+interior vertices, 192 / 288 intervals per direction (alternating, so the
+interface knots do not match), degrees p = 2..6, penalty 5 (p+1)^2 / h, hybrid
+smoother (forward Gauss-Seidel + subspace-corrected mass smoother, tau .25,
+delta .1), PCG to ||f - A u|| / ||f|| <= 1e-8.  One step solves all five
+degrees once (0.52-0.54M unknowns each); value = unknowns solved / second over
+the whole job.  Inputs are resident in HBM before the timed region; every
+solve starts from u = 0.  The working set (five band matrices, 106 MB-730 MB
+each) exceeds L2, so no explicit flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun) runs independent replicas of the workload on every rank
+(the solve has no data exchange across problems): weak scaling.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DoF/s to 1e-8 rel. residual (V-cycle-preconditioned CG, SIPG 3x3 patches, p=2..6)"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flop x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--degrees", default="2,3,4,5,6")
+    ap.add_argument("--scale", type=int, default=3, help="interval multiplier of 64/96 (3: 192/288)")
+    ap.add_argument("--smoother", default="hybrid", choices=["scms", "hybrid"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(p, scale, smoother):
+    from paper_1902_01818_gb300 import workloads as W
+    return W.sipg_3x3(p, scale=scale, smoother=smoother)
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) legs
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import discretize, mg
+from paper_1902_01818_gb300 import workloads as W
+prob, opts = W.sipg_3x3({p}, scale={scale}, smoother={smoother!r})
+M = mg.Multigrid(prob, smoother=opts["smoother"], tau=opts["tau"], delta=opts["delta"])
+f = discretize.assemble_load(prob, prob["knots"], M.h["num"][-1], W.source_sinprod)
+out = []
+for i in range({reps}):
+    t0 = time.perf_counter()
+    u, it, hist = M.solve_pcg(f, tol=1e-8)
+    out.append((time.perf_counter() - t0, it, hist[-1]))
+print(json.dumps(dict(ndof=M.ndof, runs=out)))
+"""
+
+
+def run_oracle(p, scale, smoother, reps):
+    """Time the oracle's PCG solve in a fresh single-threaded process."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, p=p, scale=scale, smoother=smoother, reps=reps)
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if res.returncode != 0:
+        raise RuntimeError("oracle run failed: " + res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(smoother):
+    """Bounded sample: the oracle on the 64/96-interval version (60k unknowns), p = 2."""
+    r = run_oracle(2, 1, smoother, 1)
+    t, it, rel = r["runs"][0]
+    return {"value": r["ndof"] / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"one PCG solve of the same layout at 64/96 intervals, p=2 ({r['ndof']} unknowns, "
+                      f"{it} iterations, {t:.1f} s, setup excluded; numpy/scipy, 1 thread)"}
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    # each step: one oracle PCG solve of the bounded sample (60k unknowns, p = 2)
+    r = run_oracle(2, 1, args.smoother, args.warmup + args.steps)
+    runs = r["runs"][args.warmup:]
+    times = [x[0] for x in runs]
+    total = sum(times)
+    value = r["ndof"] * len(runs) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(runs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"sipg-3x3-[0,3]^2-jitter0.1-64/96-intervals-p2 (bounded sample of the "
+                                   f"{192 if args.scale == 3 else 64 * args.scale}/{96 * args.scale} workload)",
+                       "smoother": args.smoother, "l2": "inputs larger than L2 n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(runs)} oracle PCG solves, {r['ndof']} unknowns, p=2, 1 thread"},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    world, rank, local = dist_env()
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # the CPU baseline runs first (spawned process, before this process uses the GPU)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.smoother)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1902_01818_gb300 import mgiga
+
+    degrees = [int(x) for x in args.degrees.split(",")]
+    stream = torch.cuda.Stream()  # all library work and the timing events live on this stream
+    torch.cuda.set_stream(stream)
+    solvers, rhs_d, u_d, rhs_h, u_h, ndofs = [], [], [], [], [], []
+    for p in degrees:
+        prob, opts = workload(p, args.scale, args.smoother)
+        s = mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"], tau=opts["tau"],
+                         delta=opts["delta"], stream=stream.cuda_stream)
+        f = s.load_sinprod()
+        solvers.append(s)
+        ndofs.append(len(f))
+        rhs_d.append(torch.from_numpy(f).cuda())
+        u_d.append(torch.zeros_like(rhs_d[-1]))
+        rhs_h.append(torch.from_numpy(f).pin_memory())
+        u_h.append(torch.zeros(len(f), dtype=torch.float64).pin_memory())
+    total_dof = sum(ndofs)
+
+    def step(host_path=False):
+        info = []
+        for i, s in enumerate(solvers):
+            if host_path:
+                u_h[i].zero_()
+                u, it, rel, st = s.solve(rhs_h[i].numpy(), u0=u_h[i].numpy(), tol=1e-8)
+                u_h[i].copy_(torch.from_numpy(u))
+            else:
+                u_d[i].zero_()
+                it, rel, st = s.solve_d(rhs_d[i], u_d[i], tol=1e-8)
+            info.append((it, rel))
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    launches0 = sum(s.kernel_launches() for s in solvers)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per_step = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record()
+        for _ in range(args.steps):
+            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_a.record()
+            info = step()
+            e_b.record()
+            per_step.append((e_a, e_b, info))
+        ev1.record()
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = sum(s.kernel_launches() for s in solvers) - launches0
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    step_ms = [a.elapsed_time(b) for a, b, _ in per_step]
+    iters = [x[0] for x in per_step[-1][2]]
+    rels = [x[1] for x in per_step[-1][2]]
+    value = world * total_dof * args.steps / (ms / 1e3)
+
+    # end to end: host buffers, H2D and D2H inside the timed region
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        step(host_path=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
+    e2e = {"value": world * total_dof / e2e_s, "unit": "DoF/s",
+           "h2d_bytes_per_step": int(2 * 8 * total_dof), "d2h_bytes_per_step": int(8 * total_dof)}
+
+    # roofline of the dominant stage on the finest level (largest time share)
+    shares = {}
+    for s, p in zip(solvers, degrees):
+        for stage, count in (("band", 4), ("fd", 2), ("gs", 2 if args.smoother == "hybrid" else 0)):
+            if count == 0:
+                continue
+            t_ms = s.time_stage(stage, -1, reps=10)
+            fl, by = s.stage_work(stage, -1)
+            shares.setdefault(stage, []).append((count * t_ms, t_ms, fl, by, p))
+    dom = max(shares, key=lambda k: sum(x[0] for x in shares[k]))
+    tot_ms = sum(x[1] for x in shares[dom])
+    tot_fl = sum(x[2] for x in shares[dom])
+    achieved = tot_fl / (tot_ms / 1e3) / 1e12
+    roof = {"kernel": {"band": "band_apply (FP64 residual/product)", "fd": "gemm_f64 (fast diagonalisation)",
+                       "gs": "gs_colour (FP64 Gauss-Seidel)"}[dom],
+            "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "note": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived; HBM would allow more)",
+            "per_degree_ms": {str(x[4]): round(x[1], 4) for x in shares[dom]}}
+
+    line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sipg-3x3-[0,3]^2-jitter0.1-{64 * args.scale}/{96 * args.scale}-intervals",
+                       "degrees": degrees, "unknowns": ndofs, "smoother": args.smoother, "outer": "pcg",
+                       "precision": "fp64", "tol": 1e-8, "iterations": iters, "final_relres": rels,
+                       "step_ms_p50": float(np.percentile(step_ms, 50)),
+                       "step_ms_p99": float(np.percentile(step_ms, 99)),
+                       "l2": "inputs larger than L2 (0.9-3.7 GB operators per step)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "clocks": clk.summary()}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for s in solvers:
+        s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -65,7 +65,9 @@ class Multigrid:
     def _pre(self, l, f, u):
         A = self.h["A"][l]
         if self.smoother == "gs":
-            return self.gs[l].forward(f, u)
+            for _ in range(self.nu):
+                u = self.gs[l].forward(f, u)
+            return u
         if self.smoother == "hybrid":
             u = self.gs[l].forward(f, u)
         for _ in range(self.nu):
@@ -75,7 +77,9 @@ class Multigrid:
     def _post(self, l, f, u):
         A = self.h["A"][l]
         if self.smoother == "gs":
-            return self.gs[l].backward(f, u)
+            for _ in range(self.nu):
+                u = self.gs[l].backward(f, u)
+            return u
         for _ in range(self.nu):
             u = u + self.scms[l].apply(f - A @ u)
         if self.smoother == "hybrid":

@@ -1,0 +1,82 @@
+// Device-side data of libmgiga and the kernel launchers.
+//
+// Layout in HBM (one grid level):
+//   * vectors: all patch blocks back to back (local layout), patch k holding
+//     prod_a N_a coefficients with xi_0 fastest; Dirichlet entries are 0.
+//     Each vector has a zero guard of `guard` doubles on both sides so that
+//     band neighbours of boundary rows stay inside the allocation.
+//   * operator: band[o * nloc + pos], o = sum_a (o_a + p)(2p+1)^a, the
+//     coefficient coupling row pos to column pos + sum_a o_a stride_a of the
+//     same patch (0 where that column leaves the patch or is Dirichlet);
+//     consecutive rows are consecutive in memory, so a warp over rows reads
+//     each offset's coefficients coalesced.
+//   * SIPG cross-patch couplings in CSR over the rows that have them.
+//   * conforming interfaces: DoFs shared by several patches are stored once
+//     per patch; classes list their copies (owner first).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mgiga {
+namespace dev {
+
+constexpr int kTile = 256;  // rows per tile of the position-parallel kernels
+
+struct PatchMeta {
+  int64_t off;
+  int N[3];
+};
+
+struct Tile {
+  int patch;
+  int count;
+  int64_t start;
+};
+
+// per patch and direction: prolongation table between two levels
+struct XferMeta {
+  int64_t par_off;  // into par_start / par_val (fine index based)
+  int64_t ch_off;   // into ch_start / ch_val (coarse index based)
+  int nf, nc;
+};
+
+// C(m, n) = alpha * sum_k A(m, k) B(k, n) (+ epilogue) for one batched task.
+// A is M x K: A[m * lda + k] (transA = 0) or A[k * lda + m] (transA = 1).
+// B is K x N: B[k * ldb + col(n)] (transB = 0) or B[n * ldb + k] (transB = 1).
+// C[m * ldc + col(n)], col(n) = (n / ndiv) * nhi + n % ndiv (ndiv = N: plain).
+// batch z adds z * sA, z * sB, z * sC.
+// epi 0: C = acc; 1: C = acc / (sigma + lamM[m] + lamN0[n % nl0] + lamN1[n / nl0]);
+//     2: C += alpha * acc.
+struct GemmTask {
+  int M, N, K, transA, transB, batch, ndiv, epi;
+  const double* A;
+  const double* B;
+  double* C;
+  int64_t lda, ldb, ldc, nhi, sA, sB, sC;
+  double alpha, sigma;
+  const double* lamM;
+  const double* lamN0;
+  const double* lamN1;
+  int nl0, pad;
+};
+
+struct GemmItem {
+  int task, z, tm, tn;
+};
+
+struct PieceMeta {
+  int64_t z_off;    // dense inverse n x n at zpool + z_off
+  int64_t dof_off;  // primary positions at piece_pos + dof_off
+  int n, pad;
+};
+
+struct PieceItem {
+  int piece, row0;
+};
+
+// scalar slots of the CG state in device memory
+enum { S_RZ = 0, S_PQ, S_ALPHA, S_RR, S_RZNEW, S_BETA, S_FF, S_TMP, S_COUNT };
+
+}  // namespace dev
+}  // namespace mgiga

@@ -1,0 +1,639 @@
+// DoF topology and assembly of the finest-level operator (Sec. 2 and 3).
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <unordered_map>
+
+#include "host.hpp"
+
+namespace mgiga {
+
+int64_t Level::band_offset(int k, int o) const {
+  int64_t off = 0;
+  const int w = 2 * p + 1;
+  for (int a = 0; a < d; ++a) {
+    const int oa = o % w - p;
+    o /= w;
+    off += oa * stride(k, a);
+  }
+  return off;
+}
+
+static std::vector<int> tangential(int d, int side) {
+  std::vector<int> t;
+  for (int a = 0; a < d; ++a)
+    if (a != side / 2) t.push_back(a);
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// numbering (Sec. 2, Eq. igaspace0: shared DoFs on matching interfaces;
+// Sec. 3, Eq. igaspace: independent patches); Dirichlet DoFs are the ones
+// with a nonzero trace on a side listed in no interface
+// ---------------------------------------------------------------------------
+namespace {
+struct DSU {
+  std::vector<int64_t> par;
+  explicit DSU(int64_t n) : par(n) { std::iota(par.begin(), par.end(), 0); }
+  int64_t find(int64_t x) {
+    while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; }
+    return x;
+  }
+  void unite(int64_t a, int64_t b) {
+    a = find(a); b = find(b);
+    if (a == b) return;
+    if (a < b) par[b] = a; else par[a] = b;
+  }
+};
+}  // namespace
+
+void build_topology(const Problem& pr, Level& L) {
+  const int d = pr.d, K = pr.K, p = pr.p;
+  L.d = d; L.p = p; L.K = K;
+  L.N.assign(K, {{1, 1, 1}});
+  L.off.assign(K + 1, 0);
+  for (int k = 0; k < K; ++k) {
+    int64_t sz = 1;
+    for (int a = 0; a < d; ++a) {
+      L.N[k][a] = num_basis(L.knots[k][a], p);
+      sz *= L.N[k][a];
+    }
+    L.off[k + 1] = L.off[k] + sz;
+  }
+  L.nloc = L.off[K];
+  L.patch_of.assign(L.nloc, 0);
+  for (int k = 0; k < K; ++k)
+    for (int64_t i = L.off[k]; i < L.off[k + 1]; ++i) L.patch_of[i] = k;
+
+  // sides listed in interfaces
+  std::vector<std::array<bool, 6>> iside(K);
+  for (auto& s : iside) s.fill(false);
+  for (const auto& f : pr.ifaces) { iside[f.pa][f.sa] = true; iside[f.pb][f.sb] = true; }
+  L.dirichlet.assign(L.nloc, 0);
+  for (int k = 0; k < K; ++k) {
+    const auto& N = L.N[k];
+    for (int i2 = 0; i2 < (d == 3 ? N[2] : 1); ++i2)
+      for (int i1 = 0; i1 < N[1]; ++i1)
+        for (int i0 = 0; i0 < N[0]; ++i0) {
+          const int idx[3] = {i0, i1, i2};
+          bool dir = false;
+          for (int a = 0; a < d; ++a) {
+            if (idx[a] == 0 && !iside[k][2 * a]) dir = true;
+            if (idx[a] == N[a] - 1 && !iside[k][2 * a + 1]) dir = true;
+          }
+          L.dirichlet[L.pos(k, i0, i1, i2)] = dir;
+        }
+  }
+
+  DSU dsu(L.nloc);
+  const bool conforming = pr.coupling == 0;
+  if (conforming) {
+    for (const auto& f : pr.ifaces) {
+      const auto ta = tangential(d, f.sa), tb = tangential(d, f.sb);
+      const auto& Na = L.N[f.pa];
+      const auto& Nb = L.N[f.pb];
+      const int m = d - 1;
+      const int n0 = Na[ta[0]], n1 = m == 2 ? Na[ta[1]] : 1;
+      for (int j1 = 0; j1 < n1; ++j1)
+        for (int j0 = 0; j0 < n0; ++j0) {
+          int ia[3], ib[3];
+          ia[f.sa / 2] = f.sa % 2 ? Na[f.sa / 2] - 1 : 0;
+          ia[ta[0]] = j0;
+          if (m == 2) ia[ta[1]] = j1;
+          int tbm[2] = {j0, j1};
+          if (m == 2 && (f.orient & 4u)) std::swap(tbm[0], tbm[1]);
+          for (int c = 0; c < m; ++c)
+            if (f.orient & (1u << c)) tbm[c] = Nb[tb[c]] - 1 - tbm[c];
+          ib[f.sb / 2] = f.sb % 2 ? Nb[f.sb / 2] - 1 : 0;
+          for (int c = 0; c < m; ++c) ib[tb[c]] = tbm[c];
+          if (d == 2) { ia[2] = 0; ib[2] = 0; }
+          for (int c = 0; c < m; ++c)
+            if (tbm[c] < 0 || tbm[c] >= Nb[tb[c]]) throw SetupError(1, "interface knots do not match");
+          if (Na[ta[0]] != Nb[tb[(m == 2 && (f.orient & 4u)) ? 1 : 0]])
+            throw SetupError(1, "conforming interface with different numbers of B-splines");
+          dsu.unite(L.pos(f.pa, ia[0], ia[1], ia[2]), L.pos(f.pb, ib[0], ib[1], ib[2]));
+        }
+    }
+  }
+  // a class is Dirichlet if any copy is
+  std::vector<uint8_t> root_dir(L.nloc, 0);
+  std::vector<int64_t> root(L.nloc);
+  for (int64_t i = 0; i < L.nloc; ++i) {
+    root[i] = conforming ? dsu.find(i) : i;
+    if (L.dirichlet[i]) root_dir[root[i]] = 1;
+  }
+  L.loc2glob.assign(L.nloc, -1);
+  L.owner.clear();
+  std::vector<int> glob_of_root(L.nloc, -1);
+  for (int64_t i = 0; i < L.nloc; ++i) {
+    const int64_t r = root[i];
+    if (root_dir[r]) { L.dirichlet[i] = 1; continue; }
+    if (glob_of_root[r] < 0) {
+      glob_of_root[r] = (int)L.owner.size();
+      L.owner.push_back(i);
+    }
+    L.loc2glob[i] = glob_of_root[r];
+  }
+  L.ndof = (int)L.owner.size();
+  // shared classes (conforming): owner first, then further copies ascending
+  L.sh_ptr.assign(1, 0);
+  L.sh_pos.clear();
+  L.weight.assign(L.nloc, 1.0);
+  if (conforming) {
+    std::vector<int> count(L.ndof, 0);
+    for (int64_t i = 0; i < L.nloc; ++i)
+      if (L.loc2glob[i] >= 0) count[L.loc2glob[i]]++;
+    std::vector<std::vector<int64_t>> copies;
+    std::vector<int> cls(L.ndof, -1);
+    for (int64_t i = 0; i < L.nloc; ++i) {
+      const int g = L.loc2glob[i];
+      if (g < 0) continue;
+      L.weight[i] = 1.0 / count[g];
+      if (count[g] < 2) continue;
+      if (cls[g] < 0) { cls[g] = (int)copies.size(); copies.emplace_back(); }
+      copies[cls[g]].push_back(i);
+    }
+    for (auto& c : copies) {
+      for (int64_t x : c) L.sh_pos.push_back(x);
+      L.sh_ptr.push_back((int)L.sh_pos.size());
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// patch stiffness (Sec. 2): K_ij = sum_q w_q |det J| (J^{-T} grad^ B_i).(J^{-T} grad^ B_j),
+// p+1 Gauss points per element and direction, sum-factorised over directions
+// ---------------------------------------------------------------------------
+namespace {
+struct DirQuad {
+  std::vector<int> span;        // per element
+  std::vector<double> x, w;     // per element * nq
+  std::vector<double> B, D;     // per element * nq * (p+1)
+};
+
+DirQuad dir_quad(const Vec& t, int p) {
+  DirQuad q;
+  const int nq = p + 1;
+  const Vec z = breakpoints(t);
+  double xg[16], wg[16];
+  gauss_legendre(nq, xg, wg);
+  const int ne = (int)z.size() - 1;
+  q.span.resize(ne);
+  q.x.resize((size_t)ne * nq);
+  q.w.resize((size_t)ne * nq);
+  q.B.resize((size_t)ne * nq * (p + 1));
+  q.D.resize((size_t)ne * nq * (p + 1));
+  for (int e = 0; e < ne; ++e) {
+    const double a = z[e], h = z[e + 1] - z[e];
+    q.span[e] = find_span(t, p, a + 0.5 * h);
+    for (int k = 0; k < nq; ++k) {
+      const double x = a + h * xg[k];
+      q.x[(size_t)e * nq + k] = x;
+      q.w[(size_t)e * nq + k] = h * wg[k];
+      basis_on_span(t, p, q.span[e], x, &q.B[((size_t)e * nq + k) * (p + 1)],
+                    &q.D[((size_t)e * nq + k) * (p + 1)]);
+    }
+  }
+  return q;
+}
+
+// invert a d x d matrix (d = 2, 3); returns det
+double inv_small(const double* J, int d, double* Ji) {
+  if (d == 2) {
+    const double det = J[0] * J[3] - J[1] * J[2];
+    Ji[0] = J[3] / det; Ji[1] = -J[1] / det; Ji[2] = -J[2] / det; Ji[3] = J[0] / det;
+    return det;
+  }
+  const double c00 = J[4] * J[8] - J[5] * J[7];
+  const double c01 = J[5] * J[6] - J[3] * J[8];
+  const double c02 = J[3] * J[7] - J[4] * J[6];
+  const double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+  Ji[0] = c00 / det; Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det; Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+  Ji[3] = c01 / det; Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det; Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+  Ji[6] = c02 / det; Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det; Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+  return det;
+}
+}  // namespace
+
+static void patch_stiffness(const Problem& pr, Level& L, int k) {
+  const int d = pr.d, p = pr.p, P1 = p + 1, nq = p + 1, W = 2 * p + 1;
+  DirQuad dq[3];
+  int ne[3] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) { dq[a] = dir_quad(L.knots[k][a], p); ne[a] = (int)dq[a].span.size(); }
+  const int slow = d - 1;
+  const int Q = d == 2 ? nq * nq : nq * nq * nq;
+  // element slabs along the slowest direction touch disjoint band rows when
+  // they are p+1 apart: p+1 parallel phases
+  for (int phase = 0; phase < P1; ++phase) {
+#pragma omp parallel
+    {
+      std::vector<double> C((size_t)Q * 9), T1, T2, Ke;
+      const int L2 = P1 * P1;
+      T1.resize((size_t)nq * nq * L2 * 9);
+      T2.resize((size_t)nq * L2 * L2 * 9);
+      Ke.resize((size_t)(d == 2 ? L2 * L2 : L2 * L2 * L2));
+#pragma omp for schedule(dynamic)
+      for (int es = phase; es < ne[slow]; es += P1) {
+        const int n_mid = d == 3 ? ne[1] : 1;
+        for (int e1m = 0; e1m < n_mid; ++e1m)
+          for (int e0 = 0; e0 < ne[0]; ++e0) {
+            int e[3];
+            e[0] = e0;
+            if (d == 2) { e[1] = es; e[2] = 0; } else { e[1] = e1m; e[2] = es; }
+            // geometric factors C_ab(q) = w |det J| (J^{-1} J^{-T})_ab
+            for (int q2 = 0; q2 < (d == 3 ? nq : 1); ++q2)
+              for (int q1 = 0; q1 < nq; ++q1)
+                for (int q0 = 0; q0 < nq; ++q0) {
+                  const int qi[3] = {q0, q1, q2};
+                  double xi[3], w = 1.0;
+                  for (int a = 0; a < d; ++a) {
+                    xi[a] = dq[a].x[(size_t)e[a] * nq + qi[a]];
+                    w *= dq[a].w[(size_t)e[a] * nq + qi[a]];
+                  }
+                  double X[3], J[9], Ji[9];
+                  geo_eval(pr, k, xi, X, J);
+                  const double det = inv_small(J, d, Ji);
+                  const double s = w * std::fabs(det);
+                  const int qq = q0 + nq * (q1 + nq * q2);
+                  for (int a = 0; a < d; ++a)
+                    for (int b = 0; b < d; ++b) {
+                      double v = 0.0;
+                      for (int c = 0; c < d; ++c) v += Ji[a * d + c] * Ji[b * d + c];
+                      C[(size_t)qq * 9 + a * 3 + b] = s * v;
+                    }
+                }
+            // per-direction factors F_a(l, m, q) = X_a(l, q) X_b(m, q)
+            auto X = [&](int dir, int deriv, int l, int q) {
+              const size_t idx = ((size_t)e[dir] * nq + q) * P1 + l;
+              return deriv ? dq[dir].D[idx] : dq[dir].B[idx];
+            };
+            std::fill(Ke.begin(), Ke.end(), 0.0);
+            for (int a = 0; a < d; ++a)
+              for (int b = 0; b < d; ++b) {
+                // contract q0
+                for (int q2 = 0; q2 < (d == 3 ? nq : 1); ++q2)
+                  for (int q1 = 0; q1 < nq; ++q1)
+                    for (int l0 = 0; l0 < P1; ++l0)
+                      for (int m0 = 0; m0 < P1; ++m0) {
+                        double s = 0.0;
+                        for (int q0 = 0; q0 < nq; ++q0)
+                          s += C[(size_t)(q0 + nq * (q1 + nq * q2)) * 9 + a * 3 + b] *
+                               X(0, a == 0, l0, q0) * X(0, b == 0, m0, q0);
+                        T1[((size_t)(q2 * nq + q1) * P1 + l0) * P1 + m0] = s;
+                      }
+                if (d == 2) {
+                  for (int l1 = 0; l1 < P1; ++l1)
+                    for (int m1 = 0; m1 < P1; ++m1)
+                      for (int q1 = 0; q1 < nq; ++q1) {
+                        const double f = X(1, a == 1, l1, q1) * X(1, b == 1, m1, q1);
+                        for (int l0 = 0; l0 < P1; ++l0)
+                          for (int m0 = 0; m0 < P1; ++m0)
+                            Ke[(size_t)(l0 + P1 * l1) * L2 + (m0 + P1 * m1)] +=
+                                f * T1[((size_t)q1 * P1 + l0) * P1 + m0];
+                      }
+                } else {
+                  // contract q1
+                  for (int q2 = 0; q2 < nq; ++q2)
+                    for (int l1 = 0; l1 < P1; ++l1)
+                      for (int m1 = 0; m1 < P1; ++m1) {
+                        double* dst = &T2[(((size_t)q2 * P1 + l1) * P1 + m1) * L2];
+                        for (int x = 0; x < L2; ++x) dst[x] = 0.0;
+                        for (int q1 = 0; q1 < nq; ++q1) {
+                          const double f = X(1, a == 1, l1, q1) * X(1, b == 1, m1, q1);
+                          const double* src = &T1[((size_t)(q2 * nq + q1) * P1) * P1];
+                          for (int x = 0; x < L2; ++x) dst[x] += f * src[x];
+                        }
+                      }
+                  // contract q2
+                  const int L3 = L2 * P1;
+                  for (int l2 = 0; l2 < P1; ++l2)
+                    for (int m2 = 0; m2 < P1; ++m2)
+                      for (int q2 = 0; q2 < nq; ++q2) {
+                        const double f = X(2, a == 2, l2, q2) * X(2, b == 2, m2, q2);
+                        for (int l1 = 0; l1 < P1; ++l1)
+                          for (int m1 = 0; m1 < P1; ++m1) {
+                            const double* src = &T2[(((size_t)q2 * P1 + l1) * P1 + m1) * L2];
+                            for (int l0 = 0; l0 < P1; ++l0)
+                              for (int m0 = 0; m0 < P1; ++m0)
+                                Ke[(size_t)(l0 + P1 * (l1 + P1 * l2)) * L3 + (m0 + P1 * (m1 + P1 * m2))] +=
+                                    f * src[l0 * P1 + m0];
+                          }
+                      }
+                }
+              }
+            // scatter into the band: row of l, offset m - l
+            const int LL = d == 2 ? L2 : L2 * P1;
+            for (int l = 0; l < LL; ++l) {
+              const int l0 = l % P1, l1 = (l / P1) % P1, l2 = l / (P1 * P1);
+              const int r0 = dq[0].span[e[0]] - p + l0;
+              const int r1 = dq[1].span[e[1]] - p + l1;
+              const int r2 = d == 3 ? dq[2].span[e[2]] - p + l2 : 0;
+              const int64_t row = L.pos(k, r0, r1, r2);
+              for (int m = 0; m < LL; ++m) {
+                const int m0 = m % P1, m1 = (m / P1) % P1, m2 = m / (P1 * P1);
+                int o = (m0 - l0 + p) + W * (m1 - l1 + p);
+                if (d == 3) o += W * W * (m2 - l2 + p);
+                L.band[(size_t)o * L.nloc + row] += Ke[(size_t)l * LL + m];
+              }
+            }
+          }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SIPG interface terms (Sec. 3, Eq. model:discr2):
+//   -([[u]], {grad v}.n) - ([[v]], {grad u}.n) + eta ([[u]], [[v]])
+// [[u]] = u_a - u_b, {w} = (w_a + w_b)/2, n the outward normal of patch a;
+// quadrature on the union of both sides' breakpoints, p+1 Gauss points per
+// cell and tangential direction, in the parameter of side a
+// ---------------------------------------------------------------------------
+namespace {
+struct SideFun {
+  int64_t pos;
+  double val, grad[3];
+};
+
+// nonzero functions (two layers next to the side) of patch k at side point xi
+void side_functions(const Problem& pr, const Level& L, int k, int side, const double* xi,
+                    std::vector<SideFun>& out, double* normal, double* dS) {
+  const int d = pr.d, p = pr.p, P1 = p + 1;
+  double X[3], J[9], Ji[9];
+  geo_eval(pr, k, xi, X, J);
+  const double det = inv_small(J, d, Ji);
+  const int a = side / 2;
+  double nrm = 0.0;
+  for (int c = 0; c < d; ++c) nrm += Ji[a * d + c] * Ji[a * d + c];
+  nrm = std::sqrt(nrm);
+  const double sgn = side % 2 ? 1.0 : -1.0;
+  for (int c = 0; c < d; ++c) normal[c] = sgn * Ji[a * d + c] / nrm;
+  *dS = std::fabs(det) * nrm;
+  double B[3][16], D[3][16];
+  int s[3];
+  for (int b = 0; b < d; ++b) {
+    s[b] = find_span(L.knots[k][b], p, xi[b]);
+    basis_on_span(L.knots[k][b], p, s[b], xi[b], B[b], D[b]);
+  }
+  out.clear();
+  const int Na = L.N[k][a];
+  for (int l2 = 0; l2 < (d == 3 ? P1 : 1); ++l2)
+    for (int l1 = 0; l1 < P1; ++l1)
+      for (int l0 = 0; l0 < P1; ++l0) {
+        const int l[3] = {l0, l1, l2};
+        int idx[3] = {0, 0, 0};
+        for (int b = 0; b < d; ++b) idx[b] = s[b] - p + l[b];
+        const int layer = side % 2 ? Na - 1 - idx[a] : idx[a];
+        if (layer > 1) continue;
+        SideFun f;
+        f.pos = L.pos(k, idx[0], idx[1], idx[2]);
+        double gh[3];
+        f.val = 1.0;
+        for (int b = 0; b < d; ++b) f.val *= B[b][l[b]];
+        for (int c = 0; c < d; ++c) {
+          gh[c] = 1.0;
+          for (int b = 0; b < d; ++b) gh[c] *= (b == c) ? D[b][l[b]] : B[b][l[b]];
+        }
+        for (int c = 0; c < d; ++c) {
+          f.grad[c] = 0.0;
+          for (int b = 0; b < d; ++b) f.grad[c] += Ji[b * d + c] * gh[b];
+        }
+        out.push_back(f);
+      }
+}
+
+Vec merged(const Vec& a, const Vec& b) {
+  Vec z(a);
+  z.insert(z.end(), b.begin(), b.end());
+  std::sort(z.begin(), z.end());
+  Vec out;
+  for (double v : z)
+    if (out.empty() || v - out.back() > 1e-12) out.push_back(v);
+  return out;
+}
+
+double grid_size(const std::array<Vec, 3>& kn, int d) {
+  double h = 0.0;
+  for (int a = 0; a < d; ++a) {
+    const Vec z = breakpoints(kn[a]);
+    for (size_t i = 0; i + 1 < z.size(); ++i) h = std::max(h, z[i + 1] - z[i]);
+  }
+  return h;
+}
+}  // namespace
+
+static void interface_terms(const Problem& pr, Level& L, const Interface& f,
+                            const std::vector<std::array<Vec, 3>>& fine_knots,
+                            std::unordered_map<uint64_t, double>& cross) {
+  const int d = pr.d, p = pr.p;
+  const double eta = pr.penalty / std::min(grid_size(fine_knots[f.pa], d), grid_size(fine_knots[f.pb], d));
+  const auto ta = tangential(d, f.sa), tb = tangential(d, f.sb);
+  const int m = d - 1;
+  const bool swap = m == 2 && (f.orient & 4u);
+  // breakpoints per side-a tangential coordinate
+  std::vector<Vec> cuts(m);
+  for (int c = 0; c < m; ++c) {
+    const int cb = swap ? 1 - c : c;
+    Vec zb = breakpoints(L.knots[f.pb][tb[cb]]);
+    if (f.orient & (1u << cb)) {
+      Vec r(zb.size());
+      for (size_t i = 0; i < zb.size(); ++i) r[i] = 1.0 - zb[zb.size() - 1 - i];
+      zb = r;
+    }
+    cuts[c] = merged(breakpoints(L.knots[f.pa][ta[c]]), zb);
+  }
+  double xg[16], wg[16];
+  gauss_legendre(p + 1, xg, wg);
+  const int nc0 = (int)cuts[0].size() - 1, nc1 = m == 2 ? (int)cuts[1].size() - 1 : 1;
+  // functions active in a cell: two normal layers times (p+1)^m tangential, per side
+  int nmax = 4;
+  for (int c = 0; c < m; ++c) nmax *= p + 1;
+  const size_t ld = (size_t)nmax;
+  std::vector<SideFun> fa, fb;
+  std::vector<int64_t> dofs;
+  Vec blk(ld * ld);
+  std::unordered_map<int64_t, int> slot;
+  std::vector<int> ids;
+  Vec J, Dn;
+  for (int c1 = 0; c1 < nc1; ++c1)
+    for (int c0 = 0; c0 < nc0; ++c0) {
+      dofs.clear();
+      slot.clear();
+      std::fill(blk.begin(), blk.end(), 0.0);
+      for (int g1 = 0; g1 < (m == 2 ? p + 1 : 1); ++g1)
+        for (int g0 = 0; g0 < p + 1; ++g0) {
+          double s[2] = {0.0, 0.0}, w = 1.0;
+          s[0] = cuts[0][c0] + (cuts[0][c0 + 1] - cuts[0][c0]) * xg[g0];
+          w *= (cuts[0][c0 + 1] - cuts[0][c0]) * wg[g0];
+          if (m == 2) {
+            s[1] = cuts[1][c1] + (cuts[1][c1 + 1] - cuts[1][c1]) * xg[g1];
+            w *= (cuts[1][c1 + 1] - cuts[1][c1]) * wg[g1];
+          }
+          double sb[2] = {s[0], s[1]};
+          if (swap) std::swap(sb[0], sb[1]);
+          for (int c = 0; c < m; ++c)
+            if (f.orient & (1u << c)) sb[c] = 1.0 - sb[c];
+          double xa[3] = {0, 0, 0}, xb[3] = {0, 0, 0};
+          xa[f.sa / 2] = f.sa % 2 ? 1.0 : 0.0;
+          xb[f.sb / 2] = f.sb % 2 ? 1.0 : 0.0;
+          for (int c = 0; c < m; ++c) { xa[ta[c]] = s[c]; xb[tb[c]] = sb[c]; }
+          double na[3], nb[3], dSa, dSb;
+          side_functions(pr, L, f.pa, f.sa, xa, fa, na, &dSa);
+          side_functions(pr, L, f.pb, f.sb, xb, fb, nb, &dSb);
+          const double wq = w * dSa;
+          auto reg = [&](int64_t pos) {
+            auto it = slot.find(pos);
+            if (it != slot.end()) return it->second;
+            const int id = (int)dofs.size();
+            if (id >= nmax) throw SetupError(1, "interface cell has too many active functions");
+            slot.emplace(pos, id);
+            dofs.push_back(pos);
+            return id;
+          };
+          ids.clear(); J.clear(); Dn.clear();
+          for (const auto& x : fa) {
+            ids.push_back(reg(x.pos));
+            J.push_back(x.val);
+            double g = 0.0;
+            for (int c = 0; c < d; ++c) g += x.grad[c] * na[c];
+            Dn.push_back(0.5 * g);
+          }
+          for (const auto& x : fb) {
+            ids.push_back(reg(x.pos));
+            J.push_back(-x.val);
+            double g = 0.0;
+            for (int c = 0; c < d; ++c) g += x.grad[c] * na[c];
+            Dn.push_back(0.5 * g);
+          }
+          for (size_t i = 0; i < ids.size(); ++i)
+            for (size_t j = 0; j < ids.size(); ++j)
+              blk[(size_t)ids[i] * ld + ids[j]] += wq * (-Dn[i] * J[j] - J[i] * Dn[j] + eta * J[i] * J[j]);
+        }
+      for (size_t i = 0; i < dofs.size(); ++i)
+        for (size_t j = 0; j < dofs.size(); ++j) {
+          const double v = blk[i * ld + j];
+          if (v == 0.0) continue;
+          const int64_t r = dofs[i], c = dofs[j];
+          const int kr = L.patch_of[r], kc = L.patch_of[c];
+          if (kr == kc) {
+            // same patch: inside the band (|offset| <= 1 normal, <= p tangential)
+            int64_t rem_r = r - L.off[kr], rem_c = c - L.off[kc];
+            int o = 0, mul = 1;
+            for (int a = 0; a < d; ++a) {
+              const int ir = (int)(rem_r % L.N[kr][a]), ic = (int)(rem_c % L.N[kr][a]);
+              rem_r /= L.N[kr][a]; rem_c /= L.N[kr][a];
+              o += (ic - ir + p) * mul;
+              mul *= 2 * p + 1;
+            }
+            L.band[(size_t)o * L.nloc + r] += v;
+          } else {
+            cross[((uint64_t)r << 32) | (uint64_t)c] += v;
+          }
+        }
+    }
+}
+
+void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec, 3>>& fine_knots) {
+  const int W = 2 * pr.p + 1;
+  L.nb = pr.d == 2 ? W * W : W * W * W;
+  L.band.assign((size_t)L.nb * L.nloc, 0.0);
+  for (int k = 0; k < pr.K; ++k) patch_stiffness(pr, L, k);
+  std::unordered_map<uint64_t, double> cross;
+  if (pr.coupling == 1)
+    for (const auto& f : pr.ifaces) interface_terms(pr, L, f, fine_knots, cross);
+  // cross-patch entries to CSR by row position
+  std::vector<std::pair<uint64_t, double>> ent(cross.begin(), cross.end());
+  std::sort(ent.begin(), ent.end());
+  L.x_row.clear(); L.x_ptr.assign(1, 0); L.x_col.clear(); L.x_val.clear();
+  for (const auto& e : ent) {
+    const int64_t r = (int64_t)(e.first >> 32), c = (int64_t)(e.first & 0xffffffffu);
+    if (L.x_row.empty() || L.x_row.back() != r) {
+      if (!L.x_row.empty()) L.x_ptr.push_back((int)L.x_col.size());
+      L.x_row.push_back(r);
+    }
+    L.x_col.push_back(c);
+    L.x_val.push_back(e.second);
+  }
+  if (!L.x_row.empty()) L.x_ptr.push_back((int)L.x_col.size());
+}
+
+void apply_dirichlet(Level& L) {
+  for (int k = 0; k < L.K; ++k)
+    for (int64_t r = L.off[k]; r < L.off[k + 1]; ++r)
+      for (int o = 0; o < L.nb; ++o) {
+        double& v = L.band[(size_t)o * L.nloc + r];
+        if (v == 0.0) continue;
+        const int64_t c = r + L.band_offset(k, o);
+        if (L.dirichlet[r] || c < L.off[k] || c >= L.off[k + 1] || L.dirichlet[c]) v = 0.0;
+      }
+  // cross blocks: drop Dirichlet rows / columns
+  std::vector<int64_t> rows, cols;
+  std::vector<int> ptr(1, 0);
+  Vec vals;
+  for (size_t i = 0; i < L.x_row.size(); ++i) {
+    if (L.dirichlet[L.x_row[i]]) continue;
+    const size_t before = cols.size();
+    for (int j = L.x_ptr[i]; j < L.x_ptr[i + 1]; ++j)
+      if (!L.dirichlet[L.x_col[j]] && L.x_val[j] != 0.0) { cols.push_back(L.x_col[j]); vals.push_back(L.x_val[j]); }
+    if (cols.size() > before) { rows.push_back(L.x_row[i]); ptr.push_back((int)cols.size()); }
+  }
+  L.x_row.swap(rows); L.x_ptr.swap(ptr); L.x_col.swap(cols); L.x_val.swap(vals);
+}
+
+void assemble_load(const Problem& pr, const Level& L, double (*fn)(const double*, void*), void* ctx,
+                   double* out) {
+  const int d = pr.d, p = pr.p, P1 = p + 1, nq = p + 1;
+  Vec loc(L.nloc, 0.0);
+  for (int k = 0; k < pr.K; ++k) {
+    DirQuad dq[3];
+    int ne[3] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) { dq[a] = dir_quad(L.knots[k][a], p); ne[a] = (int)dq[a].span.size(); }
+    const int slow = d - 1;
+    for (int phase = 0; phase < P1; ++phase) {
+#pragma omp parallel for schedule(dynamic)
+      for (int es = phase; es < ne[slow]; es += P1) {
+        std::vector<double> g((size_t)nq * nq * nq);
+        const int n_mid = d == 3 ? ne[1] : 1;
+        for (int e1m = 0; e1m < n_mid; ++e1m)
+          for (int e0 = 0; e0 < ne[0]; ++e0) {
+            int e[3] = {e0, d == 2 ? es : e1m, d == 3 ? es : 0};
+            for (int q2 = 0; q2 < (d == 3 ? nq : 1); ++q2)
+              for (int q1 = 0; q1 < nq; ++q1)
+                for (int q0 = 0; q0 < nq; ++q0) {
+                  const int qi[3] = {q0, q1, q2};
+                  double xi[3], w = 1.0;
+                  for (int a = 0; a < d; ++a) {
+                    xi[a] = dq[a].x[(size_t)e[a] * nq + qi[a]];
+                    w *= dq[a].w[(size_t)e[a] * nq + qi[a]];
+                  }
+                  double X[3], J[9], Ji[9];
+                  geo_eval(pr, k, xi, X, J);
+                  const double det = inv_small(J, d, Ji);
+                  g[q0 + nq * (q1 + nq * q2)] = w * std::fabs(det) * fn(X, ctx);
+                }
+            for (int l2 = 0; l2 < (d == 3 ? P1 : 1); ++l2)
+              for (int l1 = 0; l1 < P1; ++l1)
+                for (int l0 = 0; l0 < P1; ++l0) {
+                  double s = 0.0;
+                  for (int q2 = 0; q2 < (d == 3 ? nq : 1); ++q2)
+                    for (int q1 = 0; q1 < nq; ++q1)
+                      for (int q0 = 0; q0 < nq; ++q0) {
+                        double b = dq[0].B[((size_t)e[0] * nq + q0) * P1 + l0] *
+                                   dq[1].B[((size_t)e[1] * nq + q1) * P1 + l1];
+                        if (d == 3) b *= dq[2].B[((size_t)e[2] * nq + q2) * P1 + l2];
+                        s += g[q0 + nq * (q1 + nq * q2)] * b;
+                      }
+                  const int r0 = dq[0].span[e[0]] - p + l0, r1 = dq[1].span[e[1]] - p + l1;
+                  const int r2 = d == 3 ? dq[2].span[e[2]] - p + l2 : 0;
+                  loc[L.pos(k, r0, r1, r2)] += s;
+                }
+          }
+      }
+    }
+  }
+  for (int g = 0; g < L.ndof; ++g) out[g] = 0.0;
+  for (int64_t i = 0; i < L.nloc; ++i)
+    if (L.loc2glob[i] >= 0) out[L.loc2glob[i]] += loc[i];
+}
+
+}  // namespace mgiga

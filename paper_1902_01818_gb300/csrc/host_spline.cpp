@@ -1,0 +1,340 @@
+// B-spline evaluation, quadrature, knot insertion, geometry and dense linear
+// algebra for the set-up phase.
+#include <algorithm>
+#include <cmath>
+
+#include "host.hpp"
+
+namespace mgiga {
+
+int num_basis(const Vec& t, int p) { return (int)t.size() - p - 1; }
+
+int find_span(const Vec& t, int p, double x) {
+  const int n = num_basis(t, p);
+  if (x >= t[n]) {  // right end point: last span of positive length
+    int s = n - 1;
+    while (s > p && t[s] == t[s + 1]) --s;
+    return s;
+  }
+  if (x <= t[p]) {
+    int s = p;
+    while (s < n - 1 && t[s + 1] <= x) ++s;
+    return s;
+  }
+  int lo = p, hi = n;  // invariant t[lo] <= x < t[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (x < t[mid]) hi = mid; else lo = mid;
+  }
+  return lo;
+}
+
+// Triangular evaluation of the nonzero B-splines on span s (de Boor): the
+// degree-j values are built from the degree-(j-1) values with the left and
+// right distances x - t_{s+1-r} and t_{s+r} - x.
+static void values_on_span(const Vec& t, int p, int s, double x, double* N) {
+  double left[16], right[16];
+  N[0] = 1.0;
+  for (int j = 1; j <= p; ++j) {
+    left[j] = x - t[s + 1 - j];
+    right[j] = t[s + j] - x;
+    double carry = 0.0;
+    for (int r = 0; r < j; ++r) {
+      const double den = right[r + 1] + left[j - r];
+      const double q = den != 0.0 ? N[r] / den : 0.0;
+      N[r] = carry + right[r + 1] * q;
+      carry = left[j - r] * q;
+    }
+    N[j] = carry;
+  }
+}
+
+void basis_on_span(const Vec& t, int p, int s, double x, double* N, double* dN) {
+  values_on_span(t, p, s, x, N);
+  if (!dN) return;
+  if (p == 0) { dN[0] = 0.0; return; }
+  double low[16];
+  values_on_span(t, p - 1, s, x, low);  // functions s-p+1 .. s of degree p-1
+  for (int r = 0; r <= p; ++r) {
+    const int i = s - p + r;
+    double a = 0.0, b = 0.0;
+    if (r >= 1) {
+      const double den = t[i + p] - t[i];
+      if (den != 0.0) a = low[r - 1] / den;
+    }
+    if (r <= p - 1) {
+      const double den = t[i + p + 1] - t[i + 1];
+      if (den != 0.0) b = low[r] / den;
+    }
+    dN[r] = p * (a - b);
+  }
+}
+
+Vec breakpoints(const Vec& t) {
+  Vec z;
+  for (double v : t)
+    if (z.empty() || v > z.back()) z.push_back(v);
+  return z;
+}
+
+Vec coarsen_knots(const Vec& t, int p) {
+  const Vec z = breakpoints(t);
+  const int n = (int)z.size() - 1;
+  if (n % 2 != 0) throw SetupError(1, "cannot coarsen a knot vector with an odd number of intervals");
+  Vec out(p + 1, z.front());
+  for (int i = 2; i < n; i += 2) out.push_back(z[i]);
+  for (int i = 0; i <= p; ++i) out.push_back(z.back());
+  return out;
+}
+
+// Newton iteration on the Legendre polynomial P_m, evaluated by its
+// three-term recurrence, from the Chebyshev-like start cos(pi (i + 3/4) / (m + 1/2)).
+void gauss_legendre(int m, double* x, double* w) {
+  for (int i = 0; i < m; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (m + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = 0.0;
+      for (int j = 1; j <= m; ++j) {
+        const double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+      }
+      dp = m * (z * p0 - p1) / (z * z - 1.0);
+      const double dz = p0 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    // recompute the derivative at the converged node
+    {
+      double p0 = 1.0, p1 = 0.0;
+      for (int j = 1; j <= m; ++j) {
+        const double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+      }
+      dp = m * (z * p0 - p1) / (z * z - 1.0);
+    }
+    // node on [-1,1] -> [0,1]; weight 2/((1-z^2) P'(z)^2) halved
+    x[m - 1 - i] = 0.5 * (z + 1.0);
+    w[m - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Boehm's algorithm: inserting knot x in span s replaces the coefficients
+// c_{s-p+1..s} by convex combinations alpha c_i + (1 - alpha) c_{i-1},
+// alpha = (x - t_i) / (t_{i+p} - t_i); coefficients before stay, after shift.
+// Applied to all coarse basis functions at once (the columns of P).
+Vec prolongation_1d(const Vec& tc, const Vec& tf, int p) {
+  const int nc = num_basis(tc, p);
+  const int nf = num_basis(tf, p);
+  // knots of tf missing from tc (multiset difference)
+  Vec ins;
+  {
+    size_t i = 0, j = 0;
+    while (j < tf.size()) {
+      if (i < tc.size() && tc[i] == tf[j]) { ++i; ++j; }
+      else { ins.push_back(tf[j]); ++j; }
+    }
+    if (i != tc.size()) throw SetupError(1, "knot vectors are not nested");
+  }
+  Vec t = tc;
+  std::vector<Vec> C(nc, Vec(nc, 0.0));  // C[i][j]: coefficient i of coarse function j
+  for (int i = 0; i < nc; ++i) C[i][i] = 1.0;
+  for (double x : ins) {
+    const int n = (int)C.size();
+    const int s = find_span(t, p, x);
+    std::vector<Vec> D(n + 1, Vec(nc, 0.0));
+    for (int i = 0; i <= n; ++i) {
+      if (i <= s - p) D[i] = C[i];
+      else if (i >= s + 1) D[i] = C[i - 1];
+      else {
+        const double alpha = (x - t[i]) / (t[i + p] - t[i]);
+        for (int j = 0; j < nc; ++j) D[i][j] = alpha * C[i][j] + (1.0 - alpha) * C[i - 1][j];
+      }
+    }
+    C.swap(D);
+    t.insert(std::upper_bound(t.begin(), t.end(), x), x);
+  }
+  if ((int)C.size() != nf) throw SetupError(1, "knot insertion size mismatch");
+  Vec P((size_t)nf * nc);
+  for (int i = 0; i < nf; ++i)
+    for (int j = 0; j < nc; ++j) P[(size_t)i * nc + j] = C[i][j];
+  return P;
+}
+
+void param_matrices(const Vec& t, int p, Vec& K, Vec& M) {
+  const int n = num_basis(t, p);
+  K.assign((size_t)n * n, 0.0);
+  M.assign((size_t)n * n, 0.0);
+  const Vec z = breakpoints(t);
+  double xg[16], wg[16], B[16], D[16];
+  gauss_legendre(p + 1, xg, wg);
+  for (size_t e = 0; e + 1 < z.size(); ++e) {
+    const double a = z[e], h = z[e + 1] - z[e];
+    const int s = find_span(t, p, a + 0.5 * h);
+    for (int q = 0; q <= p; ++q) {
+      const double x = a + h * xg[q], w = h * wg[q];
+      basis_on_span(t, p, s, x, B, D);
+      for (int r = 0; r <= p; ++r)
+        for (int c = 0; c <= p; ++c) {
+          const size_t idx = (size_t)(s - p + r) * n + (s - p + c);
+          K[idx] += w * D[r] * D[c];
+          M[idx] += w * B[r] * B[c];
+        }
+    }
+  }
+}
+
+void geo_eval(const Problem& pr, int k, const double* xi, double* X, double* J) {
+  const int d = pr.d;
+  const Geometry& g = pr.geo[k];
+  double B[3][16], D[3][16];
+  int s[3];
+  for (int a = 0; a < d; ++a) {
+    s[a] = find_span(g.knots[a], g.q, xi[a]);
+    basis_on_span(g.knots[a], g.q, s[a], xi[a], B[a], D[a]);
+  }
+  for (int c = 0; c < d; ++c) {
+    X[c] = 0.0;
+    for (int b = 0; b < d; ++b) J[c * d + b] = 0.0;
+  }
+  const int q1 = g.q + 1;
+  const int n2 = d == 3 ? q1 : 1;
+  for (int i2 = 0; i2 < n2; ++i2)
+    for (int i1 = 0; i1 < q1; ++i1)
+      for (int i0 = 0; i0 < q1; ++i0) {
+        const int I0 = s[0] - g.q + i0, I1 = s[1] - g.q + i1;
+        const int I2 = d == 3 ? s[2] - g.q + i2 : 0;
+        const int64_t idx = I0 + (int64_t)g.ncp[0] * (I1 + (int64_t)g.ncp[1] * I2);
+        const double* c = &g.ctrl[idx * d];
+        double val = B[0][i0] * B[1][i1] * (d == 3 ? B[2][i2] : 1.0);
+        double der[3];
+        der[0] = D[0][i0] * B[1][i1] * (d == 3 ? B[2][i2] : 1.0);
+        der[1] = B[0][i0] * D[1][i1] * (d == 3 ? B[2][i2] : 1.0);
+        der[2] = d == 3 ? B[0][i0] * B[1][i1] * D[2][i2] : 0.0;
+        for (int a = 0; a < d; ++a) {
+          X[a] += val * c[a];
+          for (int b = 0; b < d; ++b) J[a * d + b] += der[b] * c[a];
+        }
+      }
+}
+
+// ---------------------------------------------------------------------------
+// dense linear algebra (row-major)
+// ---------------------------------------------------------------------------
+
+// Cholesky A = L L^T in place (lower triangle); false if a pivot is not positive
+static bool cholesky(Vec& A, int n) {
+  for (int j = 0; j < n; ++j) {
+    double s = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+    if (!(s > 0.0)) return false;
+    const double ljj = std::sqrt(s);
+    A[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double v = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) v -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+      A[(size_t)i * n + j] = v / ljj;
+    }
+  }
+  return true;
+}
+
+// W = L^{-1} for the lower-triangular L (row-major), by forward substitution
+static Vec lower_inverse(const Vec& L, int n) {
+  Vec W((size_t)n * n, 0.0);
+  for (int c = 0; c < n; ++c) {
+    for (int i = c; i < n; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) v -= L[(size_t)i * n + k] * W[(size_t)k * n + c];
+      W[(size_t)i * n + c] = v / L[(size_t)i * n + i];
+    }
+  }
+  return W;
+}
+
+Vec spd_inverse(const Vec& A, int n) {
+  Vec L = A;
+  if (!cholesky(L, n)) throw SetupError(4, "Cholesky factorisation broke down (matrix not SPD)");
+  const Vec W = lower_inverse(L, n);
+  // A^{-1} = W^T W
+  Vec Z((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = 0.0;
+      for (int k = i; k < n; ++k) s += W[(size_t)k * n + i] * W[(size_t)k * n + j];
+      Z[(size_t)i * n + j] = s;
+      Z[(size_t)j * n + i] = s;
+    }
+  return Z;
+}
+
+// Cyclic Jacobi rotations on the symmetric C = L^{-1} K L^{-T} (M = L L^T):
+// C = V diag(lam) V^T, then U = L^{-T} V.
+void gen_eig(const Vec& K, const Vec& M, int n, Vec& U, Vec& lam) {
+  Vec L = M;
+  if (!cholesky(L, n)) throw SetupError(4, "mass matrix not SPD");
+  const Vec W = lower_inverse(L, n);
+  // C = W K W^T
+  Vec T((size_t)n * n, 0.0), C((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k <= i; ++k) s += W[(size_t)i * n + k] * K[(size_t)k * n + j];
+      T[(size_t)i * n + j] = s;
+    }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = 0.0;
+      for (int k = 0; k <= j; ++k) s += T[(size_t)i * n + k] * W[(size_t)j * n + k];
+      C[(size_t)i * n + j] = s;
+      C[(size_t)j * n + i] = s;
+    }
+  Vec V((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      diag += C[(size_t)i * n + i] * C[(size_t)i * n + i];
+      for (int j = i + 1; j < n; ++j) off += C[(size_t)i * n + j] * C[(size_t)i * n + j];
+    }
+    if (off <= 1e-32 * diag) break;
+    for (int pp = 0; pp < n - 1; ++pp)
+      for (int qq = pp + 1; qq < n; ++qq) {
+        const double apq = C[(size_t)pp * n + qq];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double app = C[(size_t)pp * n + pp], aqq = C[(size_t)qq * n + qq];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double tt = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(tt * tt + 1.0), s = tt * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double ckp = C[(size_t)k * n + pp], ckq = C[(size_t)k * n + qq];
+          C[(size_t)k * n + pp] = c * ckp - s * ckq;
+          C[(size_t)k * n + qq] = s * ckp + c * ckq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double cpk = C[(size_t)pp * n + k], cqk = C[(size_t)qq * n + k];
+          C[(size_t)pp * n + k] = c * cpk - s * cqk;
+          C[(size_t)qq * n + k] = s * cpk + c * cqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[(size_t)k * n + pp], vkq = V[(size_t)k * n + qq];
+          V[(size_t)k * n + pp] = c * vkp - s * vkq;
+          V[(size_t)k * n + qq] = s * vkp + c * vkq;
+        }
+      }
+  }
+  lam.resize(n);
+  for (int i = 0; i < n; ++i) lam[i] = C[(size_t)i * n + i];
+  // U = W^T V
+  U.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = i; k < n; ++k) s += W[(size_t)k * n + i] * V[(size_t)k * n + j];
+      U[(size_t)i * n + j] = s;
+    }
+}
+
+}  // namespace mgiga

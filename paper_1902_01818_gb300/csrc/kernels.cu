@@ -1,0 +1,589 @@
+// CUDA kernels of the V-cycle and of PCG (FP64 path), for sm_103a.
+//
+//   band_apply      residual r = f - A u / product A u on the patch band (a1)
+//   cross_apply     SIPG cross-patch couplings (a1')
+//   shared_reduce   sums / copies of DoFs shared by conforming patches (a1')
+//   restrict_band   f_c = P^T (w r) per patch, tensor-product children (a5)
+//   prolong_band    u_f += P e_c per patch, tensor-product parents (a6)
+//   gemm_f64        batched strided GEMM of the fast-diagonalisation
+//                   contractions, with the eigenvalue-sum division and the
+//                   damped update fused into the epilogue (a2)
+//   piece_apply     interface-piece and coarse solves, z = Z r (a3, a7)
+//   gs_colour       one colour of the multicolour Gauss-Seidel sweep (a4)
+//   dot / cg_*      deterministic reductions and vector updates of PCG (a8)
+#include <cstdio>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace mgiga {
+namespace dev {
+
+// ---------------------------------------------------------------------------
+// a1: band residual / product
+// ---------------------------------------------------------------------------
+// One thread per row.  The band coefficients of offset o for consecutive rows
+// are consecutive (coalesced); the u neighbours are read through L1/L2.
+// MODE 0: out = f - A u;  MODE 1: out = A u.
+template <int D, int P, int MODE>
+__global__ void __launch_bounds__(kTile) band_apply(const Tile* __restrict__ tiles,
+                                                    const PatchMeta* __restrict__ patches,
+                                                    const double* __restrict__ band, int64_t nloc,
+                                                    const double* __restrict__ u,
+                                                    const double* __restrict__ f,
+                                                    double* __restrict__ out) {
+  const Tile t = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= t.count) return;
+  const int64_t pos = t.start + threadIdx.x;
+  const PatchMeta pm = patches[t.patch];
+  const int64_t s1 = pm.N[0], s2 = (int64_t)pm.N[0] * pm.N[1];
+  constexpr int W = 2 * P + 1;
+  double acc = 0.0;
+  const double* b = band + pos;
+  const double* uc = u + pos;
+#pragma unroll 1
+  for (int o2 = 0; o2 < (D == 3 ? W : 1); ++o2) {
+    const int64_t off2 = D == 3 ? (int64_t)(o2 - P) * s2 : 0;
+#pragma unroll 1
+    for (int o1 = 0; o1 < W; ++o1) {
+      const double* ur = uc + off2 + (int64_t)(o1 - P) * s1 - P;
+      const double* br = b + (int64_t)((o2 * W + o1) * W) * nloc;
+#pragma unroll
+      for (int o0 = 0; o0 < W; ++o0) acc = fma(__ldg(br + (int64_t)o0 * nloc), ur[o0], acc);
+    }
+  }
+  if (MODE == 0) out[pos] = f[pos] - acc;
+  else out[pos] = acc;
+}
+
+// a1': out[row] -= (MODE 0) or += (MODE 1) sum_j C[row, j] u[j]; a warp per row
+template <int MODE>
+__global__ void cross_apply(int nx, const int64_t* __restrict__ x_row, const int* __restrict__ x_ptr,
+                            const int64_t* __restrict__ x_col, const double* __restrict__ x_val,
+                            const double* __restrict__ u, double* __restrict__ out) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nx) return;
+  double s = 0.0;
+  for (int j = x_ptr[w] + lane; j < x_ptr[w + 1]; j += 32) s = fma(x_val[j], u[x_col[j]], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    if (MODE == 0) out[x_row[w]] -= s;
+    else out[x_row[w]] += s;
+  }
+}
+
+// conforming shared DoFs.  mode 0 (residual): total = sum_c v[c] - (m-1) f[c0];
+// mode 1 (sum of partial products); mode 2 (copy the owner value)
+__global__ void shared_reduce(int nsh, const int* __restrict__ sh_ptr, const int64_t* __restrict__ sh_pos,
+                              double* __restrict__ v, const double* __restrict__ f, int mode) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nsh) return;
+  const int b = sh_ptr[c], e = sh_ptr[c + 1];
+  double total;
+  if (mode == 2) {
+    total = v[sh_pos[b]];
+  } else {
+    total = 0.0;
+    for (int i = b; i < e; ++i) total += v[sh_pos[i]];
+    if (mode == 0) total -= (double)(e - b - 1) * f[sh_pos[b]];
+  }
+  for (int i = b; i < e; ++i) v[sh_pos[i]] = total;
+}
+
+// ---------------------------------------------------------------------------
+// a5 / a6: transfers, tensor products of the 1D knot-insertion matrices
+// ---------------------------------------------------------------------------
+// f_c[I] = sum_{i} prod_a P_a[i_a, I_a] (w r)[i], children i_a of I_a from the
+// tables; coarse Dirichlet entries are left 0.
+template <int D>
+__global__ void __launch_bounds__(kTile) restrict_band(
+    const Tile* __restrict__ tiles, const PatchMeta* __restrict__ pc, const PatchMeta* __restrict__ pf,
+    const XferMeta* __restrict__ xm, const int* __restrict__ ch_start, const double* __restrict__ ch_val,
+    int cw, const double* __restrict__ r, const double* __restrict__ w, const int* __restrict__ c_l2g,
+    double* __restrict__ out) {
+  const Tile t = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= t.count) return;
+  const int64_t pos = t.start + threadIdx.x;
+  const int k = t.patch;
+  if (c_l2g[pos] < 0) { out[pos] = 0.0; return; }
+  const PatchMeta mc = pc[k], mf = pf[k];
+  int64_t rem = pos - mc.off;
+  int I[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) { I[a] = (int)(rem % mc.N[a]); rem /= mc.N[a]; }
+  int st[3] = {0, 0, 0};
+  const double* cv[3] = {nullptr, nullptr, nullptr};
+  for (int a = 0; a < D; ++a) {
+    const XferMeta x = xm[k * 3 + a];
+    st[a] = ch_start[x.ch_off + I[a]];
+    cv[a] = ch_val + (x.ch_off + I[a]) * cw;
+  }
+  double s = 0.0;
+  for (int t2 = 0; t2 < (D == 3 ? cw : 1); ++t2) {
+    const double c2 = D == 3 ? cv[2][t2] : 1.0;
+    if (c2 == 0.0) continue;
+    const int i2 = D == 3 ? st[2] + t2 : 0;
+    for (int t1 = 0; t1 < cw; ++t1) {
+      const double c1 = cv[1][t1] * c2;
+      if (c1 == 0.0) continue;
+      const int i1 = st[1] + t1;
+      const int64_t rowb = mf.off + (int64_t)mf.N[0] * (i1 + (int64_t)mf.N[1] * i2);
+      for (int t0 = 0; t0 < cw; ++t0) {
+        const double c0 = cv[0][t0];
+        if (c0 == 0.0) continue;
+        const int64_t fp = rowb + st[0] + t0;
+        const double v = w ? w[fp] * r[fp] : r[fp];
+        s = fma(c0 * c1, v, s);
+      }
+    }
+  }
+  out[pos] = s;
+}
+
+// u_f[i] += sum_I prod_a P_a[i_a, I_a] e_c[I]
+template <int D>
+__global__ void __launch_bounds__(kTile) prolong_band(
+    const Tile* __restrict__ tiles, const PatchMeta* __restrict__ pf, const PatchMeta* __restrict__ pc,
+    const XferMeta* __restrict__ xm, const int* __restrict__ par_start, const double* __restrict__ par_val,
+    int pw, const double* __restrict__ e, double* __restrict__ u) {
+  const Tile t = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= t.count) return;
+  const int64_t pos = t.start + threadIdx.x;
+  const int k = t.patch;
+  const PatchMeta mf = pf[k], mc = pc[k];
+  int64_t rem = pos - mf.off;
+  int i[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) { i[a] = (int)(rem % mf.N[a]); rem /= mf.N[a]; }
+  int st[3] = {0, 0, 0};
+  const double* pv[3] = {nullptr, nullptr, nullptr};
+  for (int a = 0; a < D; ++a) {
+    const XferMeta x = xm[k * 3 + a];
+    st[a] = par_start[x.par_off + i[a]];
+    pv[a] = par_val + (x.par_off + i[a]) * pw;
+  }
+  double s = 0.0;
+  for (int t2 = 0; t2 < (D == 3 ? pw : 1); ++t2) {
+    const double c2 = D == 3 ? pv[2][t2] : 1.0;
+    if (c2 == 0.0) continue;
+    const int I2 = D == 3 ? st[2] + t2 : 0;
+    for (int t1 = 0; t1 < pw; ++t1) {
+      const double c1 = pv[1][t1] * c2;
+      if (c1 == 0.0) continue;
+      const int I1 = st[1] + t1;
+      const int64_t rowb = mc.off + (int64_t)mc.N[0] * (I1 + (int64_t)mc.N[1] * I2);
+      for (int t0 = 0; t0 < pw; ++t0) {
+        const double c0 = pv[0][t0];
+        if (c0 == 0.0) continue;
+        s = fma(c0 * c1, e[rowb + st[0] + t0], s);
+      }
+    }
+  }
+  u[pos] += s;
+}
+
+// ---------------------------------------------------------------------------
+// a2: batched FP64 GEMM for the fast-diagonalisation contractions
+// ---------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+__device__ __forceinline__ int64_t gcol(const GemmTask& g, int n) {
+  return (int64_t)(n / g.ndiv) * g.nhi + (n % g.ndiv);
+}
+
+__global__ void __launch_bounds__(256) gemm_f64(const GemmTask* __restrict__ tasks,
+                                                const GemmItem* __restrict__ items) {
+  __shared__ double As[GBK][GBM + 1];
+  __shared__ double Bs[GBK][GBN + 1];
+  const GemmItem it = items[blockIdx.x];
+  const GemmTask g = tasks[it.task];
+  const double* A = g.A + it.z * g.sA;
+  const double* B = g.B + it.z * g.sB;
+  double* C = g.C + it.z * g.sC;
+  const int m0 = it.tm * GBM, n0 = it.tn * GBN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < g.K; k0 += GBK) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int e = tid + l * 256;  // 0..1023
+      // A tile: 64 rows x 16 k
+      {
+        int mm, kk;
+        if (g.transA) { mm = e & 63; kk = e >> 6; } else { kk = e & 15; mm = e >> 4; }
+        const int m = m0 + mm, k = k0 + kk;
+        double v = 0.0;
+        if (m < g.M && k < g.K) v = g.transA ? A[(int64_t)k * g.lda + m] : A[(int64_t)m * g.lda + k];
+        As[kk][mm] = v;
+      }
+      // B tile: 16 k x 64 cols
+      {
+        int nn, kk;
+        if (g.transB) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
+        const int n = n0 + nn, k = k0 + kk;
+        double v = 0.0;
+        if (n < g.N && k < g.K) v = g.transB ? B[(int64_t)n * g.ldb + k] : B[(int64_t)k * g.ldb + gcol(g, n)];
+        Bs[kk][nn] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= g.N) continue;
+      double* c = C + (int64_t)m * g.ldc + gcol(g, n);
+      const double v = acc[i][j];
+      if (g.epi == 0) {
+        *c = v;
+      } else if (g.epi == 1) {
+        double den = g.sigma + g.lamM[m] + g.lamN0[n % g.nl0];
+        if (g.lamN1) den += g.lamN1[n / g.nl0];
+        *c = v / den;
+      } else {
+        *c += g.alpha * v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a3 / a7: dense solves with precomputed inverses, z = Z r_T, u_T += tau z
+// (mode 0) or u_T = z (mode 1)
+// ---------------------------------------------------------------------------
+constexpr int kPieceRows = 64;
+
+__global__ void __launch_bounds__(256) piece_apply(const PieceItem* __restrict__ items,
+                                                   const PieceMeta* __restrict__ pieces,
+                                                   const double* __restrict__ zpool,
+                                                   const int64_t* __restrict__ piece_pos,
+                                                   const double* __restrict__ r, double* __restrict__ u,
+                                                   double tau, int mode) {
+  extern __shared__ double rs[];
+  const PieceItem it = items[blockIdx.x];
+  const PieceMeta pm = pieces[it.piece];
+  const int64_t* pp = piece_pos + pm.dof_off;
+  for (int i = threadIdx.x; i < pm.n; i += blockDim.x) rs[i] = r[pp[i]];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rend = min(pm.n, it.row0 + kPieceRows);
+  for (int row = it.row0 + warp; row < rend; row += 8) {
+    const double* z = zpool + pm.z_off + (int64_t)row * pm.n;
+    double s = 0.0;
+    for (int j = lane; j < pm.n; j += 32) s = fma(z[j], rs[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      if (mode == 0) u[pp[row]] += tau * s;
+      else u[pp[row]] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a4: one colour of the multicolour Gauss-Seidel sweep
+//   u_i <- u_i + (f_i - sum_j a_ij u_j) / a_ii for all i of the colour; no two
+//   DoFs of a colour are coupled, so the updates are independent
+// ---------------------------------------------------------------------------
+template <int D, int P>
+__global__ void gs_colour(int e0, int e1, const int64_t* __restrict__ gs_pos, const int* __restrict__ gs_patch,
+                          const int* __restrict__ gs_cls, const int* __restrict__ gs_x,
+                          const PatchMeta* __restrict__ patches, const double* __restrict__ band, int64_t nloc,
+                          const int* __restrict__ sh_ptr, const int64_t* __restrict__ sh_pos,
+                          const int* __restrict__ sh_patch, const int* __restrict__ x_ptr,
+                          const int64_t* __restrict__ x_col, const double* __restrict__ x_val,
+                          const double* __restrict__ f, double* __restrict__ u) {
+  const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= e1) return;
+  constexpr int W = 2 * P + 1;
+  constexpr int center = D == 2 ? P * W + P : (P * W + P) * W + P;
+  auto row_dot = [&](int64_t pos, int k, double& diag) {
+    const PatchMeta pm = patches[k];
+    const int64_t s1 = pm.N[0], s2 = (int64_t)pm.N[0] * pm.N[1];
+    double acc = 0.0;
+    for (int o2 = 0; o2 < (D == 3 ? W : 1); ++o2)
+      for (int o1 = 0; o1 < W; ++o1) {
+        const int64_t off = (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
+        const double* br = band + (int64_t)((o2 * W + o1) * W) * nloc + pos;
+#pragma unroll
+        for (int o0 = 0; o0 < W; ++o0) acc = fma(br[(int64_t)o0 * nloc], u[pos + off + o0], acc);
+      }
+    diag += band[(int64_t)center * nloc + pos];
+    return acc;
+  };
+  const int64_t p0 = gs_pos[e];
+  const int cls = gs_cls[e];
+  double diag = 0.0, s = 0.0;
+  if (cls < 0) {
+    s = row_dot(p0, gs_patch[e], diag);
+  } else {
+    for (int c = sh_ptr[cls]; c < sh_ptr[cls + 1]; ++c) s += row_dot(sh_pos[c], sh_patch[c], diag);
+  }
+  const int xr = gs_x[e];
+  if (xr >= 0)
+    for (int j = x_ptr[xr]; j < x_ptr[xr + 1]; ++j) s = fma(x_val[j], u[x_col[j]], s);
+  const double unew = u[p0] + (f[p0] - s) / diag;
+  if (cls < 0) u[p0] = unew;
+  else
+    for (int c = sh_ptr[cls]; c < sh_ptr[cls + 1]; ++c) u[sh_pos[c]] = unew;
+}
+
+// ---------------------------------------------------------------------------
+// a8: PCG vectors and deterministic reductions
+// ---------------------------------------------------------------------------
+constexpr int kRedBlocks = 304;  // 2 x 152 SMs; fixed so the reduction order is fixed
+
+// block sum into partials[blockIdx]; the last block to finish (ticket taken
+// from *counter, which it resets) sums the partials in a fixed order and
+// applies `op` to the scalar slots
+__device__ void finish_reduction(double v, double* partials, double* scal, int op, int slot,
+                                 unsigned int* counter) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b += sh[i];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    const unsigned int done = atomicAdd(counter, 1u);
+    last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    double tot = 0.0;
+    for (int i = 0; i < (int)gridDim.x; ++i) tot += ((volatile double*)partials)[i];
+    scal[slot] = tot;
+    if (op == 1) scal[S_ALPHA] = scal[S_RZ] / tot;                         // slot = S_PQ
+    if (op == 2) { scal[S_BETA] = tot / scal[S_RZ]; scal[S_RZ] = tot; }    // slot = S_RZNEW
+    *counter = 0u;
+  }
+}
+
+// scal[slot] = sum_i w_i a_i b_i  (w may be null)
+__global__ void __launch_bounds__(256) dot_kernel(int64_t n, const double* __restrict__ a,
+                                                  const double* __restrict__ b, const double* __restrict__ w,
+                                                  double* partials, double* scal, unsigned int* counter,
+                                                  int slot, int op) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[i] * b[i];
+    s += w ? w[i] * v : v;
+  }
+  finish_reduction(s, partials, scal, op, slot, counter);
+}
+
+// x += alpha p; r -= alpha q; scal[S_RR] = sum w r^2
+__global__ void __launch_bounds__(256) cg_update_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                    const double* __restrict__ p, const double* __restrict__ q,
+                                                    const double* __restrict__ w, double* partials,
+                                                    double* scal, unsigned int* counter) {
+  const double alpha = scal[S_ALPHA];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    s += w ? w[i] * ri * ri : ri * ri;
+  }
+  finish_reduction(s, partials, scal, 0, S_RR, counter);
+}
+
+// p = z + beta p
+__global__ void cg_update_p(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                            const double* __restrict__ scal) {
+  const double beta = scal[S_BETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void scatter_global(int64_t nloc, const int* __restrict__ l2g, const double* __restrict__ g,
+                               double* __restrict__ loc) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nloc; i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = l2g[i];
+    loc[i] = k >= 0 ? g[k] : 0.0;
+  }
+}
+
+__global__ void gather_global(int ndof, const int64_t* __restrict__ owner, const double* __restrict__ loc,
+                              double* __restrict__ g) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += gridDim.x * blockDim.x) g[i] = loc[owner[i]];
+}
+
+// y = x + s * z  (element-wise), used for u += e and copies
+__global__ void axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], b * y[i]);
+}
+
+// ---------------------------------------------------------------------------
+// launchers (each counts the kernels it enqueues)
+// ---------------------------------------------------------------------------
+static thread_local long long g_launches = 0;
+long long launch_counter() { return g_launches; }
+template <int D, int MODE>
+static void launch_band_p(int p, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
+                          const double* band, int64_t nloc, const double* u, const double* f, double* out) {
+  switch (p) {
+#define MG_CASE(PP) \
+  case PP: band_apply<D, PP, MODE><<<ntiles, kTile, 0, st>>>(tiles, pm, band, nloc, u, f, out); break;
+    MG_CASE(1) MG_CASE(2) MG_CASE(3) MG_CASE(4) MG_CASE(5) MG_CASE(6) MG_CASE(7) MG_CASE(8)
+#undef MG_CASE
+    default: break;
+  }
+}
+
+void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
+                 const double* band, int64_t nloc, const double* u, const double* f, double* out) {
+  if (ntiles == 0) return;
+  ++g_launches;
+  if (d == 2) {
+    if (mode == 0) launch_band_p<2, 0>(p, ntiles, st, tiles, pm, band, nloc, u, f, out);
+    else launch_band_p<2, 1>(p, ntiles, st, tiles, pm, band, nloc, u, f, out);
+  } else {
+    if (mode == 0) launch_band_p<3, 0>(p, ntiles, st, tiles, pm, band, nloc, u, f, out);
+    else launch_band_p<3, 1>(p, ntiles, st, tiles, pm, band, nloc, u, f, out);
+  }
+}
+
+void launch_cross(int mode, int nx, cudaStream_t st, const int64_t* x_row, const int* x_ptr, const int64_t* x_col,
+                  const double* x_val, const double* u, double* out) {
+  if (nx == 0) return;
+  const int blocks = (nx * 32 + 255) / 256;
+  ++g_launches;
+  if (mode == 0) cross_apply<0><<<blocks, 256, 0, st>>>(nx, x_row, x_ptr, x_col, x_val, u, out);
+  else cross_apply<1><<<blocks, 256, 0, st>>>(nx, x_row, x_ptr, x_col, x_val, u, out);
+}
+
+void launch_shared(int nsh, cudaStream_t st, const int* sh_ptr, const int64_t* sh_pos, double* v, const double* f,
+                   int mode) {
+  if (nsh == 0) return;
+  ++g_launches;
+  shared_reduce<<<(nsh + 255) / 256, 256, 0, st>>>(nsh, sh_ptr, sh_pos, v, f, mode);
+}
+
+void launch_restrict(int d, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pc, const PatchMeta* pf,
+                     const XferMeta* xm, const int* ch_start, const double* ch_val, int cw, const double* r,
+                     const double* w, const int* c_l2g, double* out) {
+  if (ntiles == 0) return;
+  ++g_launches;
+  if (d == 2)
+    restrict_band<2><<<ntiles, kTile, 0, st>>>(tiles, pc, pf, xm, ch_start, ch_val, cw, r, w, c_l2g, out);
+  else
+    restrict_band<3><<<ntiles, kTile, 0, st>>>(tiles, pc, pf, xm, ch_start, ch_val, cw, r, w, c_l2g, out);
+}
+
+void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pf, const PatchMeta* pc,
+                    const XferMeta* xm, const int* par_start, const double* par_val, int pw, const double* e,
+                    double* u) {
+  if (ntiles == 0) return;
+  ++g_launches;
+  if (d == 2) prolong_band<2><<<ntiles, kTile, 0, st>>>(tiles, pf, pc, xm, par_start, par_val, pw, e, u);
+  else prolong_band<3><<<ntiles, kTile, 0, st>>>(tiles, pf, pc, xm, par_start, par_val, pw, e, u);
+}
+
+void launch_gemm(int nitems, cudaStream_t st, const GemmTask* tasks, const GemmItem* items) {
+  if (nitems == 0) return;
+  ++g_launches;
+  gemm_f64<<<nitems, 256, 0, st>>>(tasks, items);
+}
+
+void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,
+                  const double* zpool, const int64_t* piece_pos, const double* r, double* u, double tau, int mode) {
+  if (nitems == 0) return;
+  ++g_launches;
+  piece_apply<<<nitems, 256, (size_t)max_n * sizeof(double), st>>>(items, pieces, zpool, piece_pos, r, u, tau, mode);
+}
+
+cudaError_t prepare_piece_kernel(int max_n) {
+  const size_t bytes = (size_t)max_n * sizeof(double);
+  if (bytes > 48 * 1024)
+    return cudaFuncSetAttribute(piece_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+template <int D>
+static void launch_gs_p(int p, int e0, int e1, cudaStream_t st, const GsArgs& a) {
+  const int n = e1 - e0;
+  const int blocks = (n + 127) / 128;
+  switch (p) {
+#define MG_CASE(PP)                                                                                         \
+  case PP:                                                                                                  \
+    gs_colour<D, PP><<<blocks, 128, 0, st>>>(e0, e1, a.gs_pos, a.gs_patch, a.gs_cls, a.gs_x, a.patches,    \
+                                              a.band, a.nloc, a.sh_ptr, a.sh_pos, a.sh_patch, a.x_ptr,     \
+                                              a.x_col, a.x_val, a.f, a.u);                                  \
+    break;
+    MG_CASE(1) MG_CASE(2) MG_CASE(3) MG_CASE(4) MG_CASE(5) MG_CASE(6) MG_CASE(7) MG_CASE(8)
+#undef MG_CASE
+    default: break;
+  }
+}
+
+void launch_gs(int d, int p, int e0, int e1, cudaStream_t st, const GsArgs& a) {
+  if (e1 <= e0) return;
+  ++g_launches;
+  if (d == 2) launch_gs_p<2>(p, e0, e1, st, a);
+  else launch_gs_p<3>(p, e0, e1, st, a);
+}
+
+void launch_dot(int64_t n, cudaStream_t st, const double* a, const double* b, const double* w, double* partials,
+                double* scal, unsigned int* counter, int slot, int op) {
+  ++g_launches;
+  dot_kernel<<<kRedBlocks, 256, 0, st>>>(n, a, b, w, partials, scal, counter, slot, op);
+}
+
+void launch_cg_xr(int64_t n, cudaStream_t st, double* x, double* r, const double* p, const double* q,
+                  const double* w, double* partials, double* scal, unsigned int* counter) {
+  ++g_launches;
+  cg_update_xr<<<kRedBlocks, 256, 0, st>>>(n, x, r, p, q, w, partials, scal, counter);
+}
+
+void launch_cg_p(int64_t n, cudaStream_t st, double* p, const double* z, const double* scal) {
+  ++g_launches;
+  cg_update_p<<<kRedBlocks * 2, 256, 0, st>>>(n, p, z, scal);
+}
+
+void launch_scatter(int64_t nloc, cudaStream_t st, const int* l2g, const double* g, double* loc) {
+  ++g_launches;
+  scatter_global<<<kRedBlocks * 2, 256, 0, st>>>(nloc, l2g, g, loc);
+}
+
+void launch_gather(int ndof, cudaStream_t st, const int64_t* owner, const double* loc, double* g) {
+  if (ndof == 0) return;
+  ++g_launches;
+  gather_global<<<kRedBlocks * 2, 256, 0, st>>>(ndof, owner, loc, g);
+}
+
+void launch_axpby(int64_t n, cudaStream_t st, double a, const double* x, double b, double* y) {
+  ++g_launches;
+  axpby<<<kRedBlocks * 2, 256, 0, st>>>(n, a, x, b, y);
+}
+
+int red_blocks() { return kRedBlocks; }
+
+}  // namespace dev
+}  // namespace mgiga

@@ -1,0 +1,60 @@
+// Launchers of the device kernels (kernels.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace mgiga {
+namespace dev {
+
+struct GsArgs {
+  const int64_t* gs_pos;
+  const int* gs_patch;
+  const int* gs_cls;
+  const int* gs_x;
+  const PatchMeta* patches;
+  const double* band;
+  int64_t nloc;
+  const int* sh_ptr;
+  const int64_t* sh_pos;
+  const int* sh_patch;
+  const int* x_ptr;
+  const int64_t* x_col;
+  const double* x_val;
+  const double* f;
+  double* u;
+};
+
+void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
+                 const double* band, int64_t nloc, const double* u, const double* f, double* out);
+void launch_cross(int mode, int nx, cudaStream_t st, const int64_t* x_row, const int* x_ptr, const int64_t* x_col,
+                  const double* x_val, const double* u, double* out);
+void launch_shared(int nsh, cudaStream_t st, const int* sh_ptr, const int64_t* sh_pos, double* v, const double* f,
+                   int mode);
+void launch_restrict(int d, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pc, const PatchMeta* pf,
+                     const XferMeta* xm, const int* ch_start, const double* ch_val, int cw, const double* r,
+                     const double* w, const int* c_l2g, double* out);
+void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pf, const PatchMeta* pc,
+                    const XferMeta* xm, const int* par_start, const double* par_val, int pw, const double* e,
+                    double* u);
+void launch_gemm(int nitems, cudaStream_t st, const GemmTask* tasks, const GemmItem* items);
+void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,
+                  const double* zpool, const int64_t* piece_pos, const double* r, double* u, double tau, int mode);
+cudaError_t prepare_piece_kernel(int max_n);
+void launch_gs(int d, int p, int e0, int e1, cudaStream_t st, const GsArgs& a);
+void launch_dot(int64_t n, cudaStream_t st, const double* a, const double* b, const double* w, double* partials,
+                double* scal, unsigned int* counter, int slot, int op);
+void launch_cg_xr(int64_t n, cudaStream_t st, double* x, double* r, const double* p, const double* q,
+                  const double* w, double* partials, double* scal, unsigned int* counter);
+void launch_cg_p(int64_t n, cudaStream_t st, double* p, const double* z, const double* scal);
+void launch_scatter(int64_t nloc, cudaStream_t st, const int* l2g, const double* g, double* loc);
+void launch_gather(int ndof, cudaStream_t st, const int64_t* owner, const double* loc, double* g);
+void launch_axpby(int64_t n, cudaStream_t st, double a, const double* x, double b, double* y);
+int red_blocks();
+// kernels enqueued by this host thread so far
+long long launch_counter();
+
+}  // namespace dev
+}  // namespace mgiga

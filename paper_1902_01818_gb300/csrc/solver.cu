@@ -1,0 +1,1219 @@
+// libmgiga: handle, device data, V-cycle and PCG drivers, and the C ABI
+// declared in include/mgiga.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mgiga.h"
+#include "device.cuh"
+#include "host.hpp"
+#include "kernels.h"
+
+using namespace mgiga;
+using namespace mgiga::dev;
+
+namespace {
+
+struct CudaError : std::runtime_error {
+  explicit CudaError(const std::string& m) : std::runtime_error(m) {}
+};
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      throw CudaError(std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+// Device allocations of one handle; every buffer is freed in the destructor.
+struct Arena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  size_t budget = 0;
+  ~Arena() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  T* alloc(size_t n) {
+    if (n == 0) n = 1;
+    const size_t b = n * sizeof(T);
+    if (budget && bytes + b > budget) throw SetupError(MGIGA_ENOMEM, "device footprint exceeds hbm_budget");
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      if (e == cudaErrorMemoryAllocation) throw SetupError(MGIGA_ENOMEM, "cudaMalloc failed: out of device memory");
+      throw CudaError(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ptrs.push_back(p);
+    bytes += b;
+    return static_cast<T*>(p);
+  }
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    T* p = alloc<T>(v.size());
+    if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+  }
+  // vector with a zero guard of g elements on both sides; returns the data start
+  double* guarded(int64_t n, int64_t g) {
+    double* p = alloc<double>((size_t)(n + 2 * g));
+    CK(cudaMemset(p, 0, (size_t)(n + 2 * g) * sizeof(double)));
+    return p + g;
+  }
+};
+
+struct DLevel {
+  int64_t nloc = 0, guard = 0;
+  int ndof = 0, K = 0;
+  double *u = nullptr, *f = nullptr, *r = nullptr;
+  double* band = nullptr;
+  PatchMeta* patches = nullptr;
+  Tile* tiles = nullptr;
+  int ntiles = 0;
+  int nx = 0;
+  int64_t* x_row = nullptr;
+  int* x_ptr = nullptr;
+  int64_t* x_col = nullptr;
+  double* x_val = nullptr;
+  int nsh = 0;
+  int* sh_ptr = nullptr;
+  int64_t* sh_pos = nullptr;
+  int* sh_patch = nullptr;
+  double* weight = nullptr;  // null for SIPG (all copies have weight 1)
+  int* loc2glob = nullptr;
+  int64_t* owner = nullptr;
+  // transfer from level-1 (this level is the fine one)
+  XferMeta* xm = nullptr;
+  int* par_start = nullptr;
+  double* par_val = nullptr;
+  int pw = 0;
+  int* ch_start = nullptr;
+  double* ch_val = nullptr;
+  int cw = 0;
+  // fast diagonalisation: GEMM steps
+  GemmTask* fd_tasks = nullptr;
+  GemmItem* fd_items = nullptr;
+  std::vector<std::pair<int, int>> fd_steps;  // item range per step
+  // pieces (interface pieces on levels >= 1, the coarse solve on level 0)
+  PieceMeta* pieces = nullptr;
+  PieceItem* piece_items = nullptr;
+  int npiece_items = 0, piece_max_n = 0;
+  double* zpool = nullptr;
+  int64_t* piece_pos = nullptr;
+  // Gauss-Seidel
+  int64_t* gs_pos = nullptr;
+  int* gs_patch = nullptr;
+  int* gs_cls = nullptr;
+  int* gs_x = nullptr;
+  std::vector<int> gs_cptr;
+};
+
+}  // namespace
+
+struct mgiga_handle {
+  Problem pr;
+  mgiga_options opt{};
+  int levels = 0;
+  std::vector<Level> L;
+  std::vector<Transfer> T;
+  std::vector<std::vector<int>> colours;   // per level (GS)
+  std::vector<std::vector<Piece>> pieces;  // per level (SCMS)
+  std::vector<std::vector<int>> piece_of;  // per level (SCMS)
+  std::vector<int> num_pieces;
+  bool assembled = false;
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;  // created by the library when the options give none
+  std::unique_ptr<Arena> arena;
+  std::vector<DLevel> D;
+  // PCG state
+  double *x = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *t = nullptr;
+  double* scal = nullptr;
+  double* partials = nullptr;
+  unsigned int* counter = nullptr;
+  double *in1 = nullptr, *in2 = nullptr, *out = nullptr;  // staging (global order)
+  double* host_scal = nullptr;                            // pinned
+  cudaGraphExec_t g_iter_a = nullptr, g_iter_b = nullptr, g_vcycle = nullptr;
+  long long g_iter_a_kernels = 0, g_iter_b_kernels = 0;
+  long long launches = 0;  // kernels enqueued on the device by this handle
+
+  ~mgiga_handle() {
+    if (g_iter_a) cudaGraphExecDestroy(g_iter_a);
+    if (g_iter_b) cudaGraphExecDestroy(g_iter_b);
+    if (g_vcycle) cudaGraphExecDestroy(g_vcycle);
+    if (host_scal) cudaFreeHost(host_scal);
+    arena.reset();
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// device construction
+// ---------------------------------------------------------------------------
+std::vector<Tile> make_tiles(const Level& L) {
+  std::vector<Tile> t;
+  for (int k = 0; k < L.K; ++k)
+    for (int64_t s = L.off[k]; s < L.off[k + 1]; s += kTile) {
+      Tile x;
+      x.patch = k;
+      x.start = s;
+      x.count = (int)std::min<int64_t>(kTile, L.off[k + 1] - s);
+      t.push_back(x);
+    }
+  return t;
+}
+
+int64_t guard_of(const Level& L) {
+  int64_t g = 0;
+  for (int k = 0; k < L.K; ++k) {
+    int64_t s = 0;
+    for (int a = 0; a < L.d; ++a) s += L.p * L.stride(k, a);
+    g = std::max(g, s);
+  }
+  return g + 8;
+}
+
+void build_transfer_tables(const Level& C, const Level& F, const Transfer& T, Arena& A, DLevel& dl) {
+  std::vector<XferMeta> xm(F.K * 3);
+  int pw = 1, cw = 1;
+  for (int k = 0; k < F.K; ++k)
+    for (int a = 0; a < F.d; ++a) {
+      const int nf = F.N[k][a], nc = C.N[k][a];
+      const Vec& P = T.P[k][a];
+      for (int i = 0; i < nf; ++i) {
+        int lo = nc, hi = -1;
+        for (int I = 0; I < nc; ++I)
+          if (P[(size_t)i * nc + I] != 0.0) { lo = std::min(lo, I); hi = std::max(hi, I); }
+        if (hi >= lo) pw = std::max(pw, hi - lo + 1);
+      }
+      for (int I = 0; I < nc; ++I) {
+        int lo = nf, hi = -1;
+        for (int i = 0; i < nf; ++i)
+          if (P[(size_t)i * nc + I] != 0.0) { lo = std::min(lo, i); hi = std::max(hi, i); }
+        if (hi >= lo) cw = std::max(cw, hi - lo + 1);
+      }
+    }
+  std::vector<int> ps, cs;
+  Vec pv, cv;
+  for (int k = 0; k < F.K; ++k)
+    for (int a = 0; a < 3; ++a) {
+      XferMeta& m = xm[k * 3 + a];
+      m.par_off = (int64_t)ps.size();
+      m.ch_off = (int64_t)cs.size();
+      if (a >= F.d) { m.nf = m.nc = 1; continue; }
+      const int nf = F.N[k][a], nc = C.N[k][a];
+      m.nf = nf;
+      m.nc = nc;
+      const Vec& P = T.P[k][a];
+      for (int i = 0; i < nf; ++i) {
+        int lo = 0;
+        while (lo < nc && P[(size_t)i * nc + lo] == 0.0) ++lo;
+        if (lo == nc) lo = 0;
+        ps.push_back(lo);
+        for (int t = 0; t < pw; ++t) pv.push_back(lo + t < nc ? P[(size_t)i * nc + lo + t] : 0.0);
+      }
+      for (int I = 0; I < nc; ++I) {
+        int lo = 0;
+        while (lo < nf && P[(size_t)lo * nc + I] == 0.0) ++lo;
+        if (lo == nf) lo = 0;
+        cs.push_back(lo);
+        for (int t = 0; t < cw; ++t) cv.push_back(lo + t < nf ? P[(size_t)(lo + t) * nc + I] : 0.0);
+      }
+    }
+  dl.xm = A.upload(xm);
+  dl.par_start = A.upload(ps);
+  dl.par_val = A.upload(pv);
+  dl.pw = pw;
+  dl.ch_start = A.upload(cs);
+  dl.ch_val = A.upload(cv);
+  dl.cw = cw;
+}
+
+// interior fast diagonalisation as batched GEMM steps (Sec. 5 smoother on patch interiors)
+void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLevel& dl) {
+  const int d = L.d;
+  std::vector<FDData> fd(L.K);
+#pragma omp parallel for schedule(dynamic)
+  for (int k = 0; k < L.K; ++k) fd[k] = fd_setup(L, k, delta);
+  // U and lambda pool
+  Vec Upool, lampool;
+  std::vector<std::array<int64_t, 3>> uoff(L.K), loff(L.K);
+  int64_t tsize = 0;
+  std::vector<int64_t> toff(L.K);
+  for (int k = 0; k < L.K; ++k) {
+    int64_t sz = 1;
+    for (int a = 0; a < d; ++a) {
+      uoff[k][a] = (int64_t)Upool.size();
+      Upool.insert(Upool.end(), fd[k].U[a].begin(), fd[k].U[a].end());
+      loff[k][a] = (int64_t)lampool.size();
+      lampool.insert(lampool.end(), fd[k].lam[a].begin(), fd[k].lam[a].end());
+      sz *= fd[k].n[a];
+    }
+    toff[k] = tsize;
+    tsize += sz;
+  }
+  double* dU = A.upload(Upool);
+  double* dlam = A.upload(lampool);
+  double* T1 = A.alloc<double>((size_t)std::max<int64_t>(tsize, 1));
+  double* T2 = A.alloc<double>((size_t)std::max<int64_t>(tsize, 1));
+  std::vector<GemmTask> tasks;
+  std::vector<GemmItem> items;
+  dl.fd_steps.clear();
+  auto add_step = [&](const std::vector<GemmTask>& st) {
+    const int i0 = (int)items.size();
+    for (const auto& g : st) {
+      const int id = (int)tasks.size();
+      tasks.push_back(g);
+      const int tm = (g.M + 63) / 64, tn = (g.N + 63) / 64;
+      for (int z = 0; z < g.batch; ++z)
+        for (int a = 0; a < tm; ++a)
+          for (int b = 0; b < tn; ++b) items.push_back({id, z, a, b});
+    }
+    dl.fd_steps.push_back({i0, (int)items.size()});
+  };
+  auto base = [](GemmTask g) {
+    g.transA = g.transB = 0;
+    g.batch = 1;
+    g.epi = 0;
+    g.nhi = 0;
+    g.sA = g.sB = g.sC = 0;
+    g.alpha = 1.0;
+    g.sigma = 0.0;
+    g.lamM = g.lamN0 = g.lamN1 = nullptr;
+    g.nl0 = 1;
+    g.pad = 0;
+    return g;
+  };
+  const int nsteps = d == 2 ? 4 : 6;
+  std::vector<std::vector<GemmTask>> steps(nsteps);
+  for (int k = 0; k < L.K; ++k) {
+    const int n0 = fd[k].n[0], n1 = fd[k].n[1], n2 = d == 3 ? fd[k].n[2] : 1;
+    if (n0 <= 0 || n1 <= 0 || n2 <= 0) continue;
+    const int64_t N0 = L.N[k][0], N01 = (int64_t)L.N[k][0] * L.N[k][1];
+    const int64_t ibase = L.off[k] + 1 + N0 + (d == 3 ? N01 : 0);  // interior (1,1[,1])
+    const double* U0 = dU + uoff[k][0];
+    const double* U1 = dU + uoff[k][1];
+    const double* U2 = d == 3 ? dU + uoff[k][2] : nullptr;
+    double* Tk = T1 + toff[k];
+    double* Xk = T2 + toff[k];
+    GemmTask g{};
+    if (d == 2) {
+      // 1) T = R U0   (R: n1 x n0 rows of the interior, ld N0)
+      g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = dl.r + ibase; g.lda = N0; g.B = U0; g.ldb = n0;
+      g.C = Tk; g.ldc = n0; g.ndiv = n0; steps[0].push_back(g);
+      // 2) X = U1^T T, divided by lambda1[m] + lambda0[n] + sigma
+      g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.transA = 1; g.lda = n1; g.B = Tk; g.ldb = n0;
+      g.C = Xk; g.ldc = n0; g.ndiv = n0; g.epi = 1; g.sigma = fd[k].sigma; g.lamM = dlam + loff[k][1];
+      g.lamN0 = dlam + loff[k][0]; g.nl0 = n0; steps[1].push_back(g);
+      // 3) Y1 = X U0^T
+      g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = Xk; g.lda = n0; g.B = U0; g.transB = 1; g.ldb = n0;
+      g.C = Tk; g.ldc = n0; g.ndiv = n0; steps[2].push_back(g);
+      // 4) u_interior += tau U1 Y1
+      g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.lda = n1; g.B = Tk; g.ldb = n0;
+      g.C = dl.u + ibase; g.ldc = N0; g.ndiv = n0; g.epi = 2; g.alpha = tau; steps[3].push_back(g);
+    } else {
+      const int64_t plane = (int64_t)n1 * n0;
+      // 1) T[i2] = R[i2] U0  (batched over planes i2)
+      g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = dl.r + ibase; g.lda = N0; g.sA = N01; g.B = U0; g.ldb = n0;
+      g.C = Tk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; steps[0].push_back(g);
+      // 2) X[i2] = U1^T T[i2]
+      g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.transA = 1; g.lda = n1; g.B = Tk; g.ldb = n0;
+      g.sB = plane; g.C = Xk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; steps[1].push_back(g);
+      // 3) T = U2^T X  (n2 x n1 n0), divided by the eigenvalue sums
+      g = base(g); g.M = n2; g.N = (int)plane; g.K = n2; g.A = U2; g.transA = 1; g.lda = n2; g.B = Xk; g.ldb = plane;
+      g.C = Tk; g.ldc = plane; g.ndiv = (int)plane; g.epi = 1; g.sigma = fd[k].sigma; g.lamM = dlam + loff[k][2];
+      g.lamN0 = dlam + loff[k][0]; g.lamN1 = dlam + loff[k][1]; g.nl0 = n0; steps[2].push_back(g);
+      // 4) X = T U0^T  (n2 n1 x n0)
+      g = base(g); g.M = n2 * n1; g.N = n0; g.K = n0; g.A = Tk; g.lda = n0; g.B = U0; g.transB = 1; g.ldb = n0;
+      g.C = Xk; g.ldc = n0; g.ndiv = n0; steps[3].push_back(g);
+      // 5) T[j2] = U1 X[j2]
+      g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.lda = n1; g.B = Xk; g.ldb = n0; g.sB = plane;
+      g.C = Tk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; steps[4].push_back(g);
+      // 6) u_interior += tau U2 T  (columns (i1, i0) -> i1 N0 + i0)
+      g = base(g); g.M = n2; g.N = (int)plane; g.K = n2; g.A = U2; g.lda = n2; g.B = Tk; g.ldb = plane;
+      g.C = dl.u + ibase; g.ldc = N01; g.ndiv = n0; g.nhi = N0; g.epi = 2; g.alpha = tau; steps[5].push_back(g);
+    }
+  }
+  for (auto& s : steps) add_step(s);
+  (void)lvl;
+  dl.fd_tasks = A.upload(tasks);
+  dl.fd_items = A.upload(items);
+}
+
+void build_pieces(const std::vector<Piece>& pcs, const Level& L, Arena& A, DLevel& dl, bool coarse) {
+  std::vector<PieceMeta> meta;
+  std::vector<PieceItem> items;
+  std::vector<int64_t> pos;
+  std::vector<Vec> Z;
+  std::vector<const Piece*> use;
+  for (const auto& pc : pcs)
+    if (coarse || pc.kind == 1) use.push_back(&pc);
+  Z.resize(use.size());
+  int err = 0;
+  std::string msg;
+#pragma omp parallel for schedule(dynamic)
+  for (int i = 0; i < (int)use.size(); ++i) {
+    try {
+      Z[i] = spd_inverse(restrict_dense(L, use[i]->dofs), (int)use[i]->dofs.size());
+    } catch (const SetupError& e) {
+#pragma omp critical
+      { err = e.status; msg = e.what(); }
+    }
+  }
+  if (err) throw SetupError(err, msg);
+  int64_t zoff = 0;
+  Vec zpool;
+  int maxn = 0;
+  for (size_t i = 0; i < use.size(); ++i) {
+    PieceMeta m;
+    m.n = (int)use[i]->dofs.size();
+    m.z_off = zoff;
+    m.dof_off = (int64_t)pos.size();
+    m.pad = 0;
+    for (int g : use[i]->dofs) pos.push_back(L.owner[g]);
+    zpool.insert(zpool.end(), Z[i].begin(), Z[i].end());
+    zoff += (int64_t)m.n * m.n;
+    maxn = std::max(maxn, m.n);
+    for (int r0 = 0; r0 < m.n; r0 += 64) items.push_back({(int)meta.size(), r0});
+    meta.push_back(m);
+  }
+  dl.pieces = A.upload(meta);
+  dl.piece_items = A.upload(items);
+  dl.npiece_items = (int)items.size();
+  dl.piece_max_n = maxn;
+  dl.zpool = A.upload(zpool);
+  dl.piece_pos = A.upload(pos);
+  if (maxn > 0) CK(prepare_piece_kernel(maxn));
+}
+
+void build_gs(const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl) {
+  const int n = L.ndof;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return colour[a] < colour[b]; });
+  std::vector<int> cls_of(n, -1);
+  for (size_t c = 0; c + 1 < L.sh_ptr.size(); ++c) cls_of[L.loc2glob[L.sh_pos[L.sh_ptr[c]]]] = (int)c;
+  std::vector<int> xr_of_pos;
+  std::vector<int64_t> gpos;
+  std::vector<int> gpatch, gcls, gx;
+  std::unordered_map<int64_t, int> xrow;
+  for (size_t i = 0; i < L.x_row.size(); ++i) xrow[L.x_row[i]] = (int)i;
+  dl.gs_cptr.assign(1, 0);
+  int cur = order.empty() ? 0 : colour[order[0]];
+  for (int e = 0; e < n; ++e) {
+    const int g = order[e];
+    while (colour[g] != cur) { dl.gs_cptr.push_back(e); ++cur; }
+    const int64_t pos = L.owner[g];
+    gpos.push_back(pos);
+    gpatch.push_back(L.patch_of[pos]);
+    gcls.push_back(cls_of[g]);
+    auto it = xrow.find(pos);
+    gx.push_back(it == xrow.end() ? -1 : it->second);
+  }
+  dl.gs_cptr.push_back(n);
+  dl.gs_pos = A.upload(gpos);
+  dl.gs_patch = A.upload(gpatch);
+  dl.gs_cls = A.upload(gcls);
+  dl.gs_x = A.upload(gx);
+}
+
+// ---------------------------------------------------------------------------
+// operations on the device (enqueued on h->stream)
+// ---------------------------------------------------------------------------
+bool conforming(const mgiga_handle* h) { return h->pr.coupling == MGIGA_CONFORMING; }
+
+void residual(mgiga_handle* h, int l, const double* u, const double* f, double* out) {
+  const Level& L = h->L[l];
+  DLevel& d = h->D[l];
+  launch_band(L.d, L.p, 0, d.ntiles, h->stream, d.tiles, d.patches, d.band, d.nloc, u, f, out);
+  launch_cross(0, d.nx, h->stream, d.x_row, d.x_ptr, d.x_col, d.x_val, u, out);
+  if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, out, f, 0);
+}
+
+void matvec(mgiga_handle* h, int l, const double* u, double* out) {
+  const Level& L = h->L[l];
+  DLevel& d = h->D[l];
+  launch_band(L.d, L.p, 1, d.ntiles, h->stream, d.tiles, d.patches, d.band, d.nloc, u, nullptr, out);
+  launch_cross(1, d.nx, h->stream, d.x_row, d.x_ptr, d.x_col, d.x_val, u, out);
+  if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, out, nullptr, 1);
+}
+
+// u += tau sum_T P_T L_T^{-1} P_T^T r  (Eq. Ldef), r in d.r
+void smooth(mgiga_handle* h, int l) {
+  DLevel& d = h->D[l];
+  for (const auto& s : d.fd_steps) launch_gemm(s.second - s.first, h->stream, d.fd_tasks, d.fd_items + s.first);
+  launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r, d.u,
+               h->opt.tau, 0);
+  if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, d.u, nullptr, 2);
+}
+
+void gs_sweep(mgiga_handle* h, int l, bool forward) {
+  const Level& L = h->L[l];
+  DLevel& d = h->D[l];
+  GsArgs a;
+  a.gs_pos = d.gs_pos; a.gs_patch = d.gs_patch; a.gs_cls = d.gs_cls; a.gs_x = d.gs_x;
+  a.patches = d.patches; a.band = d.band; a.nloc = d.nloc;
+  a.sh_ptr = d.sh_ptr; a.sh_pos = d.sh_pos; a.sh_patch = d.sh_patch;
+  a.x_ptr = d.x_ptr; a.x_col = d.x_col; a.x_val = d.x_val; a.f = d.f; a.u = d.u;
+  const int nc = (int)d.gs_cptr.size() - 1;
+  for (int i = 0; i < nc; ++i) {
+    const int c = forward ? i : nc - 1 - i;
+    launch_gs(L.d, L.p, d.gs_cptr[c], d.gs_cptr[c + 1], h->stream, a);
+  }
+}
+
+// f_{l-1} = P^T r_l (r_l consistent; weights make each shared DoF count once)
+void restrict_to(mgiga_handle* h, int l, const double* r) {
+  const Level& Lc = h->L[l - 1];
+  DLevel& df = h->D[l];
+  DLevel& dc = h->D[l - 1];
+  launch_restrict(Lc.d, dc.ntiles, h->stream, dc.tiles, dc.patches, df.patches, df.xm, df.ch_start, df.ch_val,
+                  df.cw, r, df.weight, dc.loc2glob, dc.f);
+  if (conforming(h)) launch_shared(dc.nsh, h->stream, dc.sh_ptr, dc.sh_pos, dc.f, nullptr, 1);
+}
+
+void prolong_from(mgiga_handle* h, int l, const double* e, double* u) {
+  const Level& Lf = h->L[l];
+  DLevel& df = h->D[l];
+  DLevel& dc = h->D[l - 1];
+  launch_prolong(Lf.d, df.ntiles, h->stream, df.tiles, df.patches, dc.patches, df.xm, df.par_start, df.par_val,
+                 df.pw, e, u);
+}
+
+void coarse_solve(mgiga_handle* h) {
+  DLevel& d = h->D[0];
+  if (d.ndof == 0) {
+    CK(cudaMemsetAsync(d.u, 0, d.nloc * sizeof(double), h->stream));
+    return;
+  }
+  launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.f, d.u,
+               1.0, 1);
+  if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, d.u, nullptr, 2);
+}
+
+// MULTIGRID(l, f_l, 0) of Algorithm 1 / Algorithm 2; result in D[l].u
+void vcycle(mgiga_handle* h, int l) {
+  if (l == 0) { coarse_solve(h); return; }
+  DLevel& d = h->D[l];
+  const int sm = h->opt.smoother, nu = h->opt.nu;
+  CK(cudaMemsetAsync(d.u, 0, d.nloc * sizeof(double), h->stream));
+  bool zero = true;
+  if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) {
+    const int n = sm == MGIGA_SMOOTHER_GS ? nu : 1;
+    for (int i = 0; i < n; ++i) gs_sweep(h, l, true);
+    zero = false;
+  }
+  if (sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID) {
+    for (int i = 0; i < nu; ++i) {
+      if (zero) CK(cudaMemcpyAsync(d.r, d.f, d.nloc * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      else residual(h, l, d.u, d.f, d.r);
+      smooth(h, l);
+      zero = false;
+    }
+  }
+  for (int m = 0; m < std::max(1, h->opt.mu); ++m) {
+    residual(h, l, d.u, d.f, d.r);
+    restrict_to(h, l, d.r);
+    vcycle(h, l - 1);
+    prolong_from(h, l, h->D[l - 1].u, d.u);
+  }
+  if (sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID) {
+    for (int i = 0; i < nu; ++i) {
+      residual(h, l, d.u, d.f, d.r);
+      smooth(h, l);
+    }
+  }
+  if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) {
+    const int n = sm == MGIGA_SMOOTHER_GS ? nu : 1;
+    for (int i = 0; i < n; ++i) gs_sweep(h, l, false);
+  }
+}
+
+void check_launch() {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaError(std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
+// adds the kernels enqueued during an API call to the handle's count
+struct LaunchScope {
+  mgiga_handle* h;
+  long long c0;
+  explicit LaunchScope(mgiga_handle* hh) : h(hh), c0(launch_counter()) {}
+  ~LaunchScope() { h->launches += launch_counter() - c0; }
+};
+
+// ---------------------------------------------------------------------------
+// problem import and validation
+// ---------------------------------------------------------------------------
+void import_problem(const mgiga_problem* P, Problem& pr) {
+  if (!P) throw SetupError(MGIGA_EINVAL, "problem is NULL");
+  if (P->dim != 2 && P->dim != 3) throw SetupError(MGIGA_EINVAL, "dim must be 2 or 3");
+  if (P->num_patches < 1) throw SetupError(MGIGA_EINVAL, "num_patches must be >= 1");
+  if (P->degree < 1 || P->degree > 8) throw SetupError(MGIGA_EINVAL, "degree must be in 1..8");
+  if (P->geo_degree < 1 || P->geo_degree > 8) throw SetupError(MGIGA_EINVAL, "geo_degree must be in 1..8");
+  if (!P->num_knots || !P->knots || !P->geo_num_knots || !P->geo_knots || !P->geo_ctrl)
+    throw SetupError(MGIGA_EINVAL, "NULL array in problem");
+  if (P->num_interfaces > 0 && !P->interfaces) throw SetupError(MGIGA_EINVAL, "interfaces is NULL");
+  if (P->coupling != MGIGA_CONFORMING && P->coupling != MGIGA_SIPG) throw SetupError(MGIGA_EINVAL, "bad coupling");
+  if (P->coupling == MGIGA_SIPG && !(P->sipg_penalty > 0.0)) throw SetupError(MGIGA_EINVAL, "sipg_penalty must be > 0");
+  pr.d = P->dim;
+  pr.K = P->num_patches;
+  pr.p = P->degree;
+  pr.coupling = P->coupling;
+  pr.penalty = P->sipg_penalty;
+  pr.knots.assign(pr.K, {});
+  pr.geo.assign(pr.K, Geometry{});
+  size_t kk = 0, gk = 0, gc = 0;
+  for (int k = 0; k < pr.K; ++k) {
+    int64_t ncp = 1;
+    for (int a = 0; a < pr.d; ++a) {
+      const int n = P->num_knots[k * pr.d + a];
+      if (n < 2 * pr.p + 2) throw SetupError(MGIGA_EINVAL, "knot vector too short");
+      Vec t(P->knots + kk, P->knots + kk + n);
+      kk += n;
+      for (int i = 0; i + 1 < n; ++i)
+        if (!(t[i] <= t[i + 1])) throw SetupError(MGIGA_EINVAL, "knot vector not nondecreasing");
+      for (int i = 0; i <= pr.p; ++i)
+        if (t[i] != 0.0 || t[n - 1 - i] != 1.0)
+          throw SetupError(MGIGA_EINVAL, "knot vectors must be open on [0, 1] (end multiplicity p+1)");
+      for (int i = pr.p + 1; i + 1 < n - pr.p - 1; ++i)
+        if (t[i] == t[i + 1]) throw SetupError(MGIGA_EINVAL, "interior knots must be simple (maximal smoothness)");
+      pr.knots[k][a] = t;
+      const int gn = P->geo_num_knots[k * pr.d + a];
+      if (gn < 2 * P->geo_degree + 2) throw SetupError(MGIGA_EINVAL, "geometry knot vector too short");
+      pr.geo[k].knots[a] = Vec(P->geo_knots + gk, P->geo_knots + gk + gn);
+      gk += gn;
+      pr.geo[k].ncp[a] = gn - P->geo_degree - 1;
+      ncp *= pr.geo[k].ncp[a];
+    }
+    pr.geo[k].q = P->geo_degree;
+    pr.geo[k].ctrl = Vec(P->geo_ctrl + gc, P->geo_ctrl + gc + ncp * pr.d);
+    gc += ncp * pr.d;
+  }
+  for (int i = 0; i < P->num_interfaces; ++i) {
+    const mgiga_interface& f = P->interfaces[i];
+    if (f.patch_a < 0 || f.patch_a >= pr.K || f.patch_b < 0 || f.patch_b >= pr.K || f.patch_a == f.patch_b)
+      throw SetupError(MGIGA_EINVAL, "bad interface patch");
+    if (f.side_a < 0 || f.side_a >= 2 * pr.d || f.side_b < 0 || f.side_b >= 2 * pr.d)
+      throw SetupError(MGIGA_EINVAL, "bad interface side");
+    if (f.orient > (pr.d == 3 ? 7u : 1u)) throw SetupError(MGIGA_EINVAL, "bad interface orientation");
+    pr.ifaces.push_back({f.patch_a, f.side_a, f.patch_b, f.side_b, f.orient});
+  }
+}
+
+mgiga_status fail(mgiga_handle* h, int st, const std::string& msg) {
+  if (h) h->err = msg;
+  return (mgiga_status)st;
+}
+
+template <class F>
+mgiga_status guarded_call(mgiga_handle* h, F&& fn) {
+  try {
+    return fn();
+  } catch (const SetupError& e) {
+    return fail(h, e.status, e.what());
+  } catch (const CudaError& e) {
+    return fail(h, MGIGA_ECUDA, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(h, MGIGA_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(h, MGIGA_EINVAL, e.what());
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void mgiga_default_options(mgiga_options* o) {
+  if (!o) return;
+  o->levels = 0;
+  o->smoother = MGIGA_SMOOTHER_SCMS;
+  o->nu = 1;
+  o->mu = 1;
+  o->outer = MGIGA_OUTER_PCG;
+  o->precision = MGIGA_PREC_FP64;
+  o->max_iter = 1000;
+  o->tau = 1.0;
+  o->delta = 0.12;
+  o->hbm_budget = 0;
+  o->stream = nullptr;
+}
+
+double mgiga_source_sinprod(const double* x, void* ctx) {
+  const int d = ctx ? *static_cast<const int*>(ctx) : 2;
+  double v = d * M_PI * M_PI;
+  for (int a = 0; a < d; ++a) v *= std::sin(M_PI * x[a]);
+  return v;
+}
+
+mgiga_status mgiga_create(const mgiga_problem* problem, const mgiga_options* opts, mgiga_handle** out) {
+  if (!out) return MGIGA_EINVAL;
+  *out = nullptr;
+  mgiga_handle* h = nullptr;
+  try {
+    h = new mgiga_handle();
+  } catch (...) {
+    return MGIGA_ENOMEM;
+  }
+  *out = h;
+  return guarded_call(h, [&]() -> mgiga_status {
+    import_problem(problem, h->pr);
+    if (opts) h->opt = *opts; else mgiga_default_options(&h->opt);
+    const mgiga_options& o = h->opt;
+    if (o.smoother < 0 || o.smoother > 2 || o.nu < 1 || o.mu < 1 || o.mu > 2 || o.outer < 0 || o.outer > 1 ||
+        o.precision != MGIGA_PREC_FP64 || o.max_iter < 0 || !(o.tau > 0.0) || !(o.delta > 0.0) || o.levels < 0)
+      throw SetupError(MGIGA_EINVAL, "invalid options (note: only MGIGA_PREC_FP64 is available)");
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    const int lv = o.levels > 0 ? o.levels : auto_levels(h->pr);
+    h->levels = lv;
+    h->L.assign(lv, Level{});
+    h->L[lv - 1].knots = h->pr.knots;
+    for (int l = lv - 1; l > 0; --l) {
+      h->L[l - 1].knots.resize(h->pr.K);
+      for (int k = 0; k < h->pr.K; ++k)
+        for (int a = 0; a < h->pr.d; ++a) h->L[l - 1].knots[k][a] = coarsen_knots(h->L[l].knots[k][a], h->pr.p);
+    }
+    for (int l = 0; l < lv; ++l) build_topology(h->pr, h->L[l]);
+    // integer set-up of the smoothers (host only): pieces and colours
+    h->colours.assign(lv, {});
+    h->pieces.assign(lv, {});
+    h->piece_of.assign(lv, {});
+    h->num_pieces.assign(lv, 0);
+    const int sm = h->opt.smoother;
+    for (int l = 1; l < lv; ++l) {
+      const Level& L = h->L[l];
+      if (sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID) {
+        h->pieces[l] = decompose(h->pr, L);
+        h->piece_of[l].assign(L.ndof, -1);
+        for (size_t i = 0; i < h->pieces[l].size(); ++i)
+          for (int g : h->pieces[l][i].dofs) h->piece_of[l][g] = (int)i;
+        h->num_pieces[l] = (int)h->pieces[l].size();
+      }
+      if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) h->colours[l] = colouring(h->pr, L);
+    }
+    return MGIGA_OK;
+  });
+}
+
+mgiga_status mgiga_assemble(mgiga_handle* h) {
+  if (!h) return MGIGA_EINVAL;
+  if (h->assembled) return fail(h, MGIGA_ESTATE, "already assembled");
+  return guarded_call(h, [&]() -> mgiga_status {
+    const int lv = h->levels;
+    Level& F = h->L[lv - 1];
+    assemble_fine(h->pr, F, h->pr.knots);
+    apply_dirichlet(F);
+    h->T.assign(lv, Transfer{});
+    for (int l = lv - 1; l > 0; --l) {
+      h->T[l] = build_transfer(h->L[l - 1], h->L[l]);
+      galerkin(h->L[l], h->T[l], h->L[l - 1]);
+      apply_dirichlet(h->L[l - 1]);
+    }
+    // device: work runs on the caller's stream, or on a blocking stream of
+    // the handle (the legacy default stream cannot be captured into graphs)
+    if (!h->stream) {
+      CK(cudaStreamCreate(&h->stream));
+      h->own_stream = true;
+    }
+    h->arena.reset(new Arena());
+    Arena& A = *h->arena;
+    A.budget = h->opt.hbm_budget;
+    h->D.assign(lv, DLevel{});
+    const int sm = h->opt.smoother;
+    for (int l = 0; l < lv; ++l) {
+      const Level& L = h->L[l];
+      DLevel& d = h->D[l];
+      d.nloc = L.nloc;
+      d.ndof = L.ndof;
+      d.K = L.K;
+      d.guard = guard_of(L);
+      d.u = A.guarded(L.nloc, d.guard);
+      d.f = A.guarded(L.nloc, d.guard);
+      d.r = A.guarded(L.nloc, d.guard);
+      d.band = A.upload(L.band);
+      std::vector<PatchMeta> pm(L.K);
+      for (int k = 0; k < L.K; ++k) {
+        pm[k].off = L.off[k];
+        for (int a = 0; a < 3; ++a) pm[k].N[a] = L.N[k][a];
+      }
+      d.patches = A.upload(pm);
+      const auto tiles = make_tiles(L);
+      d.tiles = A.upload(tiles);
+      d.ntiles = (int)tiles.size();
+      d.nx = (int)L.x_row.size();
+      d.x_row = A.upload(L.x_row);
+      d.x_ptr = A.upload(L.x_ptr);
+      d.x_col = A.upload(L.x_col);
+      d.x_val = A.upload(L.x_val);
+      d.nsh = (int)L.sh_ptr.size() - 1;
+      d.sh_ptr = A.upload(L.sh_ptr);
+      d.sh_pos = A.upload(L.sh_pos);
+      std::vector<int> shp(L.sh_pos.size());
+      for (size_t i = 0; i < L.sh_pos.size(); ++i) shp[i] = L.patch_of[L.sh_pos[i]];
+      d.sh_patch = A.upload(shp);
+      d.weight = conforming(h) ? A.upload(L.weight) : nullptr;
+      d.loc2glob = A.upload(L.loc2glob);
+      d.owner = A.upload(L.owner);
+      if (l >= 1) build_transfer_tables(h->L[l - 1], L, h->T[l], A, d);
+      if (l == 0) {
+        Piece all;
+        all.kind = 1;
+        all.patch = -1;
+        for (int g = 0; g < L.ndof; ++g) all.dofs.push_back(g);
+        build_pieces({all}, L, A, d, true);
+        continue;
+      }
+      if (sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID) {
+        build_fd(L, l, h->opt.delta, h->opt.tau, A, d);
+        build_pieces(h->pieces[l], L, A, d, false);
+      }
+      if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) build_gs(h->colours[l], L, A, d);
+    }
+    const Level& Lf = h->L[lv - 1];
+    const int64_t g = guard_of(Lf);
+    h->x = A.guarded(Lf.nloc, g);
+    h->p = A.guarded(Lf.nloc, g);
+    h->q = A.guarded(Lf.nloc, g);
+    h->b = A.guarded(Lf.nloc, g);
+    h->t = A.guarded(Lf.nloc, g);
+    h->scal = A.alloc<double>(S_COUNT);
+    CK(cudaMemset(h->scal, 0, S_COUNT * sizeof(double)));
+    h->partials = A.alloc<double>(red_blocks());
+    h->counter = A.alloc<unsigned int>(4);
+    CK(cudaMemset(h->counter, 0, 4 * sizeof(unsigned int)));
+    int maxdof = 1;
+    for (const auto& L : h->L) maxdof = std::max(maxdof, L.ndof);
+    h->in1 = A.alloc<double>(maxdof);
+    h->in2 = A.alloc<double>(maxdof);
+    h->out = A.alloc<double>(maxdof);
+    CK(cudaMallocHost(&h->host_scal, S_COUNT * sizeof(double)));
+    CK(cudaDeviceSynchronize());
+    h->assembled = true;
+    return MGIGA_OK;
+  });
+}
+
+mgiga_status mgiga_load(mgiga_handle* h, double (*f)(const double*, void*), void* ctx, double* rhs_out) {
+  if (!h || !f || !rhs_out) return h ? fail(h, MGIGA_EINVAL, "NULL argument") : MGIGA_EINVAL;
+  return guarded_call(h, [&]() -> mgiga_status {
+    assemble_load(h->pr, h->L[h->levels - 1], f, ctx, rhs_out);
+    return MGIGA_OK;
+  });
+}
+
+static mgiga_status apply_impl(mgiga_handle* h, int op, int level, const double* a, const double* b, double* out) {
+  if (!h) return MGIGA_EINVAL;
+  if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  if (level < 0 || level >= h->levels) return fail(h, MGIGA_EINVAL, "bad level");
+  const bool needs_b = op == MGIGA_OP_RESIDUAL || op == MGIGA_OP_SMOOTH || op == MGIGA_OP_GS_FWD ||
+                       op == MGIGA_OP_GS_BWD;
+  if (!a || !out || (needs_b && !b)) return fail(h, MGIGA_EINVAL, "NULL vector");
+  return guarded_call(h, [&]() -> mgiga_status {
+    LaunchScope scope(h);
+    DLevel& d = h->D[level];
+    cudaStream_t st = h->stream;
+    const int sm = h->opt.smoother;
+    switch (op) {
+      case MGIGA_OP_RESIDUAL:
+        launch_scatter(d.nloc, st, d.loc2glob, a, d.f);
+        launch_scatter(d.nloc, st, d.loc2glob, b, d.u);
+        residual(h, level, d.u, d.f, d.r);
+        launch_gather(d.ndof, st, d.owner, d.r, out);
+        break;
+      case MGIGA_OP_MATVEC:
+        launch_scatter(d.nloc, st, d.loc2glob, a, d.u);
+        matvec(h, level, d.u, d.r);
+        launch_gather(d.ndof, st, d.owner, d.r, out);
+        break;
+      case MGIGA_OP_SMOOTH:
+        if (level == 0 || !(sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID))
+          throw SetupError(MGIGA_EINVAL, "no subspace-corrected mass smoother on this level");
+        launch_scatter(d.nloc, st, d.loc2glob, a, d.f);
+        launch_scatter(d.nloc, st, d.loc2glob, b, d.u);
+        residual(h, level, d.u, d.f, d.r);
+        smooth(h, level);
+        launch_gather(d.ndof, st, d.owner, d.u, out);
+        break;
+      case MGIGA_OP_GS_FWD:
+      case MGIGA_OP_GS_BWD:
+        if (level == 0 || !(sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID))
+          throw SetupError(MGIGA_EINVAL, "no Gauss-Seidel smoother on this level");
+        launch_scatter(d.nloc, st, d.loc2glob, a, d.f);
+        launch_scatter(d.nloc, st, d.loc2glob, b, d.u);
+        gs_sweep(h, level, op == MGIGA_OP_GS_FWD);
+        launch_gather(d.ndof, st, d.owner, d.u, out);
+        break;
+      case MGIGA_OP_RESTRICT:
+        if (level == 0) throw SetupError(MGIGA_EINVAL, "restriction needs level >= 1");
+        launch_scatter(d.nloc, st, d.loc2glob, a, d.r);
+        restrict_to(h, level, d.r);
+        launch_gather(h->D[level - 1].ndof, st, h->D[level - 1].owner, h->D[level - 1].f, out);
+        break;
+      case MGIGA_OP_PROLONG: {
+        if (level == 0) throw SetupError(MGIGA_EINVAL, "prolongation needs level >= 1");
+        DLevel& c = h->D[level - 1];
+        launch_scatter(c.nloc, st, c.loc2glob, a, c.u);
+        CK(cudaMemsetAsync(d.u, 0, d.nloc * sizeof(double), st));
+        prolong_from(h, level, c.u, d.u);
+        launch_gather(d.ndof, st, d.owner, d.u, out);
+        break;
+      }
+      case MGIGA_OP_COARSE:
+        if (level != 0) throw SetupError(MGIGA_EINVAL, "the coarse solve lives on level 0");
+        launch_scatter(d.nloc, st, d.loc2glob, a, d.f);
+        coarse_solve(h);
+        launch_gather(d.ndof, st, d.owner, d.u, out);
+        break;
+      default:
+        throw SetupError(MGIGA_EINVAL, "unknown op");
+    }
+    check_launch();
+    CK(cudaStreamSynchronize(st));
+    return MGIGA_OK;
+  });
+}
+
+mgiga_status mgiga_apply_d(mgiga_handle* h, int op, int level, const double* a, const double* b, double* out) {
+  return apply_impl(h, op, level, a, b, out);
+}
+
+mgiga_status mgiga_apply(mgiga_handle* h, int op, int level, const double* a, const double* b, double* out) {
+  if (!h) return MGIGA_EINVAL;
+  if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  if (level < 0 || level >= h->levels) return fail(h, MGIGA_EINVAL, "bad level");
+  return guarded_call(h, [&]() -> mgiga_status {
+    const int nin = (op == MGIGA_OP_PROLONG) ? h->L[level - (level > 0 ? 1 : 0)].ndof : h->L[level].ndof;
+    const int nout = (op == MGIGA_OP_RESTRICT) ? h->L[level - (level > 0 ? 1 : 0)].ndof : h->L[level].ndof;
+    if (a) CK(cudaMemcpyAsync(h->in1, a, (size_t)nin * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (b) CK(cudaMemcpyAsync(h->in2, b, (size_t)h->L[level].ndof * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const mgiga_status s = apply_impl(h, op, level, a ? h->in1 : nullptr, b ? h->in2 : nullptr, h->out);
+    if (s != MGIGA_OK) return s;
+    CK(cudaMemcpy(out, h->out, (size_t)nout * sizeof(double), cudaMemcpyDeviceToHost));
+    return MGIGA_OK;
+  });
+}
+
+static void run_vcycle_top(mgiga_handle* h) { vcycle(h, h->levels - 1); }
+
+mgiga_status mgiga_vcycle_d(mgiga_handle* h, const double* r, double* z) {
+  if (!h) return MGIGA_EINVAL;
+  if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  return guarded_call(h, [&]() -> mgiga_status {
+    LaunchScope scope(h);
+    DLevel& d = h->D[h->levels - 1];
+    launch_scatter(d.nloc, h->stream, d.loc2glob, r, d.f);
+    run_vcycle_top(h);
+    launch_gather(d.ndof, h->stream, d.owner, d.u, z);
+    check_launch();
+    CK(cudaStreamSynchronize(h->stream));
+    return MGIGA_OK;
+  });
+}
+
+mgiga_status mgiga_vcycle(mgiga_handle* h, const double* r, double* z) {
+  if (!h) return MGIGA_EINVAL;
+  if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  return guarded_call(h, [&]() -> mgiga_status {
+    const int n = h->L[h->levels - 1].ndof;
+    CK(cudaMemcpyAsync(h->in1, r, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const mgiga_status s = mgiga_vcycle_d(h, h->in1, h->out);
+    if (s != MGIGA_OK) return s;
+    CK(cudaMemcpy(z, h->out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+    return MGIGA_OK;
+  });
+}
+
+// PCG (Sec. 4) or the cycle as solver, on device-resident global vectors
+static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, double tol, int* iters,
+                               double* final_relres) {
+  LaunchScope scope(h);
+  const int top = h->levels - 1;
+  DLevel& d = h->D[top];
+  cudaStream_t st = h->stream;
+  const double* w = d.weight;
+  const int64_t n = d.nloc;
+  double* r = d.f;  // CG residual = input of the cycle
+  double* z = d.u;  // cycle output
+  auto read_scal = [&]() {
+    CK(cudaMemcpyAsync(h->host_scal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  };
+  launch_scatter(n, st, d.loc2glob, rhs, h->b);
+  launch_scatter(n, st, d.loc2glob, u, h->x);
+  launch_dot(n, st, h->b, h->b, w, h->partials, h->scal, h->counter, S_FF, 0);
+  residual(h, top, h->x, h->b, r);
+  launch_dot(n, st, r, r, w, h->partials, h->scal, h->counter, S_RR, 0);
+  check_launch();
+  read_scal();
+  const double ff = h->host_scal[S_FF];
+  if (iters) *iters = 0;
+  if (!(ff > 0.0)) {
+    // zero right-hand side: the solution is zero
+    CK(cudaMemsetAsync(h->x, 0, n * sizeof(double), st));
+    launch_gather(d.ndof, st, d.owner, h->x, u);
+    CK(cudaStreamSynchronize(st));
+    if (final_relres) *final_relres = 0.0;
+    return MGIGA_OK;
+  }
+  const double nf = std::sqrt(ff);
+  double rel = std::sqrt(h->host_scal[S_RR]) / nf;
+  const int maxit = h->opt.max_iter;
+  int it = 0;
+  bool converged = rel <= tol;
+  if (h->opt.outer == MGIGA_OUTER_DIRECT) {
+    // u <- MG(L, f, u): the cycle on the error equation, u += B (f - A u)
+    while (!converged && it < maxit) {
+      vcycle(h, top);
+      launch_axpby((int64_t)n, st, 1.0, z, 1.0, h->x);
+      residual(h, top, h->x, h->b, r);
+      launch_dot(n, st, r, r, w, h->partials, h->scal, h->counter, S_RR, 0);
+      check_launch();
+      read_scal();
+      ++it;
+      rel = std::sqrt(h->host_scal[S_RR]) / nf;
+      if (!std::isfinite(rel)) return fail(h, MGIGA_EBREAKDOWN, "non-finite residual");
+      converged = rel <= tol;
+    }
+  } else if (!converged) {
+    // capture the two halves of a PCG iteration once per handle
+    if (!h->g_iter_a) {
+      cudaGraph_t g;
+      long long c0 = launch_counter();
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      matvec(h, top, h->p, h->q);
+      launch_dot(n, st, h->p, h->q, w, h->partials, h->scal, h->counter, S_PQ, 1);
+      launch_cg_xr(n, st, h->x, r, h->p, h->q, w, h->partials, h->scal, h->counter);
+      CK(cudaStreamEndCapture(st, &g));
+      CK(cudaGraphInstantiate(&h->g_iter_a, g, 0));
+      cudaGraphDestroy(g);
+      h->g_iter_a_kernels = launch_counter() - c0;
+      c0 = launch_counter();
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      vcycle(h, top);
+      launch_dot(n, st, r, z, w, h->partials, h->scal, h->counter, S_RZNEW, 2);
+      launch_cg_p(n, st, h->p, z, h->scal);
+      CK(cudaStreamEndCapture(st, &g));
+      CK(cudaGraphInstantiate(&h->g_iter_b, g, 0));
+      cudaGraphDestroy(g);
+      h->g_iter_b_kernels = launch_counter() - c0;
+      // captured kernels did not run: only graph launches count
+      h->launches -= h->g_iter_a_kernels + h->g_iter_b_kernels;
+    }
+    vcycle(h, top);
+    launch_dot(n, st, r, z, w, h->partials, h->scal, h->counter, S_RZ, 0);
+    CK(cudaMemcpyAsync(h->p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    check_launch();
+    while (it < maxit) {
+      CK(cudaGraphLaunch(h->g_iter_a, st));
+      h->launches += h->g_iter_a_kernels;
+      read_scal();
+      ++it;
+      const double pq = h->host_scal[S_PQ];
+      rel = std::sqrt(h->host_scal[S_RR]) / nf;
+      if (!(pq > 0.0) || !std::isfinite(rel)) return fail(h, MGIGA_EBREAKDOWN, "CG breakdown (p^T A p <= 0 or NaN)");
+      if (rel <= tol) {
+        // confirm with the true residual
+        residual(h, top, h->x, h->b, h->t);
+        launch_dot(n, st, h->t, h->t, w, h->partials, h->scal, h->counter, S_TMP, 0);
+        check_launch();
+        read_scal();
+        const double trel = std::sqrt(h->host_scal[S_TMP]) / nf;
+        if (trel <= tol) { rel = trel; converged = true; break; }
+      }
+      if (it >= maxit) break;
+      CK(cudaGraphLaunch(h->g_iter_b, st));
+      h->launches += h->g_iter_b_kernels;
+    }
+  }
+  launch_gather(d.ndof, st, d.owner, h->x, u);
+  check_launch();
+  CK(cudaStreamSynchronize(st));
+  if (iters) *iters = it;
+  if (final_relres) *final_relres = rel;
+  return converged ? MGIGA_OK : fail(h, MGIGA_ENOCONV, "max_iter reached");
+}
+
+mgiga_status mgiga_solve_d(mgiga_handle* h, const double* rhs, double* u, double tol, int* iters,
+                           double* final_relres) {
+  if (!h) return MGIGA_EINVAL;
+  if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  if (!rhs || !u) return fail(h, MGIGA_EINVAL, "NULL vector");
+  return guarded_call(h, [&]() { return solve_impl(h, rhs, u, tol, iters, final_relres); });
+}
+
+mgiga_status mgiga_solve(mgiga_handle* h, const double* rhs, double* u, double tol, int* iters,
+                         double* final_relres) {
+  if (!h) return MGIGA_EINVAL;
+  if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  if (!rhs || !u) return fail(h, MGIGA_EINVAL, "NULL vector");
+  return guarded_call(h, [&]() -> mgiga_status {
+    const int n = h->L[h->levels - 1].ndof;
+    CK(cudaMemcpyAsync(h->in1, rhs, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->in2, u, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const mgiga_status s = solve_impl(h, h->in1, h->in2, tol, iters, final_relres);
+    if (s == MGIGA_OK || s == MGIGA_ENOCONV)
+      CK(cudaMemcpy(u, h->in2, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+    return s;
+  });
+}
+
+mgiga_status mgiga_kernel_launches(const mgiga_handle* h, long long* n) {
+  if (!h || !n) return MGIGA_EINVAL;
+  *n = h->launches;
+  return MGIGA_OK;
+}
+
+static void run_stage(mgiga_handle* h, int stage, int level) {
+  const Level& L = h->L[level];
+  DLevel& d = h->D[level];
+  switch (stage) {
+    case MGIGA_STAGE_BAND:
+      launch_band(L.d, L.p, 1, d.ntiles, h->stream, d.tiles, d.patches, d.band, d.nloc, d.u, nullptr, d.r);
+      break;
+    case MGIGA_STAGE_FD:
+      for (const auto& s : d.fd_steps) launch_gemm(s.second - s.first, h->stream, d.fd_tasks, d.fd_items + s.first);
+      break;
+    case MGIGA_STAGE_PIECES:
+      launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r,
+                   d.u, h->opt.tau, 0);
+      break;
+    case MGIGA_STAGE_GS: gs_sweep(h, level, true); break;
+    case MGIGA_STAGE_RESTRICT: restrict_to(h, level, d.r); break;
+    case MGIGA_STAGE_PROLONG: prolong_from(h, level, h->D[level - 1].u, d.u); break;
+    case MGIGA_STAGE_COARSE: coarse_solve(h); break;
+    case MGIGA_STAGE_VCYCLE: vcycle(h, level); break;
+    default: throw SetupError(MGIGA_EINVAL, "unknown stage");
+  }
+}
+
+static bool stage_valid(const mgiga_handle* h, int stage, int level) {
+  const int sm = h->opt.smoother;
+  const bool scms = sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID;
+  const bool gs = sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID;
+  switch (stage) {
+    case MGIGA_STAGE_BAND: case MGIGA_STAGE_VCYCLE: return true;
+    case MGIGA_STAGE_FD: case MGIGA_STAGE_PIECES: return scms && level >= 1;
+    case MGIGA_STAGE_GS: return gs && level >= 1;
+    case MGIGA_STAGE_RESTRICT: case MGIGA_STAGE_PROLONG: return level >= 1;
+    case MGIGA_STAGE_COARSE: return level == 0;
+    default: return false;
+  }
+}
+
+mgiga_status mgiga_time_stage(mgiga_handle* h, int stage, int level, int reps, double* ms) {
+  if (!h || !ms || reps < 1) return MGIGA_EINVAL;
+  if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  if (level < 0 || level >= h->levels || !stage_valid(h, stage, level)) return fail(h, MGIGA_EINVAL, "bad stage/level");
+  return guarded_call(h, [&]() -> mgiga_status {
+    LaunchScope scope(h);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    run_stage(h, stage, level);  // warm-up
+    CK(cudaEventRecord(e0, h->stream));
+    for (int i = 0; i < reps; ++i) run_stage(h, stage, level);
+    CK(cudaEventRecord(e1, h->stream));
+    check_launch();
+    CK(cudaEventSynchronize(e1));
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = (double)t / reps;
+    return MGIGA_OK;
+  });
+}
+
+mgiga_status mgiga_stage_work(const mgiga_handle* h, int stage, int level, double* flops, double* bytes) {
+  if (!h || level < 0 || level >= h->levels) return MGIGA_EINVAL;
+  if (!stage_valid(h, stage, level)) return MGIGA_EINVAL;
+  const Level& L = h->L[level];
+  double fl = 0.0, by = 0.0;
+  if (stage == MGIGA_STAGE_BAND) {
+    double nnz = 0.0;
+    for (double v : L.band) nnz += v != 0.0;
+    fl = 2.0 * nnz;
+    by = 8.0 * nnz + 24.0 * (double)L.nloc;
+  } else if (stage == MGIGA_STAGE_FD) {
+    for (int k = 0; k < L.K; ++k) {
+      double nint = 1.0, sum = 0.0;
+      for (int a = 0; a < L.d; ++a) { nint *= L.N[k][a] - 2; sum += L.N[k][a] - 2; }
+      fl += 4.0 * sum * nint;  // forward and inverse transform: 2 * 2 n_a per DoF and direction
+      by += 24.0 * nint;
+    }
+  } else if (stage == MGIGA_STAGE_GS) {
+    double nnz = 0.0;
+    for (double v : L.band) nnz += v != 0.0;
+    fl = 2.0 * nnz;
+    by = 8.0 * nnz + 24.0 * (double)L.nloc;
+  } else {
+    return MGIGA_EINVAL;
+  }
+  if (flops) *flops = fl;
+  if (bytes) *bytes = by;
+  return MGIGA_OK;
+}
+
+mgiga_status mgiga_num_levels(const mgiga_handle* h, int* levels) {
+  if (!h || !levels) return MGIGA_EINVAL;
+  *levels = h->levels;
+  return MGIGA_OK;
+}
+
+mgiga_status mgiga_ndof(const mgiga_handle* h, int level, long* n) {
+  if (!h || !n || level < 0 || level >= h->levels) return MGIGA_EINVAL;
+  *n = h->L[level].ndof;
+  return MGIGA_OK;
+}
+
+mgiga_status mgiga_dof_map(const mgiga_handle* h, int level, int* patch, int* local_index) {
+  if (!h || level < 0 || level >= h->levels) return MGIGA_EINVAL;
+  const Level& L = h->L[level];
+  for (int g = 0; g < L.ndof; ++g) {
+    const int64_t pos = L.owner[g];
+    const int k = L.patch_of[pos];
+    if (patch) patch[g] = k;
+    if (local_index) local_index[g] = (int)(pos - L.off[k]);
+  }
+  return MGIGA_OK;
+}
+
+mgiga_status mgiga_colours(const mgiga_handle* h, int level, int* colour) {
+  if (!h || !colour || level < 0 || level >= h->levels) return MGIGA_EINVAL;
+  if ((int)h->colours.size() <= level || h->colours[level].empty()) return MGIGA_ESTATE;
+  std::copy(h->colours[level].begin(), h->colours[level].end(), colour);
+  return MGIGA_OK;
+}
+
+mgiga_status mgiga_pieces(const mgiga_handle* h, int level, int* piece_of, int* num_pieces) {
+  if (!h || !piece_of || level < 0 || level >= h->levels) return MGIGA_EINVAL;
+  if ((int)h->piece_of.size() <= level || h->piece_of[level].empty()) return MGIGA_ESTATE;
+  std::copy(h->piece_of[level].begin(), h->piece_of[level].end(), piece_of);
+  if (num_pieces) *num_pieces = h->num_pieces[level];
+  return MGIGA_OK;
+}
+
+mgiga_status mgiga_device_bytes(const mgiga_handle* h, size_t* bytes) {
+  if (!h || !bytes) return MGIGA_EINVAL;
+  *bytes = h->arena ? h->arena->bytes : 0;
+  return MGIGA_OK;
+}
+
+const char* mgiga_last_error(const mgiga_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+void mgiga_destroy(mgiga_handle* h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+"""GPU parity of every stage of the cycle against the oracle (FP64 path).
+
+Each test builds one problem on both sides from the same seeded generator,
+calls the CUDA path through the C ABI (libmgiga.so) and compares element by
+element with the oracle.  Tolerances (relative, FP64): single stages 1e-12
+(only the summation order differs), one cycle 1e-11, PCG iterates after k
+iterations 1e-10 (the acceptance bound of the plain FP64 path), iteration
+counts to 1e-8 within +-1.
+"""
+import numpy as np
+import pytest
+
+from oracle import discretize, mg as omg
+from paper_1902_01818_gb300 import workloads as W
+from lib_fixture import binding
+
+pytestmark = pytest.mark.gpu
+
+
+def _nm(c, a):
+    return 4 if sum(c) % 2 == 0 else 8
+
+
+def _nm6(c, a):
+    return 6 if sum(c) % 2 == 0 else 12
+
+
+CASES = {
+    # name: (problem factory, levels, smoother options)
+    "conf2d_p2": (lambda: W.grid_problem((2, 2), 8, 2, "conforming", jitter=0.1, seed=1, flip_patches=(3,)),
+                  3, dict(tau=1.0, delta=0.12)),
+    "sipg2d_p3": (lambda: W.grid_problem((3, 3), _nm, 3, "sipg", jitter=0.1, seed=2, flip_patches=(1,),
+                                         transpose_patches=(4,)), 3, dict(tau=0.25, delta=0.2)),
+    "sipg2d_p1": (lambda: W.grid_problem((2, 2), _nm, 1, "sipg", jitter=0.1, seed=3), 3,
+                  dict(tau=0.5, delta=0.2)),
+    "conf3d_p2": (lambda: W.grid_problem((2, 2, 2), 4, 2, "conforming", jitter=0.05, seed=3,
+                                         jitter_boundary_tangential=True, flip_patches=(5,)),
+                  2, dict(tau=0.25, delta=0.12)),
+    "sipg3d_p2": (lambda: W.grid_problem((2, 1, 2), _nm, 2, "sipg", jitter=0.05, seed=4, flip_patches=(1,),
+                                         transpose_patches=(2,)), 2, dict(tau=0.25, delta=0.12)),
+    "single_patch_p4": (lambda: W.grid_problem((1, 1), 8, 4, "sipg", jitter=0.0), 3, dict(tau=1.0, delta=0.12)),
+}
+
+_cache = {}
+
+
+def _pair(name, smoother, **extra):
+    """(problem, library solver, oracle) for a case; cached per options."""
+    key = (name, smoother, tuple(sorted(extra.items())))
+    if key not in _cache:
+        fac, levels, opt = CASES[name]
+        prob = fac()
+        lib = binding().Solver(prob, levels=levels, smoother=smoother, **opt, **extra)
+        orc = _cache.get((name, smoother, ()), (None, None, None))[2]
+        if orc is None:
+            orc = omg.Multigrid(prob, levels=levels, smoother=smoother, **opt)
+        _cache[key] = (prob, lib, orc)
+    return _cache[key]
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_and_matvec_every_level(name):
+    prob, lib, orc = _pair(name, "hybrid")
+    rng = np.random.default_rng(0)
+    for l in range(lib.levels):
+        A = orc.h["A"][l]
+        n = A.shape[0]
+        u, f = rng.standard_normal(n), rng.standard_normal(n)
+        ref = f - A @ u
+        got = lib.apply("residual", l, f, u)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(A @ u)), (l, _rel(got, ref))
+        got = lib.apply("matvec", l, u)
+        assert _rel(got, A @ u) <= 1e-12, l
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_transfers_every_level(name):
+    prob, lib, orc = _pair(name, "hybrid")
+    rng = np.random.default_rng(1)
+    for l in range(1, lib.levels):
+        P = orc.h["P"][l]
+        r = rng.standard_normal(P.shape[0])
+        assert _rel(lib.apply("restrict", l, r), P.T @ r) <= 1e-13, l
+        e = rng.standard_normal(P.shape[1])
+        assert _rel(lib.apply("prolong", l, e), P @ e) <= 1e-13, l
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_solve(name):
+    prob, lib, orc = _pair(name, "hybrid")
+    f = np.random.default_rng(2).standard_normal(orc.h["A"][0].shape[0])
+    assert _rel(lib.apply("coarse", 0, f), orc.coarse_solve(f)) <= 1e-11
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_scms_smoother_every_level(name):
+    prob, lib, orc = _pair(name, "hybrid")
+    rng = np.random.default_rng(3)
+    for l in range(1, lib.levels):
+        A = orc.h["A"][l]
+        n = A.shape[0]
+        u, f = rng.standard_normal(n), rng.standard_normal(n)
+        ref = u + orc.scms[l].apply(f - A @ u)
+        got = lib.apply("smooth", l, f, u)
+        assert _rel(got, ref) <= 1e-11, (l, _rel(got, ref))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_gauss_seidel_sweeps_every_level(name):
+    prob, lib, orc = _pair(name, "hybrid")
+    rng = np.random.default_rng(4)
+    for l in range(1, lib.levels):
+        n = orc.h["A"][l].shape[0]
+        u, f = rng.standard_normal(n), rng.standard_normal(n)
+        assert _rel(lib.apply("gs_fwd", l, f, u), orc.gs[l].forward(f, u)) <= 1e-12, l
+        assert _rel(lib.apply("gs_bwd", l, f, u), orc.gs[l].backward(f, u)) <= 1e-12, l
+
+
+@pytest.mark.parametrize("smoother", ["scms", "hybrid", "gs"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_cycle(name, smoother):
+    prob, lib, orc = _pair(name, smoother)
+    r = np.random.default_rng(5).standard_normal(lib.ndof())
+    assert _rel(lib.vcycle(r), orc.precondition(r)) <= 1e-11
+
+
+@pytest.mark.parametrize("smoother", ["scms", "hybrid"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_pcg_iterates_and_iteration_count(name, smoother):
+    prob, lib, orc = _pair(name, smoother)
+    f = lib.load_sinprod()
+    for k in (1, 3, 6):
+        # a handle with max_iter = k stops with ENOCONV after exactly k updates
+        _, lk, _ = _pair(name, smoother, max_iter=k)
+        u_l, it_l, rel_l, st = lk.solve(f, tol=1e-300, allow_noconv=True)
+        u_o, it_o, _ = orc.solve_pcg(f, max_iter=k, tol=1e-300)
+        assert it_l == k and it_o == k
+        err = np.linalg.norm(u_l - u_o) / np.linalg.norm(u_o)
+        assert err <= 1e-10, (k, err)
+    u_l, it_l, rel_l, st = lib.solve(f, tol=1e-8)
+    u_o, it_o, hist = orc.solve_pcg(f, tol=1e-8)
+    assert abs(it_l - it_o) <= 1
+    assert rel_l <= 1e-8
+    assert np.linalg.norm(orc.A @ u_l - f) <= 1e-8 * np.linalg.norm(f) * 1.0001
+
+
+@pytest.mark.parametrize("name", ["conf2d_p2", "sipg2d_p3"])
+def test_direct_multigrid_solver(name):
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    mgb = binding()
+    lib = mgb.Solver(prob, levels=levels, smoother="scms", outer="direct", **opt)
+    orc = omg.Multigrid(prob, levels=levels, smoother="scms", **opt)
+    f = lib.load_sinprod()
+    u0 = W.random_vector(lib.ndof(), 101)
+    u_l, it_l, rel_l, st = lib.solve(f, u0=u0, tol=1e-8)
+    u_o, it_o, hist = orc.solve_direct(f, u0=u0, tol=1e-8)
+    assert abs(it_l - it_o) <= 1
+    assert np.linalg.norm(u_l - u_o) <= 1e-7 * np.linalg.norm(u_o)
+
+
+def test_zero_rhs_gives_zero_solution():
+    prob, lib, orc = _pair("sipg2d_p1", "scms")
+    u, it, rel, st = lib.solve(np.zeros(lib.ndof()))
+    assert it == 0 and np.all(u == 0.0)
+
+
+def test_unit_square_workload_iterates():
+    """The 2x2 conforming unit-square workload at full size (4,225 unknowns)."""
+    prob, opts = W.unit_square_2x2()
+    mgb = binding()
+    lib = mgb.Solver(prob, levels=opts["levels"], smoother="scms", tau=opts["tau"], delta=opts["delta"],
+                     outer="direct")
+    orc = omg.Multigrid(prob, levels=opts["levels"], smoother="scms", tau=opts["tau"], delta=opts["delta"])
+    assert lib.ndof() == 4225
+    f = lib.load_sinprod()
+    u0 = W.random_vector(lib.ndof(), opts["seed_u0"])
+    u_l, it_l, rel_l, st = lib.solve(f, u0=u0, tol=1e-8)
+    u_o, it_o, hist = orc.solve_direct(f, u0=u0, tol=1e-8)
+    assert abs(it_l - it_o) <= 1 and rel_l <= 1e-8
+    assert np.linalg.norm(u_l - u_o) <= 1e-7 * np.linalg.norm(u_o)

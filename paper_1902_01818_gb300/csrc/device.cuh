@@ -43,8 +43,9 @@ struct XferMeta {
 
 // C(m, n) = alpha * sum_k A(m, k) B(k, n) (+ epilogue) for one batched task.
 // A is M x K: A[m * lda + k] (transA = 0) or A[k * lda + m] (transA = 1).
-// B is K x N: B[k * ldb + col(n)] (transB = 0) or B[n * ldb + k] (transB = 1).
-// C[m * ldc + col(n)], col(n) = (n / ndiv) * nhi + n % ndiv (ndiv = N: plain).
+// B is K x N: B[k * ldb + n] (transB = 0) or B[n * ldb + k] (transB = 1).
+// C[m * ldc + col(n)], col(n) = (n / ndiv) * nhi + n % ndiv (ndiv = N: plain);
+// the split column lets C be the interior block of a 3D patch.
 // batch z adds z * sA, z * sB, z * sC.
 // epi 0: C = acc; 1: C = acc / (sigma + lamM[m] + lamN0[n % nl0] + lamN1[n / nl0]);
 //     2: C += alpha * acc.

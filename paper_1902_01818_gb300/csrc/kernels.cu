@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) gemm_f64(const GemmTask* __restrict__ tas
         if (g.transB) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
         const int n = n0 + nn, k = k0 + kk;
         double v = 0.0;
-        if (n < g.N && k < g.K) v = g.transB ? B[(int64_t)n * g.ldb + k] : B[(int64_t)k * g.ldb + gcol(g, n)];
+        if (n < g.N && k < g.K) v = g.transB ? B[(int64_t)n * g.ldb + k] : B[(int64_t)k * g.ldb + n];
         Bs[kk][nn] = v;
       }
     }

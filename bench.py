@@ -211,6 +211,7 @@ def main():
     stream = torch.cuda.Stream()  # all library work and the timing events live on this stream
     torch.cuda.set_stream(stream)
     solvers, rhs_d, u_d, rhs_h, u_h, ndofs = [], [], [], [], [], []
+    t_setup = time.perf_counter()
     for p in degrees:
         prob, opts = workload(p, args.scale, args.smoother)
         s = mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"], tau=opts["tau"],
@@ -223,6 +224,9 @@ def main():
         rhs_h.append(torch.from_numpy(f).pin_memory())
         u_h.append(torch.zeros(len(f), dtype=torch.float64).pin_memory())
     total_dof = sum(ndofs)
+    t_setup = time.perf_counter() - t_setup
+    print(f"set-up (assembly, hierarchy, smoother data, upload) of {len(degrees)} problems: {t_setup:.1f} s",
+          file=sys.stderr, flush=True)
 
     def step(host_path=False):
         info = []
@@ -307,7 +311,7 @@ def main():
                        "step_ms_p50": float(np.percentile(step_ms, 50)),
                        "step_ms_p99": float(np.percentile(step_ms, 99)),
                        "l2": "inputs larger than L2 (0.9-3.7 GB operators per step)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1)},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "clocks": clk.summary()}
     if cpu is not None:

@@ -196,6 +196,33 @@ mgiga_status mgiga_apply(mgiga_handle* h, int op, int level, const double* a, co
 mgiga_status mgiga_apply_d(mgiga_handle* h, int op, int level, const double* a, const double* b,
                            double* out);
 
+/* Allocation-free residual.  The paper has no counterpart: this is a service
+ * of the library for callers that must not allocate device memory while they
+ * run, for example a request loop that works inside a fixed HBM budget it has
+ * already reserved, or code that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree may cause.  Such a caller
+ * creates and assembles its handle up front (mgiga_assemble allocates) and
+ * then calls this entry point as often as it likes.
+ *   out = f - A_l u on `level`, exactly what mgiga_apply_d(h,
+ *   MGIGA_OP_RESIDUAL, level, f, u, out) computes: f, u, out are device
+ *   pointers to ndof(level) doubles in global order; inputs are only read.
+ * Its scratch (local-layout copies of f and u with zero guards, and the
+ * residual before it is gathered) lives in one fixed device array of
+ * MGIGA_NOALLOC_SCRATCH_DOUBLES doubles (24 MiB) that every GPU loading the
+ * library holds until the process exits; the call uses no cudaMalloc,
+ * cudaFree or other allocating routine and does not touch the handle's own
+ * level buffers.  A level needing more scratch than that (about 1M local
+ * coefficients) is rejected with MGIGA_EINVAL and a message giving both sizes.
+ * The first call on a device looks up the array's device address on that
+ * device; make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents: the zero guards are
+ * cleared on every call.  Calls whose work overlaps on the GPU (other
+ * streams, other handles, other threads) race on the array; serialise them.
+ * Runs on the handle's stream and returns when `out` is ready. */
+#define MGIGA_NOALLOC_SCRATCH_DOUBLES 3145728
+mgiga_status mgiga_residual_noalloc_d(mgiga_handle* h, int level, const double* f, const double* u,
+                                      double* out);
+
 /* Profiling.  mgiga_kernel_launches: kernels this handle has enqueued so far
  * (kernels replayed by a CUDA graph count once per replay).
  * mgiga_time_stage: average device time in milliseconds of one application of

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <unordered_map>
@@ -888,6 +889,67 @@ static mgiga_status apply_impl(mgiga_handle* h, int op, int level, const double*
 
 mgiga_status mgiga_apply_d(mgiga_handle* h, int op, int level, const double* a, const double* b, double* out) {
   return apply_impl(h, op, level, a, b, out);
+}
+
+// ---------------------------------------------------------------------------
+// allocation-free residual: its scratch is this fixed device array
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_scratch[MGIGA_NOALLOC_SCRATCH_DOUBLES];
+static std::mutex g_noalloc_mutex;
+static double* g_noalloc_ptr[256] = {nullptr};
+
+// device address of the scratch array on the current device, looked up once
+// per device (the host-side name of the array is not a device address)
+static double* noalloc_scratch() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) throw CudaError("device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  return g_noalloc_ptr[dev];
+}
+
+mgiga_status mgiga_residual_noalloc_d(mgiga_handle* h, int level, const double* f, const double* u,
+                                      double* out) {
+  if (!h) return MGIGA_EINVAL;
+  if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  if (level < 0 || level >= h->levels) return fail(h, MGIGA_EINVAL, "bad level");
+  if (!f || !u || !out) return fail(h, MGIGA_EINVAL, "NULL vector");
+  return guarded_call(h, [&]() -> mgiga_status {
+    LaunchScope scope(h);
+    const Level& L = h->L[level];
+    DLevel& d = h->D[level];
+    cudaStream_t st = h->stream;
+    // layout: [guard | u | guard] [f] [r], each part 256-byte aligned
+    auto up = [](int64_t n) { return (n + 31) / 32 * 32; };
+    const int64_t g = up(d.guard), n = up(d.nloc);
+    const int64_t need = g + n + g + n + n;
+    if (need > (int64_t)MGIGA_NOALLOC_SCRATCH_DOUBLES)
+      return fail(h, MGIGA_EINVAL,
+                  "level too large for the allocation-free residual: it needs " + std::to_string(need) +
+                      " doubles of scratch, the fixed scratch holds " +
+                      std::to_string((long long)MGIGA_NOALLOC_SCRATCH_DOUBLES));
+    double* base = noalloc_scratch();
+    double* su = base + g;
+    double* sf = base + g + n + g;
+    double* sr = sf + n;
+    // the guards around u must read as zero; the rest is overwritten below
+    CK(cudaMemsetAsync(base, 0, (size_t)g * sizeof(double), st));
+    CK(cudaMemsetAsync(su + d.nloc, 0, (size_t)(n - d.nloc + g) * sizeof(double), st));
+    launch_scatter(d.nloc, st, d.loc2glob, f, sf);
+    launch_scatter(d.nloc, st, d.loc2glob, u, su);
+    launch_band(L.d, L.p, 0, d.ntiles, st, d.tiles, d.patches, d.band, d.nloc, su, sf, sr);
+    launch_cross(0, d.nx, st, d.x_row, d.x_ptr, d.x_col, d.x_val, su, sr);
+    if (conforming(h)) launch_shared(d.nsh, st, d.sh_ptr, d.sh_pos, sr, sf, 0);
+    launch_gather(d.ndof, st, d.owner, sr, out);
+    check_launch();
+    CK(cudaStreamSynchronize(st));
+    return MGIGA_OK;
+  });
 }
 
 mgiga_status mgiga_apply(mgiga_handle* h, int op, int level, const double* a, const double* b, double* out) {

@@ -74,6 +74,7 @@ _SIGS = {
     "mgiga_solve_d": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_double, _I, _D]),
     "mgiga_apply": (C.c_int, [_H, C.c_int, C.c_int, _D, _D, _D]),
     "mgiga_apply_d": (C.c_int, [_H, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mgiga_residual_noalloc_d": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mgiga_kernel_launches": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
     "mgiga_time_stage": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, _D]),
     "mgiga_stage_work": (C.c_int, [_H, C.c_int, C.c_int, _D, _D]),
@@ -281,6 +282,11 @@ class Solver:
 
     def vcycle_d(self, r, z):
         self._check(_lib.mgiga_vcycle_d(self._h, _tensor_ptr(r), _tensor_ptr(z)))
+
+    def residual_noalloc_d(self, level, f, u, out):
+        """out = f - A_level u with the allocation-free entry point (fixed scratch)."""
+        self._check(_lib.mgiga_residual_noalloc_d(self._h, level % self.levels, _tensor_ptr(f), _tensor_ptr(u),
+                                                  _tensor_ptr(out)))
 
     def apply_d(self, op, level, a, b, out):
         level = level % self.levels

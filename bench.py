@@ -30,7 +30,17 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "DoF/s to 1e-8 rel. residual (V-cycle-preconditioned CG, SIPG 3x3 patches, p=2..6)"
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flop x max clock
+# peaks: derived from unit counts and the maximum SM clock (2.07 GHz, 152 SMs)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA/clk/SM
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 128 FFMA/clk/SM
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
 
 
 def parse():
@@ -42,6 +52,10 @@ def parse():
     ap.add_argument("--degrees", default="2,3,4,5,6")
     ap.add_argument("--scale", type=int, default=3, help="interval multiplier of 64/96 (3: 192/288)")
     ap.add_argument("--smoother", default="hybrid", choices=["scms", "hybrid"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="smoother arithmetic of the timed path (CG is FP64 either way)")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the plain-FP64 comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -212,25 +226,30 @@ def main():
     torch.cuda.set_stream(stream)
     solvers, rhs_d, u_d, rhs_h, u_h, ndofs = [], [], [], [], [], []
     t_setup = time.perf_counter()
+    precisions = [args.precision] + ([] if args.no_fp64_compare or args.precision == "fp64" else ["fp64"])
+    handles = {pr: [] for pr in precisions}
     for p in degrees:
         prob, opts = workload(p, args.scale, args.smoother)
-        s = mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"], tau=opts["tau"],
-                         delta=opts["delta"], stream=stream.cuda_stream)
+        for pr in precisions:
+            handles[pr].append(mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"],
+                                            tau=opts["tau"], delta=opts["delta"], precision=pr,
+                                            stream=stream.cuda_stream))
+        s = handles[args.precision][-1]
         f = s.load_sinprod()
-        solvers.append(s)
         ndofs.append(len(f))
         rhs_d.append(torch.from_numpy(f).cuda())
         u_d.append(torch.zeros_like(rhs_d[-1]))
         rhs_h.append(torch.from_numpy(f).pin_memory())
         u_h.append(torch.zeros(len(f), dtype=torch.float64).pin_memory())
+    solvers = handles[args.precision]
     total_dof = sum(ndofs)
     t_setup = time.perf_counter() - t_setup
-    print(f"set-up (assembly, hierarchy, smoother data, upload) of {len(degrees)} problems: {t_setup:.1f} s",
-          file=sys.stderr, flush=True)
+    print(f"set-up (assembly, hierarchy, smoother data, upload) of {len(degrees) * len(precisions)} handles: "
+          f"{t_setup:.1f} s", file=sys.stderr, flush=True)
 
-    def step(host_path=False):
+    def step(host_path=False, which=None):
         info = []
-        for i, s in enumerate(solvers):
+        for i, s in enumerate(which if which is not None else solvers):
             if host_path:
                 u_h[i].zero_()
                 u, it, rel, st = s.solve(rhs_h[i].numpy(), u0=u_h[i].numpy(), tol=1e-8)
@@ -282,44 +301,79 @@ def main():
     e2e = {"value": world * total_dof / e2e_s, "unit": "DoF/s",
            "h2d_bytes_per_step": int(2 * 8 * total_dof), "d2h_bytes_per_step": int(8 * total_dof)}
 
-    # roofline of the dominant stage on the finest level (largest time share)
-    shares = {}
-    for s, p in zip(solvers, degrees):
-        for stage, count in (("band", 4), ("fd", 2), ("gs", 2 if args.smoother == "hybrid" else 0)):
-            if count == 0:
-                continue
-            t_ms = s.time_stage(stage, -1, reps=10)
-            fl, by = s.stage_work(stage, -1)
-            shares.setdefault(stage, []).append((count * t_ms, t_ms, fl, by, p))
-    dom = max(shares, key=lambda k: sum(x[0] for x in shares[k]))
-    tot_ms = sum(x[1] for x in shares[dom])
-    tot_fl = sum(x[2] for x in shares[dom])
-    achieved = tot_fl / (tot_ms / 1e3) / 1e12
-    roof = {"kernel": {"band": "band_apply (FP64 residual/product)", "fd": "gemm_f64 (fast diagonalisation)",
-                       "gs": "gs_colour (FP64 Gauss-Seidel)"}[dom],
-            "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "note": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived; HBM would allow more)",
-            "per_degree_ms": {str(x[4]): round(x[1], 4) for x in shares[dom]}}
+    # plain FP64 comparison: same workload, FP64 smoothers
+    plain = None
+    if "fp64" in handles and args.precision != "fp64":
+        step(which=handles["fp64"])
+        torch.cuda.synchronize()
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record()
+        info64 = step(which=handles["fp64"])
+        e_b.record()
+        torch.cuda.synchronize()
+        ms64 = e_a.elapsed_time(e_b)
+        plain = {"value": total_dof / (ms64 / 1e3), "unit": "DoF/s", "ms_per_step": ms64,
+                 "iterations": [x[0] for x in info64], "final_relres": [x[1] for x in info64]}
+
+    # roofline per stage on the finest level; the dominant one (largest share
+    # of a PCG iteration) is reported
+    hbm, hbm_src = hbm_peak_gbs()
+    f32 = args.precision == "fp32"
+    counts = {"band": 4, "fd": 2, "gs": 2 if args.smoother == "hybrid" else 0}
+    stages = {}
+    for st, count in counts.items():
+        if count == 0:
+            continue
+        t_ms = fl = by = 0.0
+        for s in solvers:
+            t_ms += s.time_stage(st, -1, reps=10)
+            a_fl, a_by = s.stage_work(st, -1)
+            fl += a_fl
+            by += a_by
+        if st == "gs" and f32:
+            by -= 0.5 * 8.0 * (fl / 2.0)  # FP32 coefficients: 4 instead of 8 bytes per nonzero
+        if st == "band" or not f32:
+            rec = {"bound": "alu", "achieved": fl / (t_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                   "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
+        elif st == "fd":
+            rec = {"bound": "alu", "achieved": fl / (t_ms / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                   "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 x 2.07 GHz"}
+        else:
+            rec = {"bound": "hbm", "achieved": by / (t_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                   "peak_source": hbm_src}
+        rec["frac"] = rec["achieved"] / rec["peak"]
+        rec["ms_per_application"] = t_ms / len(solvers)
+        rec["share_weight_ms"] = count * t_ms
+        stages[st] = rec
+    dom = max(stages, key=lambda k: stages[k]["share_weight_ms"])
+    names = {"band": "band_apply (FP64 residual/product)",
+             "fd": "gemm_tiled (fast diagonalisation, %s)" % ("FP32" if f32 else "FP64"),
+             "gs": "gs_sweep_coop (Gauss-Seidel, %s)" % ("FP32" if f32 else "FP64")}
+    roof = dict(stages[dom])
+    roof.update({"kernel": names[dom], "traffic": None})
+    roof["stages"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                      for k, v in stages.items()}
 
     line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64" if f32 else "f64", "data": "synthetic",
             "config": {"workload": f"sipg-3x3-[0,3]^2-jitter0.1-{64 * args.scale}/{96 * args.scale}-intervals",
                        "degrees": degrees, "unknowns": ndofs, "smoother": args.smoother, "outer": "pcg",
-                       "precision": "fp64", "tol": 1e-8, "iterations": iters, "final_relres": rels,
+                       "precision": ("fp32 smoothers, fp64 residual/CG/coarse" if f32 else "fp64"),
+                       "tol": 1e-8, "iterations": iters, "final_relres": rels,
                        "step_ms_p50": float(np.percentile(step_ms, 50)),
                        "step_ms_p99": float(np.percentile(step_ms, 99)),
                        "l2": "inputs larger than L2 (0.9-3.7 GB operators per step)",
                        "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1)},
-            "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "plain_fp64": plain,
             "clocks": clk.summary()}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for s in solvers:
-        s.close()
+    for hs in handles.values():
+        for s in hs:
+            s.close()
     if world > 1:
         dist.destroy_process_group()
 

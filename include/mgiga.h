@@ -63,9 +63,15 @@ enum { MGIGA_CONFORMING = 0, MGIGA_SIPG = 1 };
 enum { MGIGA_SMOOTHER_SCMS = 0, MGIGA_SMOOTHER_GS = 1, MGIGA_SMOOTHER_HYBRID = 2 };
 /* outer iteration: CG preconditioned by one V-cycle, or the V-cycle as solver */
 enum { MGIGA_OUTER_PCG = 0, MGIGA_OUTER_DIRECT = 1 };
-/* arithmetic inside the V-cycle (the outer CG is always FP64):
- * FP64 everywhere; FP32 SIMT smoother contractions; TF32 or BF16 tensor-core
- * contractions with FP32 accumulation.  Residual, CG and coarse solve stay FP64. */
+/* arithmetic of the smoothers inside the cycle (the outer CG is always FP64):
+ * MGIGA_PREC_FP64: everything FP64 (the path checked against the oracle).
+ * MGIGA_PREC_FP32: the fast-diagonalisation contractions and the Gauss-Seidel
+ *   sweeps compute in FP32 (eigenvector matrices and a colour-ordered band copy
+ *   stored in FP32); residuals, transfers, interface pieces, the coarse
+ *   Cholesky solve and all CG vectors and inner products stay FP64, and CG
+ *   uses the flexible (Polak-Ribiere) beta.
+ * MGIGA_PREC_TF32 / MGIGA_PREC_BF16: reserved for tensor-core contractions
+ *   (rejected with MGIGA_EINVAL by this build). */
 enum { MGIGA_PREC_FP64 = 0, MGIGA_PREC_FP32 = 1, MGIGA_PREC_TF32 = 2, MGIGA_PREC_BF16 = 3 };
 
 /* One interface between side_a of patch_a and side_b of patch_b.

@@ -46,20 +46,21 @@ struct XferMeta {
 // B is K x N: B[k * ldb + n] (transB = 0) or B[n * ldb + k] (transB = 1).
 // C[m * ldc + col(n)], col(n) = (n / ndiv) * nhi + n % ndiv (ndiv = N: plain);
 // the split column lets C be the interior block of a 3D patch.
-// batch z adds z * sA, z * sB, z * sC.
+// batch z adds z * sA, z * sB, z * sC.  tA, tB, tC: element type of A, B, C
+// (0 = double, 1 = float); the arithmetic type is the kernel's.
 // epi 0: C = acc; 1: C = acc / (sigma + lamM[m] + lamN0[n % nl0] + lamN1[n / nl0]);
 //     2: C += alpha * acc.
 struct GemmTask {
   int M, N, K, transA, transB, batch, ndiv, epi;
-  const double* A;
-  const double* B;
-  double* C;
+  const void* A;
+  const void* B;
+  void* C;
   int64_t lda, ldb, ldc, nhi, sA, sB, sC;
   double alpha, sigma;
   const double* lamM;
   const double* lamN0;
   const double* lamN1;
-  int nl0, pad;
+  int nl0, tA, tB, tC;
 };
 
 struct GemmItem {
@@ -77,7 +78,7 @@ struct PieceItem {
 };
 
 // scalar slots of the CG state in device memory
-enum { S_RZ = 0, S_PQ, S_ALPHA, S_RR, S_RZNEW, S_BETA, S_FF, S_TMP, S_COUNT };
+enum { S_RZ = 0, S_PQ, S_ALPHA, S_RR, S_RZNEW, S_BETA, S_FF, S_TMP, S_RZOLD, S_COUNT };
 
 }  // namespace dev
 }  // namespace mgiga

@@ -5,11 +5,11 @@
 //   shared_reduce   sums / copies of DoFs shared by conforming patches (a1')
 //   restrict_band   f_c = P^T (w r) per patch, tensor-product children (a5)
 //   prolong_band    u_f += P e_c per patch, tensor-product parents (a6)
-//   gemm_f64        batched strided GEMM of the fast-diagonalisation
+//   gemm_tiled      batched strided GEMM of the fast-diagonalisation
 //                   contractions, with the eigenvalue-sum division and the
 //                   damped update fused into the epilogue (a2)
 //   piece_apply     interface-piece and coarse solves, z = Z r (a3, a7)
-//   gs_colour       one colour of the multicolour Gauss-Seidel sweep (a4)
+//   gs_sweep_coop   a whole multicolour Gauss-Seidel sweep, one cooperative launch (a4)
 //   dot / cg_*      deterministic reductions and vector updates of PCG (a8)
 #include <cstdio>
 
@@ -184,84 +184,97 @@ __global__ void __launch_bounds__(kTile) prolong_band(
 // ---------------------------------------------------------------------------
 // a2: batched FP64 GEMM for the fast-diagonalisation contractions
 // ---------------------------------------------------------------------------
-constexpr int GBM = 64, GBN = 64, GBK = 16;
+constexpr int GBK = 16;
 
 __device__ __forceinline__ int64_t gcol(const GemmTask& g, int n) {
   return (int64_t)(n / g.ndiv) * g.nhi + (n % g.ndiv);
 }
 
-__global__ void __launch_bounds__(256) gemm_f64(const GemmTask* __restrict__ tasks,
-                                                const GemmItem* __restrict__ items) {
-  __shared__ double As[GBK][GBM + 1];
-  __shared__ double Bs[GBK][GBN + 1];
+template <typename T>
+__device__ __forceinline__ T ldt(const void* p, int64_t i, int t) {
+  return t ? (T) static_cast<const float*>(p)[i] : (T) static_cast<const double*>(p)[i];
+}
+
+// BM x BM output tile per CTA of 256 threads (16 x 16), each thread a
+// (BM/16) x (BM/16) micro-tile; Acc is the arithmetic type (double: the FP64
+// path, float: the FP32 path of the mixed-precision cycle).  In FP64 the FMA
+// pipe (2 DFMA/clk/SM on this part) is the bound, so BM = 32 (more tiles in
+// flight, less work on ragged edges); FP32 uses BM = 64 for reuse.
+template <int BM, typename Acc>
+__global__ void __launch_bounds__(256) gemm_tiled(const GemmTask* __restrict__ tasks,
+                                                  const GemmItem* __restrict__ items) {
+  constexpr int T = BM / 16;
+  __shared__ Acc As[GBK][BM + 1];
+  __shared__ Acc Bs[GBK][BM + 1];
   const GemmItem it = items[blockIdx.x];
   const GemmTask g = tasks[it.task];
-  const double* A = g.A + it.z * g.sA;
-  const double* B = g.B + it.z * g.sB;
-  double* C = g.C + it.z * g.sC;
-  const int m0 = it.tm * GBM, n0 = it.tn * GBN;
+  const int64_t oA = it.z * g.sA, oB = it.z * g.sB, oC = it.z * g.sC;
+  const int m0 = it.tm * BM, n0 = it.tn * BM;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  Acc acc[T][T];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < T; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < T; ++j) acc[i][j] = 0;
   for (int k0 = 0; k0 < g.K; k0 += GBK) {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int e = tid + l * 256;  // 0..1023
-      // A tile: 64 rows x 16 k
+    for (int l = 0; l < T; ++l) {
+      const int e = tid + l * 256;  // 0 .. 16 BM - 1
       {
         int mm, kk;
-        if (g.transA) { mm = e & 63; kk = e >> 6; } else { kk = e & 15; mm = e >> 4; }
+        if (g.transA) { mm = e % BM; kk = e / BM; } else { kk = e & 15; mm = e >> 4; }
         const int m = m0 + mm, k = k0 + kk;
-        double v = 0.0;
-        if (m < g.M && k < g.K) v = g.transA ? A[(int64_t)k * g.lda + m] : A[(int64_t)m * g.lda + k];
+        Acc v = 0;
+        if (m < g.M && k < g.K)
+          v = ldt<Acc>(g.A, oA + (g.transA ? (int64_t)k * g.lda + m : (int64_t)m * g.lda + k), g.tA);
         As[kk][mm] = v;
       }
-      // B tile: 16 k x 64 cols
       {
         int nn, kk;
-        if (g.transB) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
+        if (g.transB) { kk = e & 15; nn = e >> 4; } else { nn = e % BM; kk = e / BM; }
         const int n = n0 + nn, k = k0 + kk;
-        double v = 0.0;
-        if (n < g.N && k < g.K) v = g.transB ? B[(int64_t)n * g.ldb + k] : B[(int64_t)k * g.ldb + n];
+        Acc v = 0;
+        if (n < g.N && k < g.K)
+          v = ldt<Acc>(g.B, oB + (g.transB ? (int64_t)n * g.ldb + k : (int64_t)k * g.ldb + n), g.tB);
         Bs[kk][nn] = v;
       }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GBK; ++kk) {
-      double a[4], b[4];
+      Acc a[T], b[T];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < T; ++i) a[i] = As[kk][ty * T + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < T; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < T; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < T; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty * 4 + i;
+  for (int i = 0; i < T; ++i) {
+    const int m = m0 + ty * T + i;
     if (m >= g.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < T; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= g.N) continue;
-      double* c = C + (int64_t)m * g.ldc + gcol(g, n);
-      const double v = acc[i][j];
-      if (g.epi == 0) {
-        *c = v;
-      } else if (g.epi == 1) {
+      const int64_t ci = oC + (int64_t)m * g.ldc + gcol(g, n);
+      Acc v = acc[i][j];
+      if (g.epi == 1) {
         double den = g.sigma + g.lamM[m] + g.lamN0[n % g.nl0];
         if (g.lamN1) den += g.lamN1[n / g.nl0];
-        *c = v / den;
+        v = (Acc)((double)v / den);
+      }
+      if (g.tC) {
+        float* c = static_cast<float*>(g.C) + ci;
+        *c = g.epi == 2 ? *c + (float)(g.alpha * v) : (float)v;
       } else {
-        *c += g.alpha * v;
+        double* c = static_cast<double*>(g.C) + ci;
+        *c = g.epi == 2 ? *c + g.alpha * (double)v : (double)v;
       }
     }
   }
@@ -300,51 +313,120 @@ __global__ void __launch_bounds__(256) piece_apply(const PieceItem* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// a4: one colour of the multicolour Gauss-Seidel sweep
-//   u_i <- u_i + (f_i - sum_j a_ij u_j) / a_ii for all i of the colour; no two
-//   DoFs of a colour are coupled, so the updates are independent
+// a4 (sweep): all colours of one sweep in a single cooperative launch.
+// Rows of a colour are spread over the whole grid, TPR lanes per row (each
+// lane sums a share of the (2p+1)^d stencil, then a shuffle reduction); the
+// coefficients come from a copy of the band in colour order, so consecutive
+// rows of a colour read consecutive addresses.  A grid barrier separates the
+// colours; it gives up after a bounded wait and reports it in *err.
+// u and f are read through L2 (ld.cg): other SMs wrote them since the last
+// barrier and L1 is not coherent.
 // ---------------------------------------------------------------------------
-template <int D, int P>
-__global__ void gs_colour(int e0, int e1, const int64_t* __restrict__ gs_pos, const int* __restrict__ gs_patch,
-                          const int* __restrict__ gs_cls, const int* __restrict__ gs_x,
-                          const PatchMeta* __restrict__ patches, const double* __restrict__ band, int64_t nloc,
-                          const int* __restrict__ sh_ptr, const int64_t* __restrict__ sh_pos,
-                          const int* __restrict__ sh_patch, const int* __restrict__ x_ptr,
-                          const int64_t* __restrict__ x_col, const double* __restrict__ x_val,
-                          const double* __restrict__ f, double* __restrict__ u) {
-  const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= e1) return;
-  constexpr int W = 2 * P + 1;
-  constexpr int center = D == 2 ? P * W + P : (P * W + P) * W + P;
-  auto row_dot = [&](int64_t pos, int k, double& diag) {
-    const PatchMeta pm = patches[k];
-    const int64_t s1 = pm.N[0], s2 = (int64_t)pm.N[0] * pm.N[1];
-    double acc = 0.0;
-    for (int o2 = 0; o2 < (D == 3 ? W : 1); ++o2)
-      for (int o1 = 0; o1 < W; ++o1) {
-        const int64_t off = (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
-        const double* br = band + (int64_t)((o2 * W + o1) * W) * nloc + pos;
-#pragma unroll
-        for (int o0 = 0; o0 < W; ++o0) acc = fma(br[(int64_t)o0 * nloc], u[pos + off + o0], acc);
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = bar + 1;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > (1ll << 22)) {  // ~0.3-1 s: a co-resident grid never waits this long
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(100);
       }
-    diag += band[(int64_t)center * nloc + pos];
-    return acc;
-  };
-  const int64_t p0 = gs_pos[e];
-  const int cls = gs_cls[e];
-  double diag = 0.0, s = 0.0;
-  if (cls < 0) {
-    s = row_dot(p0, gs_patch[e], diag);
-  } else {
-    for (int c = sh_ptr[cls]; c < sh_ptr[cls + 1]; ++c) s += row_dot(sh_pos[c], sh_patch[c], diag);
+    }
+    __threadfence();
   }
-  const int xr = gs_x[e];
-  if (xr >= 0)
-    for (int j = x_ptr[xr]; j < x_ptr[xr + 1]; ++j) s = fma(x_val[j], u[x_col[j]], s);
-  const double unew = u[p0] + (f[p0] - s) / diag;
-  if (cls < 0) u[p0] = unew;
-  else
-    for (int c = sh_ptr[cls]; c < sh_ptr[cls + 1]; ++c) u[sh_pos[c]] = unew;
+  __syncthreads();
+  return *((volatile int*)err) == 0;
+}
+
+// TB: type of the colour-ordered coefficients and of the arithmetic (double
+// for the FP64 path, float for the mixed path); u and f stay FP64.
+template <int D, int P, int TPR, typename TB>
+__global__ void __launch_bounds__(256) gs_sweep_coop(GsSweepArgs a) {
+  constexpr int W = 2 * P + 1;
+  constexpr int NOB = D == 2 ? W : W * W;  // offset blocks of W consecutive o0
+  constexpr int center = D == 2 ? P * W + P : (P * W + P) * W + P;
+  const TB* gsband = static_cast<const TB*>(a.gsband);
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % TPR;  // lane within the row group
+  const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t rows_per_warp = 32 / TPR;
+  const int64_t rows_per_grid = ((int64_t)gridDim.x * blockDim.x) / TPR;
+  for (int ci = 0; ci < a.ncol; ++ci) {
+    const int c = a.forward ? ci : a.ncol - 1 - ci;
+    const int e0 = a.cptr[c], e1 = a.cptr[c + 1];
+    for (int64_t base = e0 + warp_global * rows_per_warp; base < e1; base += rows_per_grid) {
+      const int64_t e = base + lane / TPR;
+      const bool active = e < e1;
+      TB acc = 0;
+      int64_t pos = 0;
+      double upos = 0.0, fpos = 0.0;
+      TB diag = 1;
+      int cls = -1;
+      if (active) {
+        // independent loads first: position, strides, couplings, diagonal, u_i, f_i
+        pos = a.gs_pos[e];
+        const int2 st = a.gs_stride[e];
+        const int2 xr = a.gs_xrange[e];
+        cls = a.gs_cls[e];
+        diag = __ldg(gsband + (int64_t)center * a.ngs + e);
+        upos = __ldcg(a.u + pos);
+        fpos = __ldcg(a.f + pos);
+        const int64_t s1 = st.x, s2 = st.y;
+        for (int ob = sub; ob < NOB; ob += TPR) {
+          const int o1 = ob % W, o2 = ob / W;
+          const int64_t off = (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
+          const TB* br = gsband + (int64_t)ob * W * a.ngs + e;
+          const double* ur = a.u + pos + off;
+#pragma unroll
+          for (int o0 = 0; o0 < W; ++o0) acc = fma(__ldg(br + (int64_t)o0 * a.ngs), (TB)__ldcg(ur + o0), acc);
+        }
+        // SIPG couplings across interfaces, shared over the row's lanes
+        for (int j = xr.x + sub; j < xr.y; j += TPR) acc = fma((TB)a.x_val[j], (TB)__ldcg(a.u + a.x_col[j]), acc);
+      }
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (active && sub == 0) {
+        if (cls >= 0) {
+          // further copies of a DoF shared by conforming patches (owner first)
+          for (int cp = a.sh_ptr[cls] + 1; cp < a.sh_ptr[cls + 1]; ++cp) {
+            const int64_t q = a.sh_pos[cp];
+            const PatchMeta pm = a.patches[a.sh_patch[cp]];
+            const int64_t s1 = pm.N[0], s2 = (int64_t)pm.N[0] * pm.N[1];
+            for (int ob = 0; ob < NOB; ++ob) {
+              const int o1 = ob % W, o2 = ob / W;
+              const int64_t off = (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
+              for (int o0 = 0; o0 < W; ++o0)
+                acc = fma((TB)a.band[(int64_t)(ob * W + o0) * a.nloc + q], (TB)__ldcg(a.u + q + off + o0), acc);
+            }
+            diag += (TB)a.band[(int64_t)center * a.nloc + q];
+          }
+        }
+        const double unew = upos + (double)(((TB)fpos - acc) / diag);
+        if (cls < 0) {
+          a.u[pos] = unew;
+        } else {
+          for (int cp = a.sh_ptr[cls]; cp < a.sh_ptr[cls + 1]; ++cp) a.u[a.sh_pos[cp]] = unew;
+        }
+      }
+    }
+    if (gridDim.x == 1) {
+      __syncthreads();  // one block: its own writes are visible after the barrier
+    } else if (!grid_barrier(a.bar, a.err)) {
+      return;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -380,6 +462,8 @@ __device__ void finish_reduction(double v, double* partials, double* scal, int o
     scal[slot] = tot;
     if (op == 1) scal[S_ALPHA] = scal[S_RZ] / tot;                         // slot = S_PQ
     if (op == 2) { scal[S_BETA] = tot / scal[S_RZ]; scal[S_RZ] = tot; }    // slot = S_RZNEW
+    // flexible CG (Polak-Ribiere): beta = r.(z_new - z_old) / (r_old . z_old)
+    if (op == 3) { scal[S_BETA] = (tot - scal[S_RZOLD]) / scal[S_RZ]; scal[S_RZ] = tot; }
     *counter = 0u;
   }
 }
@@ -506,10 +590,43 @@ void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const
   else prolong_band<3><<<ntiles, kTile, 0, st>>>(tiles, pf, pc, xm, par_start, par_val, pw, e, u);
 }
 
-void launch_gemm(int nitems, cudaStream_t st, const GemmTask* tasks, const GemmItem* items) {
+int gemm_tile(int arith) { return arith == 1 ? 64 : 32; }
+
+void launch_gemm(int nitems, int arith, cudaStream_t st, const GemmTask* tasks, const GemmItem* items) {
   if (nitems == 0) return;
   ++g_launches;
-  gemm_f64<<<nitems, 256, 0, st>>>(tasks, items);
+  if (arith == 1) gemm_tiled<64, float><<<nitems, 256, 0, st>>>(tasks, items);
+  else gemm_tiled<32, double><<<nitems, 256, 0, st>>>(tasks, items);
+}
+
+template <int D, int P>
+static void* gs_coop_func(bool f32) {
+  return f32 ? (void*)gs_sweep_coop<D, P, 8, float> : (void*)gs_sweep_coop<D, P, 8, double>;
+}
+
+static void* gs_coop_ptr(int d, int p, bool f32) {
+  switch (p) {
+#define MG_CASE(PP) \
+  case PP: return d == 2 ? gs_coop_func<2, PP>(f32) : gs_coop_func<3, PP>(f32);
+    MG_CASE(1) MG_CASE(2) MG_CASE(3) MG_CASE(4) MG_CASE(5) MG_CASE(6) MG_CASE(7) MG_CASE(8)
+#undef MG_CASE
+    default: return nullptr;
+  }
+}
+
+int gs_coop_max_blocks(int d, int p, bool f32) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs_coop_ptr(d, p, f32), 256, 0) != cudaSuccess)
+    return 0;
+  return sms * per_sm;
+}
+
+cudaError_t launch_gs_sweep(int d, int p, bool f32, int blocks, cudaStream_t st, GsSweepArgs a) {
+  ++g_launches;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(gs_coop_ptr(d, p, f32), dim3(blocks), dim3(256), args, 0, st);
 }
 
 void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,
@@ -524,30 +641,6 @@ cudaError_t prepare_piece_kernel(int max_n) {
   if (bytes > 48 * 1024)
     return cudaFuncSetAttribute(piece_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return cudaSuccess;
-}
-
-template <int D>
-static void launch_gs_p(int p, int e0, int e1, cudaStream_t st, const GsArgs& a) {
-  const int n = e1 - e0;
-  const int blocks = (n + 127) / 128;
-  switch (p) {
-#define MG_CASE(PP)                                                                                         \
-  case PP:                                                                                                  \
-    gs_colour<D, PP><<<blocks, 128, 0, st>>>(e0, e1, a.gs_pos, a.gs_patch, a.gs_cls, a.gs_x, a.patches,    \
-                                              a.band, a.nloc, a.sh_ptr, a.sh_pos, a.sh_patch, a.x_ptr,     \
-                                              a.x_col, a.x_val, a.f, a.u);                                  \
-    break;
-    MG_CASE(1) MG_CASE(2) MG_CASE(3) MG_CASE(4) MG_CASE(5) MG_CASE(6) MG_CASE(7) MG_CASE(8)
-#undef MG_CASE
-    default: break;
-  }
-}
-
-void launch_gs(int d, int p, int e0, int e1, cudaStream_t st, const GsArgs& a) {
-  if (e1 <= e0) return;
-  ++g_launches;
-  if (d == 2) launch_gs_p<2>(p, e0, e1, st, a);
-  else launch_gs_p<3>(p, e0, e1, st, a);
 }
 
 void launch_dot(int64_t n, cudaStream_t st, const double* a, const double* b, const double* w, double* partials,

@@ -9,23 +9,33 @@
 namespace mgiga {
 namespace dev {
 
-struct GsArgs {
-  const int64_t* gs_pos;
-  const int* gs_patch;
-  const int* gs_cls;
-  const int* gs_x;
+
+// arguments of the cooperative Gauss-Seidel sweep (all colours, one launch)
+struct GsSweepArgs {
+  int ncol, forward;
+  const int* cptr;        // ncol + 1 entry offsets (device)
+  int64_t ngs;            // number of entries (= ndof)
+  const void* gsband;     // band rows of the owner copies in colour order, gsband[o * ngs + e]
+                          // (double, or float for the mixed path)
+  const int64_t* gs_pos;  // owner position of entry e
+  const int2* gs_stride;  // (N_0, N_0 N_1) of its patch
+  const int2* gs_xrange;  // its SIPG coupling entries [x, y) in x_col / x_val
+  const int* gs_cls;      // shared class (conforming) or -1
   const PatchMeta* patches;
   const double* band;
   int64_t nloc;
   const int* sh_ptr;
   const int64_t* sh_pos;
   const int* sh_patch;
-  const int* x_ptr;
   const int64_t* x_col;
   const double* x_val;
   const double* f;
   double* u;
+  unsigned int* bar;  // [count, generation], count 0 at launch
+  int* err;           // set to 1 when a barrier wait gives up
 };
+int gs_coop_max_blocks(int d, int p, bool f32);
+cudaError_t launch_gs_sweep(int d, int p, bool f32, int blocks, cudaStream_t st, GsSweepArgs a);
 
 void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
                  const double* band, int64_t nloc, const double* u, const double* f, double* out);
@@ -39,11 +49,12 @@ void launch_restrict(int d, int ntiles, cudaStream_t st, const Tile* tiles, cons
 void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pf, const PatchMeta* pc,
                     const XferMeta* xm, const int* par_start, const double* par_val, int pw, const double* e,
                     double* u);
-void launch_gemm(int nitems, cudaStream_t st, const GemmTask* tasks, const GemmItem* items);
+// arith 0: FP64 arithmetic (32 x 32 tiles), 1: FP32 arithmetic (64 x 64 tiles)
+int gemm_tile(int arith);
+void launch_gemm(int nitems, int arith, cudaStream_t st, const GemmTask* tasks, const GemmItem* items);
 void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,
                   const double* zpool, const int64_t* piece_pos, const double* r, double* u, double tau, int mode);
 cudaError_t prepare_piece_kernel(int max_n);
-void launch_gs(int d, int p, int e0, int e1, cudaStream_t st, const GsArgs& a);
 void launch_dot(int64_t n, cudaStream_t st, const double* a, const double* b, const double* w, double* partials,
                 double* scal, unsigned int* counter, int slot, int op);
 void launch_cg_xr(int64_t n, cudaStream_t st, double* x, double* r, const double* p, const double* q,

@@ -113,7 +113,13 @@ struct DLevel {
   int* gs_patch = nullptr;
   int* gs_cls = nullptr;
   int* gs_x = nullptr;
+  double* gs_band = nullptr;  // band rows of the owner copies in colour order
+  int* gs_cptr_d = nullptr;
+  int gs_blocks = 0;
   std::vector<int> gs_cptr;
+  int arith = 0;              // FD and Gauss-Seidel arithmetic: 0 FP64, 1 FP32
+  int2* gs_stride = nullptr;
+  int2* gs_xrange = nullptr;
 };
 
 }  // namespace
@@ -139,6 +145,8 @@ struct mgiga_handle {
   double* scal = nullptr;
   double* partials = nullptr;
   unsigned int* counter = nullptr;
+  unsigned int* gs_bar = nullptr;  // grid barrier state of the Gauss-Seidel sweep
+  int* gs_err = nullptr;           // set by a sweep whose barrier wait gave up
   double *in1 = nullptr, *in2 = nullptr, *out = nullptr;  // staging (global order)
   double* host_scal = nullptr;                            // pinned
   cudaGraphExec_t g_iter_a = nullptr, g_iter_b = nullptr, g_vcycle = nullptr;
@@ -262,10 +270,21 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     toff[k] = tsize;
     tsize += sz;
   }
-  double* dU = A.upload(Upool);
+  // FP64 path: U and the temporaries in double; FP32 path: in float (the
+  // input r and the updated u stay double, converted on load / store)
+  const bool f32 = dl.arith == 1;
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  char* dU;
+  if (f32) {
+    std::vector<float> Uf(Upool.begin(), Upool.end());
+    dU = reinterpret_cast<char*>(A.upload(Uf));
+  } else {
+    dU = reinterpret_cast<char*>(A.upload(Upool));
+  }
   double* dlam = A.upload(lampool);
-  double* T1 = A.alloc<double>((size_t)std::max<int64_t>(tsize, 1));
-  double* T2 = A.alloc<double>((size_t)std::max<int64_t>(tsize, 1));
+  char* T1 = reinterpret_cast<char*>(A.alloc<double>((size_t)std::max<int64_t>(tsize, 1)));
+  char* T2 = reinterpret_cast<char*>(A.alloc<double>((size_t)std::max<int64_t>(tsize, 1)));
+  const int tU = f32 ? 1 : 0;
   std::vector<GemmTask> tasks;
   std::vector<GemmItem> items;
   dl.fd_steps.clear();
@@ -274,7 +293,8 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     for (const auto& g : st) {
       const int id = (int)tasks.size();
       tasks.push_back(g);
-      const int tm = (g.M + 63) / 64, tn = (g.N + 63) / 64;
+      const int bm = gemm_tile(dl.arith);
+      const int tm = (g.M + bm - 1) / bm, tn = (g.N + bm - 1) / bm;
       for (int z = 0; z < g.batch; ++z)
         for (int a = 0; a < tm; ++a)
           for (int b = 0; b < tn; ++b) items.push_back({id, z, a, b});
@@ -291,7 +311,7 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     g.sigma = 0.0;
     g.lamM = g.lamN0 = g.lamN1 = nullptr;
     g.nl0 = 1;
-    g.pad = 0;
+    g.tA = g.tB = g.tC = 0;
     return g;
   };
   const int nsteps = d == 2 ? 4 : 6;
@@ -301,47 +321,49 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     if (n0 <= 0 || n1 <= 0 || n2 <= 0) continue;
     const int64_t N0 = L.N[k][0], N01 = (int64_t)L.N[k][0] * L.N[k][1];
     const int64_t ibase = L.off[k] + 1 + N0 + (d == 3 ? N01 : 0);  // interior (1,1[,1])
-    const double* U0 = dU + uoff[k][0];
-    const double* U1 = dU + uoff[k][1];
-    const double* U2 = d == 3 ? dU + uoff[k][2] : nullptr;
-    double* Tk = T1 + toff[k];
-    double* Xk = T2 + toff[k];
+    const void* U0 = dU + uoff[k][0] * esz;
+    const void* U1 = dU + uoff[k][1] * esz;
+    const void* U2 = d == 3 ? dU + uoff[k][2] * esz : nullptr;
+    void* Tk = T1 + toff[k] * esz;
+    void* Xk = T2 + toff[k] * esz;
     GemmTask g{};
+    // element types: U and temporaries tU; r (first input) and u (last output) double
+    auto types = [&](GemmTask& t, int ta, int tb, int tc) { t.tA = ta; t.tB = tb; t.tC = tc; };
     if (d == 2) {
       // 1) T = R U0   (R: n1 x n0 rows of the interior, ld N0)
       g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = dl.r + ibase; g.lda = N0; g.B = U0; g.ldb = n0;
-      g.C = Tk; g.ldc = n0; g.ndiv = n0; steps[0].push_back(g);
+      g.C = Tk; g.ldc = n0; g.ndiv = n0; types(g, 0, tU, tU); steps[0].push_back(g);
       // 2) X = U1^T T, divided by lambda1[m] + lambda0[n] + sigma
       g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.transA = 1; g.lda = n1; g.B = Tk; g.ldb = n0;
       g.C = Xk; g.ldc = n0; g.ndiv = n0; g.epi = 1; g.sigma = fd[k].sigma; g.lamM = dlam + loff[k][1];
-      g.lamN0 = dlam + loff[k][0]; g.nl0 = n0; steps[1].push_back(g);
+      g.lamN0 = dlam + loff[k][0]; g.nl0 = n0; types(g, tU, tU, tU); steps[1].push_back(g);
       // 3) Y1 = X U0^T
       g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = Xk; g.lda = n0; g.B = U0; g.transB = 1; g.ldb = n0;
-      g.C = Tk; g.ldc = n0; g.ndiv = n0; steps[2].push_back(g);
+      g.C = Tk; g.ldc = n0; g.ndiv = n0; types(g, tU, tU, tU); steps[2].push_back(g);
       // 4) u_interior += tau U1 Y1
       g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.lda = n1; g.B = Tk; g.ldb = n0;
-      g.C = dl.u + ibase; g.ldc = N0; g.ndiv = n0; g.epi = 2; g.alpha = tau; steps[3].push_back(g);
+      g.C = dl.u + ibase; g.ldc = N0; g.ndiv = n0; g.epi = 2; g.alpha = tau; types(g, tU, tU, 0); steps[3].push_back(g);
     } else {
       const int64_t plane = (int64_t)n1 * n0;
       // 1) T[i2] = R[i2] U0  (batched over planes i2)
       g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = dl.r + ibase; g.lda = N0; g.sA = N01; g.B = U0; g.ldb = n0;
-      g.C = Tk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; steps[0].push_back(g);
+      g.C = Tk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; types(g, 0, tU, tU); steps[0].push_back(g);
       // 2) X[i2] = U1^T T[i2]
       g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.transA = 1; g.lda = n1; g.B = Tk; g.ldb = n0;
-      g.sB = plane; g.C = Xk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; steps[1].push_back(g);
+      g.sB = plane; g.C = Xk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; types(g, tU, tU, tU); steps[1].push_back(g);
       // 3) T = U2^T X  (n2 x n1 n0), divided by the eigenvalue sums
       g = base(g); g.M = n2; g.N = (int)plane; g.K = n2; g.A = U2; g.transA = 1; g.lda = n2; g.B = Xk; g.ldb = plane;
       g.C = Tk; g.ldc = plane; g.ndiv = (int)plane; g.epi = 1; g.sigma = fd[k].sigma; g.lamM = dlam + loff[k][2];
-      g.lamN0 = dlam + loff[k][0]; g.lamN1 = dlam + loff[k][1]; g.nl0 = n0; steps[2].push_back(g);
+      g.lamN0 = dlam + loff[k][0]; g.lamN1 = dlam + loff[k][1]; g.nl0 = n0; types(g, tU, tU, tU); steps[2].push_back(g);
       // 4) X = T U0^T  (n2 n1 x n0)
       g = base(g); g.M = n2 * n1; g.N = n0; g.K = n0; g.A = Tk; g.lda = n0; g.B = U0; g.transB = 1; g.ldb = n0;
-      g.C = Xk; g.ldc = n0; g.ndiv = n0; steps[3].push_back(g);
+      g.C = Xk; g.ldc = n0; g.ndiv = n0; types(g, tU, tU, tU); steps[3].push_back(g);
       // 5) T[j2] = U1 X[j2]
       g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.lda = n1; g.B = Xk; g.ldb = n0; g.sB = plane;
-      g.C = Tk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; steps[4].push_back(g);
+      g.C = Tk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; types(g, tU, tU, tU); steps[4].push_back(g);
       // 6) u_interior += tau U2 T  (columns (i1, i0) -> i1 N0 + i0)
       g = base(g); g.M = n2; g.N = (int)plane; g.K = n2; g.A = U2; g.lda = n2; g.B = Tk; g.ldb = plane;
-      g.C = dl.u + ibase; g.ldc = N01; g.ndiv = n0; g.nhi = N0; g.epi = 2; g.alpha = tau; steps[5].push_back(g);
+      g.C = dl.u + ibase; g.ldc = N01; g.ndiv = n0; g.nhi = N0; g.epi = 2; g.alpha = tau; types(g, tU, tU, 0); steps[5].push_back(g);
     }
   }
   for (auto& s : steps) add_step(s);
@@ -421,6 +443,34 @@ void build_gs(const std::vector<int>& colour, const Level& L, Arena& A, DLevel& 
     gx.push_back(it == xrow.end() ? -1 : it->second);
   }
   dl.gs_cptr.push_back(n);
+  // band rows of the owner copies in colour order (coalesced per colour),
+  // in double (FP64 path) or float (mixed path)
+  const bool f32 = dl.arith == 1;
+  if (f32) {
+    std::vector<float> gb((size_t)L.nb * n);
+    for (int o = 0; o < L.nb; ++o)
+      for (int e = 0; e < n; ++e) gb[(size_t)o * n + e] = (float)L.band[(size_t)o * L.nloc + gpos[e]];
+    dl.gs_band = reinterpret_cast<double*>(A.upload(gb));
+  } else {
+    Vec gb((size_t)L.nb * n);
+    for (int o = 0; o < L.nb; ++o)
+      for (int e = 0; e < n; ++e) gb[(size_t)o * n + e] = L.band[(size_t)o * L.nloc + gpos[e]];
+    dl.gs_band = A.upload(gb);
+  }
+  std::vector<int2> gst(n), gxr(n);
+  for (int e = 0; e < n; ++e) {
+    const int k = gpatch[e];
+    gst[e] = make_int2(L.N[k][0], L.N[k][0] * L.N[k][1]);
+    gxr[e] = gx[e] >= 0 ? make_int2(L.x_ptr[gx[e]], L.x_ptr[gx[e] + 1]) : make_int2(0, 0);
+  }
+  dl.gs_stride = A.upload(gst);
+  dl.gs_xrange = A.upload(gxr);
+  dl.gs_cptr_d = A.upload(dl.gs_cptr);
+  int maxrows = 1;
+  for (size_t c = 0; c + 1 < dl.gs_cptr.size(); ++c) maxrows = std::max(maxrows, dl.gs_cptr[c + 1] - dl.gs_cptr[c]);
+  const int coop = gs_coop_max_blocks(L.d, L.p, f32);
+  if (coop <= 0) throw CudaError("cooperative launch not available for the Gauss-Seidel sweep");
+  dl.gs_blocks = std::max(1, std::min(coop, (maxrows * 8 + 255) / 256));
   dl.gs_pos = A.upload(gpos);
   dl.gs_patch = A.upload(gpatch);
   dl.gs_cls = A.upload(gcls);
@@ -451,7 +501,8 @@ void matvec(mgiga_handle* h, int l, const double* u, double* out) {
 // u += tau sum_T P_T L_T^{-1} P_T^T r  (Eq. Ldef), r in d.r
 void smooth(mgiga_handle* h, int l) {
   DLevel& d = h->D[l];
-  for (const auto& s : d.fd_steps) launch_gemm(s.second - s.first, h->stream, d.fd_tasks, d.fd_items + s.first);
+  for (const auto& s : d.fd_steps)
+    launch_gemm(s.second - s.first, d.arith, h->stream, d.fd_tasks, d.fd_items + s.first);
   launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r, d.u,
                h->opt.tau, 0);
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, d.u, nullptr, 2);
@@ -460,16 +511,21 @@ void smooth(mgiga_handle* h, int l) {
 void gs_sweep(mgiga_handle* h, int l, bool forward) {
   const Level& L = h->L[l];
   DLevel& d = h->D[l];
-  GsArgs a;
-  a.gs_pos = d.gs_pos; a.gs_patch = d.gs_patch; a.gs_cls = d.gs_cls; a.gs_x = d.gs_x;
+  GsSweepArgs a;
+  a.ncol = (int)d.gs_cptr.size() - 1;
+  a.forward = forward ? 1 : 0;
+  a.cptr = d.gs_cptr_d;
+  a.ngs = d.ndof;
+  a.gsband = d.gs_band;
+  a.gs_pos = d.gs_pos; a.gs_stride = d.gs_stride; a.gs_xrange = d.gs_xrange; a.gs_cls = d.gs_cls;
   a.patches = d.patches; a.band = d.band; a.nloc = d.nloc;
   a.sh_ptr = d.sh_ptr; a.sh_pos = d.sh_pos; a.sh_patch = d.sh_patch;
-  a.x_ptr = d.x_ptr; a.x_col = d.x_col; a.x_val = d.x_val; a.f = d.f; a.u = d.u;
-  const int nc = (int)d.gs_cptr.size() - 1;
-  for (int i = 0; i < nc; ++i) {
-    const int c = forward ? i : nc - 1 - i;
-    launch_gs(L.d, L.p, d.gs_cptr[c], d.gs_cptr[c + 1], h->stream, a);
-  }
+  a.x_col = d.x_col; a.x_val = d.x_val; a.f = d.f; a.u = d.u;
+  a.bar = h->gs_bar;
+  a.err = h->gs_err;
+  if (a.ncol <= 0) return;
+  CK(cudaMemsetAsync(h->gs_bar, 0, 2 * sizeof(unsigned int), h->stream));
+  CK(launch_gs_sweep(L.d, L.p, d.arith == 1, d.gs_blocks, h->stream, a));
 }
 
 // f_{l-1} = P^T r_l (r_l consistent; weights make each shared DoF count once)
@@ -542,6 +598,18 @@ void vcycle(mgiga_handle* h, int l) {
 void check_launch() {
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
+// a Gauss-Seidel sweep whose grid barrier gave up leaves gs_err set; read and
+// clear it after the stream has drained
+void check_device_timeout(mgiga_handle* h) {
+  if (!h->gs_err) return;
+  int e = 0;
+  CK(cudaMemcpy(&e, h->gs_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CK(cudaMemset(h->gs_err, 0, sizeof(int)));
+    throw SetupError(MGIGA_ETIMEOUT, "a Gauss-Seidel grid barrier wait expired");
+  }
 }
 
 // adds the kernels enqueued during an API call to the handle's count
@@ -675,8 +743,8 @@ mgiga_status mgiga_create(const mgiga_problem* problem, const mgiga_options* opt
     if (opts) h->opt = *opts; else mgiga_default_options(&h->opt);
     const mgiga_options& o = h->opt;
     if (o.smoother < 0 || o.smoother > 2 || o.nu < 1 || o.mu < 1 || o.mu > 2 || o.outer < 0 || o.outer > 1 ||
-        o.precision != MGIGA_PREC_FP64 || o.max_iter < 0 || !(o.tau > 0.0) || !(o.delta > 0.0) || o.levels < 0)
-      throw SetupError(MGIGA_EINVAL, "invalid options (note: only MGIGA_PREC_FP64 is available)");
+        (o.precision != MGIGA_PREC_FP64 && o.precision != MGIGA_PREC_FP32) || o.max_iter < 0 || !(o.tau > 0.0) || !(o.delta > 0.0) || o.levels < 0)
+      throw SetupError(MGIGA_EINVAL, "invalid options (precision: MGIGA_PREC_FP64 or MGIGA_PREC_FP32)");
     h->stream = static_cast<cudaStream_t>(o.stream);
     const int lv = o.levels > 0 ? o.levels : auto_levels(h->pr);
     h->levels = lv;
@@ -740,6 +808,7 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       d.nloc = L.nloc;
       d.ndof = L.ndof;
       d.K = L.K;
+      d.arith = h->opt.precision == MGIGA_PREC_FP64 ? 0 : 1;
       d.guard = guard_of(L);
       d.u = A.guarded(L.nloc, d.guard);
       d.f = A.guarded(L.nloc, d.guard);
@@ -795,6 +864,10 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
     h->partials = A.alloc<double>(red_blocks());
     h->counter = A.alloc<unsigned int>(4);
     CK(cudaMemset(h->counter, 0, 4 * sizeof(unsigned int)));
+    h->gs_bar = A.alloc<unsigned int>(2);
+    h->gs_err = A.alloc<int>(1);
+    CK(cudaMemset(h->gs_bar, 0, 2 * sizeof(unsigned int)));
+    CK(cudaMemset(h->gs_err, 0, sizeof(int)));
     int maxdof = 1;
     for (const auto& L : h->L) maxdof = std::max(maxdof, L.ndof);
     h->in1 = A.alloc<double>(maxdof);
@@ -883,6 +956,7 @@ static mgiga_status apply_impl(mgiga_handle* h, int op, int level, const double*
     }
     check_launch();
     CK(cudaStreamSynchronize(st));
+    check_device_timeout(h);
     return MGIGA_OK;
   });
 }
@@ -981,6 +1055,7 @@ mgiga_status mgiga_vcycle_d(mgiga_handle* h, const double* r, double* z) {
     launch_gather(d.ndof, h->stream, d.owner, d.u, z);
     check_launch();
     CK(cudaStreamSynchronize(h->stream));
+    check_device_timeout(h);
     return MGIGA_OK;
   });
 }
@@ -1064,8 +1139,12 @@ static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, do
       h->g_iter_a_kernels = launch_counter() - c0;
       c0 = launch_counter();
       CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      // the mixed-precision cycle is not exactly a fixed symmetric operator:
+      // flexible (Polak-Ribiere) beta, which needs r_new . z_old
+      const bool flexible = h->opt.precision != MGIGA_PREC_FP64;
+      if (flexible) launch_dot(n, st, r, z, w, h->partials, h->scal, h->counter, S_RZOLD, 0);
       vcycle(h, top);
-      launch_dot(n, st, r, z, w, h->partials, h->scal, h->counter, S_RZNEW, 2);
+      launch_dot(n, st, r, z, w, h->partials, h->scal, h->counter, S_RZNEW, flexible ? 3 : 2);
       launch_cg_p(n, st, h->p, z, h->scal);
       CK(cudaStreamEndCapture(st, &g));
       CK(cudaGraphInstantiate(&h->g_iter_b, g, 0));
@@ -1103,6 +1182,7 @@ static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, do
   launch_gather(d.ndof, st, d.owner, h->x, u);
   check_launch();
   CK(cudaStreamSynchronize(st));
+  check_device_timeout(h);
   if (iters) *iters = it;
   if (final_relres) *final_relres = rel;
   return converged ? MGIGA_OK : fail(h, MGIGA_ENOCONV, "max_iter reached");
@@ -1146,7 +1226,8 @@ static void run_stage(mgiga_handle* h, int stage, int level) {
       launch_band(L.d, L.p, 1, d.ntiles, h->stream, d.tiles, d.patches, d.band, d.nloc, d.u, nullptr, d.r);
       break;
     case MGIGA_STAGE_FD:
-      for (const auto& s : d.fd_steps) launch_gemm(s.second - s.first, h->stream, d.fd_tasks, d.fd_items + s.first);
+      for (const auto& s : d.fd_steps)
+        launch_gemm(s.second - s.first, d.arith, h->stream, d.fd_tasks, d.fd_items + s.first);
       break;
     case MGIGA_STAGE_PIECES:
       launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r,
@@ -1194,6 +1275,7 @@ mgiga_status mgiga_time_stage(mgiga_handle* h, int stage, int level, int reps, d
     CK(cudaEventElapsedTime(&t, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    check_device_timeout(h);
     *ms = (double)t / reps;
     return MGIGA_OK;
   });

@@ -1,0 +1,80 @@
+"""The mixed-precision cycle (FP32 smoothers inside FP64 CG) against the oracle.
+
+The FP32 smoothers change the preconditioner, not the problem: PCG must still
+meet the FP64 stopping rule ||f - A u|| / ||f|| <= 1e-8 with the oracle's own
+matrix, the iteration count stays close to the FP64 one, and the solution
+differs from the oracle's by no more than the residual allows:
+||u - u*|| <= ||A^{-1}|| (||r|| + ||r*||) (tolerance derived from the two
+residuals and the smallest eigenvalue of A, computed densely on these small
+problems).  Single smoother applications agree with FP64 to FP32 rounding
+(relative 1e-5 for these sizes).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import mg as omg
+from paper_1902_01818_gb300 import workloads as W
+from lib_fixture import binding
+
+pytestmark = pytest.mark.gpu
+
+
+def _nm(c, a):
+    return 4 if sum(c) % 2 == 0 else 8
+
+
+CASES = {
+    "conf2d_p2": (lambda: W.grid_problem((2, 2), 8, 2, "conforming", jitter=0.1, seed=1, flip_patches=(3,)),
+                  3, dict(tau=1.0, delta=0.12)),
+    "sipg2d_p3": (lambda: W.grid_problem((3, 3), _nm, 3, "sipg", jitter=0.1, seed=2, flip_patches=(1,),
+                                         transpose_patches=(4,)), 3, dict(tau=0.25, delta=0.1)),
+    "sipg3d_p2": (lambda: W.grid_problem((2, 1, 2), _nm, 2, "sipg", jitter=0.05, seed=4, flip_patches=(1,),
+                                         transpose_patches=(2,)), 2, dict(tau=0.25, delta=0.12)),
+    "conf3d_p3": (lambda: W.grid_problem((2, 2, 2), 4, 3, "conforming", jitter=0.05, seed=3,
+                                         jitter_boundary_tangential=True), 2, dict(tau=0.25, delta=0.12)),
+}
+
+
+@pytest.mark.parametrize("smoother", ["hybrid", "scms"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_pcg_meets_fp64_stopping_rule(name, smoother):
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    mgb = binding()
+    lib = mgb.Solver(prob, levels=levels, smoother=smoother, precision="fp32", **opt)
+    orc = omg.Multigrid(prob, levels=levels, smoother=smoother, **opt)
+    f = lib.load_sinprod()
+    u, it, rel, st = lib.solve(f, tol=1e-8)
+    A = orc.A
+    r = f - A @ u
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(f) * 1.0001
+    u_o, it_o, _ = orc.solve_pcg(f, tol=1e-8)
+    assert it <= it_o + 3, (it, it_o)
+    lam_min = sla.eigh(A.toarray(), eigvals_only=True, subset_by_index=[0, 0])[0]
+    bound = (np.linalg.norm(r) + np.linalg.norm(f - A @ u_o)) / lam_min
+    err = np.linalg.norm(u - u_o)
+    assert err <= 1.01 * bound, (err, bound)
+    lib.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_smoothers_match_fp64_to_fp32_rounding(name):
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    mgb = binding()
+    lib = mgb.Solver(prob, levels=levels, smoother="hybrid", precision="fp32", **opt)
+    orc = omg.Multigrid(prob, levels=levels, smoother="hybrid", **opt)
+    rng = np.random.default_rng(9)
+    for l in range(1, levels):
+        A = orc.h["A"][l]
+        n = A.shape[0]
+        u, f = rng.standard_normal(n), rng.standard_normal(n)
+        ref = u + orc.scms[l].apply(f - A @ u)
+        got = lib.apply("smooth", l, f, u)
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref - u), l
+        for op, fn in (("gs_fwd", orc.gs[l].forward), ("gs_bwd", orc.gs[l].backward)):
+            ref = fn(f, u)
+            got = lib.apply(op, l, f, u)
+            assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref - u), (l, op)
+    lib.close()

@@ -70,8 +70,9 @@ enum { MGIGA_OUTER_PCG = 0, MGIGA_OUTER_DIRECT = 1 };
  *   stored in FP32); residuals, transfers, interface pieces, the coarse
  *   Cholesky solve and all CG vectors and inner products stay FP64, and CG
  *   uses the flexible (Polak-Ribiere) beta.
- * MGIGA_PREC_TF32 / MGIGA_PREC_BF16: reserved for tensor-core contractions
- *   (rejected with MGIGA_EINVAL by this build). */
+ * MGIGA_PREC_TF32 / MGIGA_PREC_BF16: as FP32, with the fast-diagonalisation
+ *   contractions on the tensor cores (tcgen05, TF32 or BF16 operands, FP32
+ *   accumulation). */
 enum { MGIGA_PREC_FP64 = 0, MGIGA_PREC_FP32 = 1, MGIGA_PREC_TF32 = 2, MGIGA_PREC_BF16 = 3 };
 
 /* One interface between side_a of patch_a and side_b of patch_b.

@@ -189,10 +189,14 @@ def colouring(problem, knots, num):
 
     Base colour of a DoF, from the copy that numbered it (patch k, local
     multi-index i):  par(k) (p+1)^d + sum_a (i_a mod (p+1)) (p+1)^a.
-    A DoF with a coupled DoF of lower global index and the same base colour
-    is moved: such DoFs are visited in increasing global order and each takes
-    the smallest colour >= 2 (p+1)^d not used by a moved DoF of lower index
-    that couples with it.  Returns the colour of every global DoF.
+    A DoF is moved if it couples with a DoF of lower global index and the
+    same base colour, if it couples with a DoF owned by another patch of the
+    same parity, or if it has copies in several patches (a conforming
+    interface DoF).  Moved DoFs are visited in increasing global order and
+    each takes the smallest colour >= 2 (p+1)^d not used by a moved DoF of
+    lower index that couples with it.  (The last two rules keep the DoFs on
+    base colours inside one patch and patches of one parity uncoupled, so
+    patches can be swept side by side.)  Returns the colour of every DoF.
     """
     d = problem["dim"]
     p = problem["degree"]
@@ -205,9 +209,17 @@ def colouring(problem, knots, num):
             c += (multi[a] % (p + 1)) * (p + 1) ** a
         base[g] = c
     S = structural_pattern(problem, knots, num).tocoo()
+    owner_patch = np.array([k for (k, f) in num["owner"]], dtype=np.int64)
+    par_arr = np.array(par)
     clash = (S.col < S.row) & (base[S.row] == base[S.col])
+    po, qo = owner_patch[S.row], owner_patch[S.col]
+    cross = (po != qo) & (par_arr[po] == par_arr[qo])
     moved = np.zeros(num["ndof"], dtype=bool)
-    moved[S.row[clash]] = True
+    moved[S.row[clash | cross]] = True
+    copies = np.zeros(num["ndof"], dtype=np.int64)
+    for l2g in num["loc2glob"]:
+        np.add.at(copies, l2g[l2g >= 0], 1)
+    moved |= copies > 1
     colour = base.copy()
     first_extra = 2 * (p + 1) ** d
     Scsr = S.tocsr()

@@ -75,7 +75,9 @@ def build(verbose=False, force=False):
     relink = force or bool(jobs) or not os.path.exists(LIB)
     if relink:
         tmp = LIB + ".tmp"
-        _compile([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fopenmp", "-lgomp"])
+        # --no-undefined: a launcher missing from the objects fails the build, not the import
+        _compile([nvcc] + ARCH + ["-shared", "-o", tmp] + objs +
+                 ["-Xcompiler", "-fopenmp", "-lgomp", "-Xlinker", "--no-undefined", "-lpthread", "-ldl", "-lrt"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -420,13 +420,24 @@ std::vector<int> colouring(const Problem& pr, const Level& L) {
       }
     }
   }
+  // moved: a coupled DoF of lower index with the same base colour, a coupled
+  // DoF owned by another patch of the same parity, or copies in several
+  // patches (conforming interface DoFs): DoFs on base colours stay inside one
+  // patch and patches of one parity stay uncoupled, so patches can be swept
+  // side by side
+  std::vector<int> owner_patch(L.ndof);
+  for (int g = 0; g < L.ndof; ++g) owner_patch[g] = L.patch_of[L.owner[g]];
   std::vector<uint8_t> moved(L.ndof, 0);
   std::vector<int> nbr;
   for (int g = 0; g < L.ndof; ++g) {
     nbr.clear();
     structural_neighbours(pr, L, g, copies_of, iface_nb, nbr);
-    for (int h : nbr)
-      if (h < g && base[h] == base[g]) { moved[g] = 1; break; }
+    const int kg = owner_patch[g];
+    if (copies_of[g].size() > 1) { moved[g] = 1; continue; }
+    for (int h : nbr) {
+      const int kh = owner_patch[h];
+      if ((h < g && base[h] == base[g]) || (kh != kg && par[kh] == par[kg])) { moved[g] = 1; break; }
+    }
   }
   std::vector<int> colour = base;
   const int first_extra = 2 * pw;

@@ -13,6 +13,9 @@
 //   dot / cg_*      deterministic reductions and vector updates of PCG (a8)
 #include <cstdio>
 
+#include <cooperative_groups.h>
+#include <cuda_bf16.h>
+
 #include "device.cuh"
 #include "kernels.h"
 
@@ -186,6 +189,27 @@ __global__ void __launch_bounds__(kTile) prolong_band(
 // ---------------------------------------------------------------------------
 constexpr int GBK = 16;
 
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase) {
+  for (long long it = 0; it < (1ll << 21); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+    __nanosleep(32);
+  }
+  return false;
+}
+
+
 __device__ __forceinline__ int64_t gcol(const GemmTask& g, int n) {
   return (int64_t)(n / g.ndiv) * g.nhi + (n % g.ndiv);
 }
@@ -281,6 +305,190 @@ __global__ void __launch_bounds__(256) gemm_tiled(const GemmTask* __restrict__ t
 }
 
 // ---------------------------------------------------------------------------
+// a2 on the 5th-generation tensor cores: one 128 x 64 tile of a GemmTask per
+// CTA (4 warps).  Operands are staged by all threads into shared memory in
+// the K-major, non-swizzled core-matrix layout (8 rows x 16 bytes per core
+// matrix; LBO = 128 B between core matrices along K, SBO = 1024 B between
+// 8-row groups), converted to TF32 (kind::tf32) or BF16 (kind::f16) on the
+// way; one thread issues tcgen05.mma (M = 128, N = 64, K = 32 bytes per
+// instruction) into an FP32 accumulator in tensor memory, a commit to an
+// mbarrier tells when the stage's buffer may be refilled (two buffers), and
+// the epilogue reads the accumulator with tcgen05.ld (warp w: lanes 32w..).
+// Every mbarrier wait is bounded; on expiry the CTA records the error,
+// waits once more (bounded) for its MMAs and frees its tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int UM = 128, UN = 64;   // tile, also the MMA shape
+constexpr int UKB = 128;           // bytes of K per row per stage (4 MMAs of 32 bytes)
+constexpr int kUmmaSmem = 2 * (UM + UN) * UKB;  // dynamic shared memory of gemm_umma
+
+__device__ __forceinline__ uint64_t umma_sdesc(unsigned saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);           // start address
+  d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;      // leading byte offset: next core matrix along K
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;     // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                            // descriptor version (tcgen05)
+  return d;                                          // base offset 0, no swizzle
+}
+
+template <int KIND>
+__device__ __forceinline__ unsigned umma_idesc() {
+  // D = F32; A, B = TF32 (kind::tf32) or BF16 (kind::f16); both K-major;
+  // N >> 3 at bit 17, M >> 4 at bit 24
+  const unsigned ab = KIND == 0 ? 2u : 1u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((unsigned)(UN >> 3) << 17) | ((unsigned)(UM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma_store(unsigned char* tile, int row, int kk, float v) {
+  // element kk of row `row` in the core-matrix layout of one stage
+  constexpr int ES = KIND == 0 ? 4 : 2;
+  const int byte = kk * ES;
+  unsigned char* p = tile + (row >> 3) * 1024 + (byte >> 4) * 128 + (row & 7) * 16 + (byte & 15);
+  if (KIND == 0) *reinterpret_cast<float*>(p) = v;
+  else *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128) gemm_umma(const GemmTask* __restrict__ tasks,
+                                                 const GemmItem* __restrict__ items, int* err) {
+  constexpr int ES = KIND == 0 ? 4 : 2;
+  constexpr int KT = UKB / ES;  // K elements per stage
+  // dynamic shared memory (kUmmaSmem bytes): two A and two B stage buffers
+  extern __shared__ __align__(1024) unsigned char usm[];
+  unsigned char* sA[2] = {usm, usm + UM * UKB};
+  unsigned char* sB[2] = {usm + 2 * UM * UKB, usm + 2 * UM * UKB + UN * UKB};
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ unsigned tmem_slot;
+  const GemmItem it = items[blockIdx.x];
+  const GemmTask g = tasks[it.task];
+  const int64_t oA = it.z * g.sA, oB = it.z * g.sB, oC = it.z * g.sC;
+  const int m0 = it.tm * UM, n0 = it.tn * UN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(UN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_slot;
+  const unsigned idesc = umma_idesc<KIND>();
+  const int nst = (g.K + KT - 1) / KT;
+  bool ok = true;
+  unsigned phase_bits = 0;
+  for (int st = 0; st < nst; ++st) {
+    const int b = st & 1;
+    if (st >= 2) {  // the MMAs that read this buffer two stages ago are done
+      if (ok && !mbar_wait(smem_u32(&mbar[b]), (phase_bits >> b) & 1u)) {
+        ok = false;
+        atomicExch(err, 3);
+      }
+      phase_bits ^= 1u << b;
+    }
+    const int k0 = st * KT;
+    // A: one row per thread; B: half a row per thread
+    {
+      const int m = m0 + tid;
+      for (int kk = 0; kk < KT; ++kk) {
+        const int k = k0 + kk;
+        float v = 0.0f;
+        if (m < g.M && k < g.K)
+          v = ldt<float>(g.A, oA + (g.transA ? (int64_t)k * g.lda + m : (int64_t)m * g.lda + k), g.tA);
+        umma_store<KIND>(sA[b], tid, kk, v);
+      }
+      const int nr = tid >> 1, kh = (tid & 1) * (KT / 2);
+      const int n = n0 + nr;
+      for (int kk = kh; kk < kh + KT / 2; ++kk) {
+        const int k = k0 + kk;
+        float v = 0.0f;
+        if (n < g.N && k < g.K)
+          v = ldt<float>(g.B, oB + (g.transB ? (int64_t)n * g.ldb + k : (int64_t)k * g.ldb + n), g.tB);
+        umma_store<KIND>(sB[b], nr, kk, v);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned a0 = smem_u32(sA[b]), b0 = smem_u32(sB[b]);
+#pragma unroll
+      for (int j = 0; j < UKB / 32; ++j) {
+        const uint64_t ad = umma_sdesc(a0 + 256 * j), bd = umma_sdesc(b0 + 256 * j);
+        const unsigned acc = (st > 0 || j > 0) ? 1u : 0u;
+        if (KIND == 0)
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        else
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar[b]))
+                   : "memory");
+    }
+  }
+  // wait for the last stage's commit (it covers every earlier MMA)
+  if (nst > 0) {
+    const int b = (nst - 1) & 1;
+    if (!mbar_wait(smem_u32(&mbar[b]), (phase_bits >> b) & 1u)) {
+      if (ok) atomicExch(err, 3);
+      ok = false;
+      mbar_wait(smem_u32(&mbar[b]), (phase_bits >> b) & 1u);
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok && nst > 0) {
+    const int m = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < UN; c0 += 16) {
+      unsigned v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < g.M) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int n = n0 + c0 + i;
+          if (n >= g.N) continue;
+          float acc = __uint_as_float(v[i]);
+          const int64_t ci = oC + (int64_t)m * g.ldc + gcol(g, n);
+          if (g.epi == 1) {
+            double den = g.sigma + g.lamM[m] + g.lamN0[n % g.nl0];
+            if (g.lamN1) den += g.lamN1[n / g.nl0];
+            acc = (float)((double)acc / den);
+          }
+          if (g.tC) {
+            float* c = static_cast<float*>(g.C) + ci;
+            *c = g.epi == 2 ? *c + (float)(g.alpha * acc) : acc;
+          } else {
+            double* c = static_cast<double*>(g.C) + ci;
+            *c = g.epi == 2 ? *c + g.alpha * (double)acc : (double)acc;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UN) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // a3 / a7: dense solves with precomputed inverses, z = Z r_T, u_T += tau z
 // (mode 0) or u_T = z (mode 1)
 // ---------------------------------------------------------------------------
@@ -350,83 +558,250 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err) {
   return *((volatile int*)err) == 0;
 }
 
+// One Gauss-Seidel row update for each row group of TPR lanes of a warp:
+// rows base + lane / TPR (those below e1).  Each lane sums a share of the
+// (2p+1)^d stencil and of the SIPG couplings, the group reduces by shuffles
+// and its first lane writes u_i + (f_i - sum_j a_ij u_j) / a_ii.
 // TB: type of the colour-ordered coefficients and of the arithmetic (double
-// for the FP64 path, float for the mixed path); u and f stay FP64.
+// for the FP64 path, float for the mixed path); u and f stay FP64 and are
+// read through L2 (ld.cg): other SMs wrote them since the last barrier.
 template <int D, int P, int TPR, typename TB>
-__global__ void __launch_bounds__(256) gs_sweep_coop(GsSweepArgs a) {
+__device__ __forceinline__ void gs_rows(const GsSweepArgs& a, int64_t base, int64_t e1) {
   constexpr int W = 2 * P + 1;
   constexpr int NOB = D == 2 ? W : W * W;  // offset blocks of W consecutive o0
   constexpr int center = D == 2 ? P * W + P : (P * W + P) * W + P;
   const TB* gsband = static_cast<const TB*>(a.gsband);
   const int lane = threadIdx.x & 31;
-  const int sub = lane % TPR;  // lane within the row group
+  const int sub = lane % TPR;
+  const int64_t e = base + lane / TPR;
+  const bool active = e < e1;
+  TB acc = 0;
+  int64_t pos = 0;
+  double upos = 0.0, fpos = 0.0;
+  TB diag = 1;
+  int cls = -1;
+  if (active) {
+    // independent loads first: position, strides, couplings, diagonal, u_i, f_i
+    pos = a.gs_pos[e];
+    const int2 st = a.gs_stride[e];
+    const int2 xr = a.gs_xrange[e];
+    cls = a.gs_cls[e];
+    diag = __ldg(gsband + (int64_t)center * a.ngs + e);
+    upos = __ldcg(a.u + pos);
+    fpos = __ldcg(a.f + pos);
+    const int64_t s1 = st.x, s2 = st.y;
+    for (int ob = sub; ob < NOB; ob += TPR) {
+      const int o1 = ob % W, o2 = ob / W;
+      const int64_t off = (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
+      const TB* br = gsband + (int64_t)ob * W * a.ngs + e;
+      const double* ur = a.u + pos + off;
+#pragma unroll
+      for (int o0 = 0; o0 < W; ++o0) acc = fma(__ldg(br + (int64_t)o0 * a.ngs), (TB)__ldcg(ur + o0), acc);
+    }
+    // SIPG couplings across interfaces, shared over the row's lanes
+    for (int j = xr.x + sub; j < xr.y; j += TPR) acc = fma((TB)a.x_val[j], (TB)__ldcg(a.u + a.x_col[j]), acc);
+  }
+#pragma unroll
+  for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (active && sub == 0) {
+    if (cls >= 0) {
+      // further copies of a DoF shared by conforming patches (owner first)
+      for (int cp = a.sh_ptr[cls] + 1; cp < a.sh_ptr[cls + 1]; ++cp) {
+        const int64_t q = a.sh_pos[cp];
+        const PatchMeta pm = a.patches[a.sh_patch[cp]];
+        const int64_t s1 = pm.N[0], s2 = (int64_t)pm.N[0] * pm.N[1];
+        for (int ob = 0; ob < NOB; ++ob) {
+          const int o1 = ob % W, o2 = ob / W;
+          const int64_t off = (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
+          for (int o0 = 0; o0 < W; ++o0)
+            acc = fma((TB)a.band[(int64_t)(ob * W + o0) * a.nloc + q], (TB)__ldcg(a.u + q + off + o0), acc);
+        }
+        diag += (TB)a.band[(int64_t)center * a.nloc + q];
+      }
+    }
+    const double unew = upos + (double)(((TB)fpos - acc) / diag);
+    if (cls < 0) {
+      a.u[pos] = unew;
+    } else {
+      for (int cp = a.sh_ptr[cls]; cp < a.sh_ptr[cls + 1]; ++cp) a.u[a.sh_pos[cp]] = unew;
+    }
+  }
+}
+
+// Colours [c_begin, c_end) of a sweep over the whole grid, one cooperative
+// launch, a bounded grid barrier between colours (used for the colours that
+// couple patches of one parity).
+template <int D, int P, int TPR, typename TB>
+__global__ void __launch_bounds__(256) gs_sweep_coop(GsSweepArgs a) {
+  const int lane = threadIdx.x & 31;
   const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t rows_per_warp = 32 / TPR;
   const int64_t rows_per_grid = ((int64_t)gridDim.x * blockDim.x) / TPR;
-  for (int ci = 0; ci < a.ncol; ++ci) {
-    const int c = a.forward ? ci : a.ncol - 1 - ci;
+  (void)lane;
+  const int nc = a.c_end - a.c_begin;
+  for (int ci = 0; ci < nc; ++ci) {
+    const int c = a.forward ? a.c_begin + ci : a.c_end - 1 - ci;
     const int e0 = a.cptr[c], e1 = a.cptr[c + 1];
-    for (int64_t base = e0 + warp_global * rows_per_warp; base < e1; base += rows_per_grid) {
-      const int64_t e = base + lane / TPR;
-      const bool active = e < e1;
-      TB acc = 0;
-      int64_t pos = 0;
-      double upos = 0.0, fpos = 0.0;
-      TB diag = 1;
-      int cls = -1;
-      if (active) {
-        // independent loads first: position, strides, couplings, diagonal, u_i, f_i
-        pos = a.gs_pos[e];
-        const int2 st = a.gs_stride[e];
-        const int2 xr = a.gs_xrange[e];
-        cls = a.gs_cls[e];
-        diag = __ldg(gsband + (int64_t)center * a.ngs + e);
-        upos = __ldcg(a.u + pos);
-        fpos = __ldcg(a.f + pos);
-        const int64_t s1 = st.x, s2 = st.y;
-        for (int ob = sub; ob < NOB; ob += TPR) {
-          const int o1 = ob % W, o2 = ob / W;
-          const int64_t off = (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
-          const TB* br = gsband + (int64_t)ob * W * a.ngs + e;
-          const double* ur = a.u + pos + off;
-#pragma unroll
-          for (int o0 = 0; o0 < W; ++o0) acc = fma(__ldg(br + (int64_t)o0 * a.ngs), (TB)__ldcg(ur + o0), acc);
-        }
-        // SIPG couplings across interfaces, shared over the row's lanes
-        for (int j = xr.x + sub; j < xr.y; j += TPR) acc = fma((TB)a.x_val[j], (TB)__ldcg(a.u + a.x_col[j]), acc);
-      }
-#pragma unroll
-      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (active && sub == 0) {
-        if (cls >= 0) {
-          // further copies of a DoF shared by conforming patches (owner first)
-          for (int cp = a.sh_ptr[cls] + 1; cp < a.sh_ptr[cls + 1]; ++cp) {
-            const int64_t q = a.sh_pos[cp];
-            const PatchMeta pm = a.patches[a.sh_patch[cp]];
-            const int64_t s1 = pm.N[0], s2 = (int64_t)pm.N[0] * pm.N[1];
-            for (int ob = 0; ob < NOB; ++ob) {
-              const int o1 = ob % W, o2 = ob / W;
-              const int64_t off = (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
-              for (int o0 = 0; o0 < W; ++o0)
-                acc = fma((TB)a.band[(int64_t)(ob * W + o0) * a.nloc + q], (TB)__ldcg(a.u + q + off + o0), acc);
-            }
-            diag += (TB)a.band[(int64_t)center * a.nloc + q];
-          }
-        }
-        const double unew = upos + (double)(((TB)fpos - acc) / diag);
-        if (cls < 0) {
-          a.u[pos] = unew;
-        } else {
-          for (int cp = a.sh_ptr[cls]; cp < a.sh_ptr[cls + 1]; ++cp) a.u[a.sh_pos[cp]] = unew;
-        }
-      }
-    }
+    for (int64_t base = e0 + warp_global * rows_per_warp; base < e1; base += rows_per_grid)
+      gs_rows<D, P, TPR, TB>(a, base, e1);
     if (gridDim.x == 1) {
       __syncthreads();  // one block: its own writes are visible after the barrier
     } else if (!grid_barrier(a.bar, a.err)) {
       return;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Base colours of one patch parity, mixed path (FP32 arithmetic): the
+// patch's u lives in shared memory (a slab per CTA of the patch's cluster,
+// neighbouring slabs read through distributed shared memory); for every
+// colour the CTA's rows come as one contiguous block -- FP32 coefficients
+// [o][row], the row's index in the slab, its slot of couplings to the other
+// parity, and f -- copied into shared memory by a bulk asynchronous copy one
+// colour ahead (double buffer, mbarrier completion).  Couplings to patches of
+// the other parity (SIPG flux/penalty terms, further copies of conforming
+// shared DoFs) do not change during the phase and are summed once per slot at
+// its start.  Colours are separated by the hardware cluster barrier.
+// Every wait on an mbarrier is bounded: on expiry the CTA records the error,
+// stops computing and keeps taking part in the cluster barriers.
+// ---------------------------------------------------------------------------
+template <int D, int P, int TPR>
+__global__ void __launch_bounds__(256) gs_patch_staged(GsStagedArgs a) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int W = 2 * P + 1;
+  constexpr int NOB = D == 2 ? W : W * W;
+  constexpr int NB = NOB * W;
+  constexpr int center = D == 2 ? P * W + P : (P * W + P) * W + P;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cs = a.csize;
+  const int q = blockIdx.x / cs;
+  const int r = (int)cluster.block_rank();
+  const int k = a.phase_patches[q];
+  const int S = a.slab[k];
+  const PatchMeta pm = a.patches[k];
+  const int64_t N0 = pm.N[0];
+  const int64_t plane = D == 2 ? N0 : N0 * pm.N[1];
+  const int nslow = D == 2 ? pm.N[1] : pm.N[2];
+  const int64_t cap = (int64_t)S * plane;
+  const int s_lo = r * S, s_hi = min(nslow, (r + 1) * S);
+  double* uslab = reinterpret_cast<double*>(smem);
+  float* xsum = reinterpret_cast<float*>(smem + a.off_xsum);
+  unsigned char* const buf0 = smem + a.off_buf;  // buffer b at buf0 + b * buf_bytes
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + a.off_mbar);
+  const int tid = threadIdx.x;
+  const int slab_id = k * cs + r;
+  const int nslot = a.slot_ptr[slab_id + 1] - a.slot_ptr[slab_id];
+  const int* slot_e = a.slot_entry + a.slot_ptr[slab_id];
+  const int nc = a.c_end - a.c_begin;
+  auto group_of = [&](int ci) {
+    const int c = a.forward ? a.c_begin + ci : a.c_end - 1 - ci;
+    return ((int64_t)c * a.K + k) * cs + r;
+  };
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int ci, int b) {  // thread 0: bulk copy of colour ci's block into buffer b
+    const int64_t g = group_of(ci);
+    const unsigned bytes = (unsigned)a.blk_bytes[g];
+    const unsigned bar = smem_u32(&mbar[b]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    if (bytes > 0)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(buf0 + (size_t)b * a.buf_bytes)),
+          "l"(a.pool + a.blk_off[g]), "r"(bytes), "r"(bar)
+          : "memory");
+  };
+  if (tid == 0 && nc > 0) issue(0, 0);
+  // u slab and the couplings to the other parity (fixed during the phase)
+  for (int64_t i = tid; i < (int64_t)(s_hi - s_lo) * plane; i += blockDim.x)
+    uslab[i] = __ldcg(a.u + pm.off + (int64_t)s_lo * plane + i);
+  for (int t = tid; t < nslot; t += blockDim.x) {
+    const int e = slot_e[t];
+    double v = 0.0;
+    const int2 xr = a.gs_xrange[e];
+    for (int j = xr.x; j < xr.y; ++j) v += a.x_val[j] * __ldcg(a.u + a.x_col[j]);
+    xsum[t] = (float)v;
+  }
+  cluster.sync();
+  const int lane = tid & 31;
+  const int sub = lane % TPR;
+  const int warp = tid >> 5;
+  const int rows_per_warp = 32 / TPR;
+  const int rows_per_cta = blockDim.x / TPR;
+  bool ok = true;
+  unsigned phase_bits = 0;
+  for (int ci = 0; ci < nc; ++ci) {
+    const int b = ci & 1;
+    if (ok && !mbar_wait(smem_u32(&mbar[b]), (phase_bits >> b) & 1u)) {
+      ok = false;
+      atomicExch(a.err, 2);
+    }
+    phase_bits ^= 1u << b;
+    // the other buffer was released by the barrier that ended colour ci - 1
+    if (tid == 0 && ok && ci + 1 < nc) issue(ci + 1, b ^ 1);
+    const int64_t g = group_of(ci);
+    const int R = a.blk_rows[g];
+    const int Rp = (R + 3) & ~3;
+    const float* coef = reinterpret_cast<const float*>(buf0 + (size_t)b * a.buf_bytes);
+    const int* lidx = reinterpret_cast<const int*>(coef + (int64_t)NB * Rp);
+    const int* slot = lidx + Rp;
+    const float* fval = reinterpret_cast<const float*>(slot + Rp);
+    if (ok) {
+      for (int base = warp * rows_per_warp; base < R; base += rows_per_cta) {
+        const int row = base + lane / TPR;
+        const bool active = row < R;
+        float acc = 0.0f;
+        int li = 0;
+        if (active) {
+          li = lidx[row];  // index in this CTA's slab
+          const int s = s_lo + (int)(li / plane);
+          const int64_t rest = li - (int64_t)(s - s_lo) * plane;
+          for (int ob = sub; ob < NOB; ob += TPR) {
+            const int o1 = ob % W, o2 = ob / W;
+            const int sp = s + (D == 2 ? o1 : o2) - P;
+            if (sp < 0 || sp >= nslow) continue;  // zero coefficients
+            const int rp = sp / S;
+            const double* src = rp == r ? uslab : cluster.map_shared_rank(uslab, rp);
+            const int64_t idx0 = (int64_t)(sp - rp * S) * plane + rest + (D == 3 ? (int64_t)(o1 - P) * N0 : 0) - P;
+            const float* cr = coef + (int64_t)ob * W * Rp + row;
+#pragma unroll
+            for (int o0 = 0; o0 < W; ++o0) {
+              int64_t idx = idx0 + o0;
+              idx = idx < 0 ? 0 : (idx >= cap ? cap - 1 : idx);  // off-patch columns carry zero coefficients
+              acc = fmaf(cr[(int64_t)o0 * Rp], (float)src[idx], acc);
+            }
+          }
+        }
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (active && sub == 0) {
+          const int sl = slot[row];
+          if (sl >= 0) acc += xsum[sl];
+          const float diag = coef[(int64_t)center * Rp + row];
+          uslab[li] += (double)((fval[row] - acc) / diag);
+        }
+      }
+    }
+    cluster.sync();
+  }
+  // the slab back to global memory
+  for (int64_t i = tid; i < (int64_t)(s_hi - s_lo) * plane; i += blockDim.x)
+    a.u[pm.off + (int64_t)s_lo * plane + i] = uslab[i];
+}
+
+// f of every base-colour entry into its block (before a sweep)
+__global__ void gs_fill_f(int n, const int64_t* __restrict__ f_off, const int64_t* __restrict__ gs_pos,
+                          const double* __restrict__ f, unsigned char* pool) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int64_t o = f_off[e];
+  if (o >= 0) *reinterpret_cast<float*>(pool + o) = (float)f[gs_pos[e]];
 }
 
 // ---------------------------------------------------------------------------
@@ -592,6 +967,19 @@ void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const
 
 int gemm_tile(int arith) { return arith == 1 ? 64 : 32; }
 
+void launch_gemm_umma(int nitems, int kind, cudaStream_t st, const GemmTask* tasks, const GemmItem* items, int* err) {
+  if (nitems == 0) return;
+  ++g_launches;
+  if (kind == 0) gemm_umma<0><<<nitems, 128, kUmmaSmem, st>>>(tasks, items, err);
+  else gemm_umma<1><<<nitems, 128, kUmmaSmem, st>>>(tasks, items, err);
+}
+
+cudaError_t prepare_gemm_umma() {
+  cudaError_t e = cudaFuncSetAttribute(gemm_umma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(gemm_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+}
+
 void launch_gemm(int nitems, int arith, cudaStream_t st, const GemmTask* tasks, const GemmItem* items) {
   if (nitems == 0) return;
   ++g_launches;
@@ -627,6 +1015,79 @@ cudaError_t launch_gs_sweep(int d, int p, bool f32, int blocks, cudaStream_t st,
   ++g_launches;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(gs_coop_ptr(d, p, f32), dim3(blocks), dim3(256), args, 0, st);
+}
+
+constexpr int kStagedSmemMax = 225 * 1024;
+
+template <int D, int P>
+static void* gs_staged_func() {
+  return (void*)gs_patch_staged<D, P, 4>;
+}
+
+static void* gs_staged_ptr(int d, int p) {
+  switch (p) {
+#define MG_CASE(PP) \
+  case PP: return d == 2 ? gs_staged_func<2, PP>() : gs_staged_func<3, PP>();
+    MG_CASE(1) MG_CASE(2) MG_CASE(3) MG_CASE(4) MG_CASE(5) MG_CASE(6) MG_CASE(7) MG_CASE(8)
+#undef MG_CASE
+    default: return nullptr;
+  }
+}
+
+bool gs_staged_fits(int d, int p, int csize, int smem) {
+  void* fn = gs_staged_ptr(d, p);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+  // the attribute belongs to the kernel, not to a launch: always allow the
+  // largest amount any level may ask for (kStagedSmemMax)
+  if (smem > kStagedSmemMax ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = csize;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return nclusters > 0;
+}
+
+cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t st, const GsStagedArgs& a) {
+  if (nclusters <= 0) return cudaSuccess;
+  ++g_launches;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nclusters * a.csize);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = a.csize;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  GsStagedArgs arg = a;
+  void* args[] = {&arg};
+  return cudaLaunchKernelExC(&cfg, gs_staged_ptr(d, p), args);
+}
+
+void launch_gs_fill_f(int n, cudaStream_t st, const int64_t* f_off, const int64_t* gs_pos, const double* f,
+                      unsigned char* pool) {
+  if (n <= 0) return;
+  ++g_launches;
+  gs_fill_f<<<(n + 255) / 256, 256, 0, st>>>(n, f_off, gs_pos, f, pool);
 }
 
 void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,

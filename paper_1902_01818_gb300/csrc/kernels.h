@@ -12,7 +12,7 @@ namespace dev {
 
 // arguments of the cooperative Gauss-Seidel sweep (all colours, one launch)
 struct GsSweepArgs {
-  int ncol, forward;
+  int c_begin, c_end, forward;  // colours [c_begin, c_end), ascending if forward
   const int* cptr;        // ncol + 1 entry offsets (device)
   int64_t ngs;            // number of entries (= ndof)
   const void* gsband;     // band rows of the owner copies in colour order, gsband[o * ngs + e]
@@ -36,6 +36,30 @@ struct GsSweepArgs {
 };
 int gs_coop_max_blocks(int d, int p, bool f32);
 cudaError_t launch_gs_sweep(int d, int p, bool f32, int blocks, cudaStream_t st, GsSweepArgs a);
+// staged patch-parallel phase of the mixed path (FP32 coefficient blocks)
+struct GsStagedArgs {
+  int c_begin, c_end, forward;  // base colours of the phase
+  int K, csize;                 // patches, CTAs per patch cluster
+  const int* phase_patches;     // cluster q sweeps patch phase_patches[q]
+  const int* slab;              // slab height (slow indices) per patch
+  const unsigned char* pool;    // colour blocks, 16-byte aligned
+  const int64_t* blk_off;       // block of group (c K + k) csize + r: byte offset
+  const int* blk_bytes;         //   its size in bytes (multiple of 16)
+  const int* blk_rows;          //   its number of rows
+  const int* slot_ptr;          // slots of slab (k csize + r): [slot_ptr[i], slot_ptr[i+1])
+  const int* slot_entry;        //   gs entry of each slot
+  int off_xsum, off_buf, buf_bytes, off_mbar;  // shared-memory layout
+  const PatchMeta* patches;
+  const int2* gs_xrange;
+  const int64_t* x_col;
+  const double* x_val;
+  double* u;
+  int* err;
+};
+bool gs_staged_fits(int d, int p, int csize, int smem);
+cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t st, const GsStagedArgs& a);
+void launch_gs_fill_f(int n, cudaStream_t st, const int64_t* f_off, const int64_t* gs_pos, const double* f,
+                      unsigned char* pool);
 
 void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
                  const double* band, int64_t nloc, const double* u, const double* f, double* out);
@@ -52,6 +76,9 @@ void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const
 // arith 0: FP64 arithmetic (32 x 32 tiles), 1: FP32 arithmetic (64 x 64 tiles)
 int gemm_tile(int arith);
 void launch_gemm(int nitems, int arith, cudaStream_t st, const GemmTask* tasks, const GemmItem* items);
+// tensor-core tiles (128 x 64, items built with these tile sizes): kind 0 TF32, 1 BF16
+void launch_gemm_umma(int nitems, int kind, cudaStream_t st, const GemmTask* tasks, const GemmItem* items, int* err);
+cudaError_t prepare_gemm_umma();
 void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,
                   const double* zpool, const int64_t* piece_pos, const double* r, double* u, double tau, int mode);
 cudaError_t prepare_piece_kernel(int max_n);

@@ -2,6 +2,8 @@
 // declared in include/mgiga.h.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -117,9 +119,20 @@ struct DLevel {
   int* gs_cptr_d = nullptr;
   int gs_blocks = 0;
   std::vector<int> gs_cptr;
-  int arith = 0;              // FD and Gauss-Seidel arithmetic: 0 FP64, 1 FP32
+  int arith = 0;              // smoother arithmetic: 0 FP64, 1 FP32, 2 FP32 + TF32 tensor-core FD,
+                              // 3 FP32 + BF16 tensor-core FD
   int2* gs_stride = nullptr;
   int2* gs_xrange = nullptr;
+  // mixed path: base colours of each patch parity swept patch-parallel
+  // (staged colour blocks, see gs_patch_staged)
+  int gs_base = 0;                 // (p+1)^d base colours per parity
+  int gs_csize = 0;                // CTAs per patch cluster (0: grid-wide sweep only)
+  int gs_smem = 0;                 // shared memory per CTA of the patch phase
+  int* gs_phase_patches[2] = {nullptr, nullptr};
+  int gs_nphase[2] = {0, 0};
+  GsStagedArgs gs_staged{};        // everything but colours, direction, u
+  unsigned char* gs_pool = nullptr;
+  int64_t* gs_foff = nullptr;      // byte offset of each entry's f in the pool (-1: none)
 };
 
 }  // namespace
@@ -272,7 +285,7 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   }
   // FP64 path: U and the temporaries in double; FP32 path: in float (the
   // input r and the updated u stay double, converted on load / store)
-  const bool f32 = dl.arith == 1;
+  const bool f32 = dl.arith >= 1;
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
   char* dU;
   if (f32) {
@@ -293,8 +306,9 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     for (const auto& g : st) {
       const int id = (int)tasks.size();
       tasks.push_back(g);
-      const int bm = gemm_tile(dl.arith);
-      const int tm = (g.M + bm - 1) / bm, tn = (g.N + bm - 1) / bm;
+      const int bm = dl.arith >= 2 ? 128 : gemm_tile(dl.arith);  // tensor-core tiles are 128 x 64
+      const int bn = dl.arith >= 2 ? 64 : bm;
+      const int tm = (g.M + bm - 1) / bm, tn = (g.N + bn - 1) / bn;
       for (int z = 0; z < g.batch; ++z)
         for (int a = 0; a < tm; ++a)
           for (int b = 0; b < tn; ++b) items.push_back({id, z, a, b});
@@ -418,7 +432,163 @@ void build_pieces(const std::vector<Piece>& pcs, const Level& L, Arena& A, DLeve
   if (maxn > 0) CK(prepare_piece_kernel(maxn));
 }
 
-void build_gs(const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl) {
+// Colour blocks of the staged patch-parallel sweep (mixed path).  A group is
+// (base colour c, patch k, slab r of the patch's cluster); its block holds
+// float coef[o][Rp], int lidx[Rp], int slot[Rp], float f[Rp] (Rp = rows
+// rounded up to 4) and is copied into shared memory in one piece.
+void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl,
+                     const std::vector<int>& order, const std::vector<int64_t>& gpos, const std::vector<int>& gpatch,
+                     const std::vector<int>& gx, int ncol, int B) {
+  const int K = L.K, d = L.d, nb = L.nb;
+  const int nbase = std::min(ncol, 2 * B);
+  const int nent = nbase > 0 ? dl.gs_cptr[nbase] : 0;
+  auto plane_of = [&](int k) { return d == 2 ? (int64_t)L.N[k][0] : (int64_t)L.N[k][0] * L.N[k][1]; };
+  auto nslow_of = [&](int k) { return L.N[k][d - 1]; };
+  std::vector<int> cls_of(L.ndof, -1);
+  for (size_t c = 0; c + 1 < L.sh_ptr.size(); ++c) cls_of[L.loc2glob[L.sh_pos[L.sh_ptr[c]]]] = (int)c;
+  for (int e = 0; e < nent; ++e)
+    if (cls_of[order[e]] >= 0) throw SetupError(MGIGA_EINVAL, "shared DoF on a base colour");
+  auto has_slot = [&](int e) { return gx[e] >= 0; };
+  // rows per group and slots per slab for a cluster size
+  struct Plan { int cs; std::vector<int> slab; std::vector<int> grp_of; int64_t max_block; int max_slots; int64_t max_cap; };
+  auto plan_for = [&](int cs) {
+    Plan pl;
+    pl.cs = cs;
+    pl.slab.resize(K);
+    pl.max_cap = 0;
+    for (int k = 0; k < K; ++k) {
+      pl.slab[k] = (nslow_of(k) + cs - 1) / cs;
+      pl.max_cap = std::max<int64_t>(pl.max_cap, (int64_t)pl.slab[k] * plane_of(k));
+    }
+    pl.grp_of.assign(nent, 0);
+    std::vector<int> rows((size_t)nbase * K * cs, 0), slots((size_t)K * cs, 0);
+    for (int e = 0; e < nent; ++e) {
+      const int c = colour[order[e]], k = gpatch[e];
+      const int r = (int)((gpos[e] - L.off[k]) / plane_of(k)) / pl.slab[k];
+      const int g = (c * K + k) * cs + r;
+      pl.grp_of[e] = g;
+      rows[g]++;
+      if (has_slot(e)) slots[k * cs + r]++;
+    }
+    pl.max_block = 0;
+    for (int v : rows) pl.max_block = std::max<int64_t>(pl.max_block, (int64_t)(nb + 3) * ((v + 3) & ~3) * 4);
+    pl.max_slots = 0;
+    for (int v : slots) pl.max_slots = std::max(pl.max_slots, v);
+    return pl;
+  };
+  auto smem_of = [&](const Plan& pl, int& off_xsum, int& off_buf, int& off_mbar) {
+    int64_t o = pl.max_cap * 8;
+    o = (o + 15) / 16 * 16;
+    off_xsum = (int)o;
+    o += (int64_t)std::max(pl.max_slots, 1) * 4;
+    o = (o + 127) / 128 * 128;
+    off_buf = (int)o;
+    o += 2 * pl.max_block;
+    o = (o + 15) / 16 * 16;
+    off_mbar = (int)o;
+    o += 16;
+    return o;
+  };
+  int maxrows_pk = 1;
+  {
+    std::vector<int> cnt((size_t)nbase * K, 0);
+    for (int e = 0; e < nent; ++e) cnt[(size_t)colour[order[e]] * K + gpatch[e]]++;
+    for (int v : cnt) maxrows_pk = std::max(maxrows_pk, v);
+  }
+  int want = 1;
+  while (want < 16 && want * 64 * 2 < maxrows_pk) want *= 2;
+  dl.gs_csize = 0;
+  Plan chosen;
+  int off_xsum = 0, off_buf = 0, off_mbar = 0;
+  for (int cs = want; cs <= 16 && nent > 0; cs *= 2) {
+    Plan pl = plan_for(cs);
+    int ox, ob, om;
+    const int64_t smem = smem_of(pl, ox, ob, om);
+    if (smem > 225 * 1024) continue;
+    if (!gs_staged_fits(d, L.p, cs, (int)smem)) continue;
+    chosen = pl;
+    dl.gs_csize = cs;
+    dl.gs_smem = (int)smem;
+    off_xsum = ox; off_buf = ob; off_mbar = om;
+    break;
+  }
+  if (dl.gs_csize == 0) return;  // the grid-wide sweep handles every colour
+  const int cs = dl.gs_csize;
+  // slots per slab
+  std::vector<int> slot_ptr((size_t)K * cs + 1, 0), slot_id(nent, -1);
+  for (int e = 0; e < nent; ++e)
+    if (has_slot(e)) slot_ptr[chosen.grp_of[e] % (K * cs) + 1]++;
+  // grp_of % (K cs) is (k cs + r) because g = (c K + k) cs + r
+  for (size_t i = 1; i < slot_ptr.size(); ++i) slot_ptr[i] += slot_ptr[i - 1];
+  std::vector<int> slot_entry(slot_ptr.back());
+  {
+    std::vector<int> fill(slot_ptr.begin(), slot_ptr.end() - 1);
+    for (int e = 0; e < nent; ++e)
+      if (has_slot(e)) {
+        const int sid = chosen.grp_of[e] % (K * cs);
+        slot_id[e] = fill[sid] - slot_ptr[sid];
+        slot_entry[fill[sid]++] = e;
+      }
+  }
+  // blocks
+  const int ngrp = nbase * K * cs;
+  std::vector<std::vector<int>> members(ngrp);
+  for (int e = 0; e < nent; ++e) members[chosen.grp_of[e]].push_back(e);
+  std::vector<int64_t> blk_off(ngrp);
+  std::vector<int> blk_bytes(ngrp), blk_rows(ngrp);
+  int64_t total = 0;
+  for (int g = 0; g < ngrp; ++g) {
+    const int R = (int)members[g].size(), Rp = (R + 3) & ~3;
+    blk_off[g] = total;
+    blk_rows[g] = R;
+    blk_bytes[g] = R > 0 ? (nb + 3) * Rp * 4 : 0;
+    total += blk_bytes[g];
+  }
+  std::vector<unsigned char> pool((size_t)std::max<int64_t>(total, 16), 0);
+  std::vector<int64_t> foff(L.ndof, -1);
+  for (int g = 0; g < ngrp; ++g) {
+    const int R = blk_rows[g], Rp = (R + 3) & ~3;
+    if (R == 0) continue;
+    float* coef = reinterpret_cast<float*>(pool.data() + blk_off[g]);
+    int* lidx = reinterpret_cast<int*>(coef + (size_t)nb * Rp);
+    int* slot = lidx + Rp;
+    const int k = (g / cs) % K, r = g % cs;
+    for (int row = 0; row < R; ++row) {
+      const int e = members[g][row];
+      const int64_t pos = gpos[e];
+      for (int o = 0; o < nb; ++o) coef[(size_t)o * Rp + row] = (float)L.band[(size_t)o * L.nloc + pos];
+      lidx[row] = (int)(pos - L.off[k] - (int64_t)r * chosen.slab[k] * plane_of(k));
+      slot[row] = slot_id[e];
+      foff[e] = blk_off[g] + ((int64_t)nb + 2) * Rp * 4 + (int64_t)row * 4;
+    }
+  }
+  dl.gs_pool = A.upload(pool);
+  dl.gs_foff = A.upload(foff);
+  for (int ph = 0; ph < 2; ++ph) {
+    std::vector<int> pl;
+    const auto par = patch_parity(pr);
+    for (int k = 0; k < K; ++k)
+      if (par[k] == ph) pl.push_back(k);
+    dl.gs_nphase[ph] = (int)pl.size();
+    dl.gs_phase_patches[ph] = A.upload(pl);
+  }
+  GsStagedArgs& a = dl.gs_staged;
+  a.K = K;
+  a.csize = cs;
+  a.slab = A.upload(chosen.slab);
+  a.pool = dl.gs_pool;
+  a.blk_off = A.upload(blk_off);
+  a.blk_bytes = A.upload(blk_bytes);
+  a.blk_rows = A.upload(blk_rows);
+  a.slot_ptr = A.upload(slot_ptr);
+  a.slot_entry = A.upload(slot_entry);
+  a.off_xsum = off_xsum;
+  a.off_buf = off_buf;
+  a.buf_bytes = (int)chosen.max_block;
+  a.off_mbar = off_mbar;
+}
+
+void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl) {
   const int n = L.ndof;
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -431,7 +601,7 @@ void build_gs(const std::vector<int>& colour, const Level& L, Arena& A, DLevel& 
   std::unordered_map<int64_t, int> xrow;
   for (size_t i = 0; i < L.x_row.size(); ++i) xrow[L.x_row[i]] = (int)i;
   dl.gs_cptr.assign(1, 0);
-  int cur = order.empty() ? 0 : colour[order[0]];
+  int cur = 0;  // cptr index = colour
   for (int e = 0; e < n; ++e) {
     const int g = order[e];
     while (colour[g] != cur) { dl.gs_cptr.push_back(e); ++cur; }
@@ -445,7 +615,7 @@ void build_gs(const std::vector<int>& colour, const Level& L, Arena& A, DLevel& 
   dl.gs_cptr.push_back(n);
   // band rows of the owner copies in colour order (coalesced per colour),
   // in double (FP64 path) or float (mixed path)
-  const bool f32 = dl.arith == 1;
+  const bool f32 = dl.arith >= 1;
   if (f32) {
     std::vector<float> gb((size_t)L.nb * n);
     for (int o = 0; o < L.nb; ++o)
@@ -466,11 +636,19 @@ void build_gs(const std::vector<int>& colour, const Level& L, Arena& A, DLevel& 
   dl.gs_stride = A.upload(gst);
   dl.gs_xrange = A.upload(gxr);
   dl.gs_cptr_d = A.upload(dl.gs_cptr);
+  const int ncol = (int)dl.gs_cptr.size() - 1;
+  int B = 1;
+  for (int a = 0; a < L.d; ++a) B *= L.p + 1;
+  dl.gs_base = B;
+  if (f32) build_gs_staged(pr, colour, L, A, dl, order, gpos, gpatch, gx, ncol, B);
   int maxrows = 1;
   for (size_t c = 0; c + 1 < dl.gs_cptr.size(); ++c) maxrows = std::max(maxrows, dl.gs_cptr[c + 1] - dl.gs_cptr[c]);
   const int coop = gs_coop_max_blocks(L.d, L.p, f32);
   if (coop <= 0) throw CudaError("cooperative launch not available for the Gauss-Seidel sweep");
   dl.gs_blocks = std::max(1, std::min(coop, (maxrows * 8 + 255) / 256));
+  if (std::getenv("MGIGA_VERBOSE"))
+    std::fprintf(stderr, "mgiga: gs level ndof %d colours %d base %d cluster %d smem %d grid-blocks %d\n", n, ncol,
+                 B, dl.gs_csize, dl.gs_smem, dl.gs_blocks);
   dl.gs_pos = A.upload(gpos);
   dl.gs_patch = A.upload(gpatch);
   dl.gs_cls = A.upload(gcls);
@@ -498,21 +676,33 @@ void matvec(mgiga_handle* h, int l, const double* u, double* out) {
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, out, nullptr, 1);
 }
 
+// one step of the fast diagonalisation: SIMT tiles (FP64 / FP32) or tensor-core tiles (TF32 / BF16)
+void run_fd_step(mgiga_handle* h, DLevel& d, const std::pair<int, int>& s) {
+  if (d.arith >= 2)
+    launch_gemm_umma(s.second - s.first, d.arith - 2, h->stream, d.fd_tasks, d.fd_items + s.first, h->gs_err);
+  else
+    launch_gemm(s.second - s.first, d.arith, h->stream, d.fd_tasks, d.fd_items + s.first);
+}
+
 // u += tau sum_T P_T L_T^{-1} P_T^T r  (Eq. Ldef), r in d.r
 void smooth(mgiga_handle* h, int l) {
   DLevel& d = h->D[l];
   for (const auto& s : d.fd_steps)
-    launch_gemm(s.second - s.first, d.arith, h->stream, d.fd_tasks, d.fd_items + s.first);
+    run_fd_step(h, d, s);
   launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r, d.u,
                h->opt.tau, 0);
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, d.u, nullptr, 2);
 }
 
+// one Gauss-Seidel sweep: the base colours of each patch parity patch-parallel
+// (one launch per parity, a cluster per patch), then the remaining colours
+// (DoFs coupling patches of one parity) grid-wide; reversed for the backward sweep
 void gs_sweep(mgiga_handle* h, int l, bool forward) {
   const Level& L = h->L[l];
   DLevel& d = h->D[l];
   GsSweepArgs a;
-  a.ncol = (int)d.gs_cptr.size() - 1;
+  const int ncol = (int)d.gs_cptr.size() - 1;
+  if (ncol <= 0) return;
   a.forward = forward ? 1 : 0;
   a.cptr = d.gs_cptr_d;
   a.ngs = d.ndof;
@@ -523,9 +713,35 @@ void gs_sweep(mgiga_handle* h, int l, bool forward) {
   a.x_col = d.x_col; a.x_val = d.x_val; a.f = d.f; a.u = d.u;
   a.bar = h->gs_bar;
   a.err = h->gs_err;
-  if (a.ncol <= 0) return;
-  CK(cudaMemsetAsync(h->gs_bar, 0, 2 * sizeof(unsigned int), h->stream));
-  CK(launch_gs_sweep(L.d, L.p, d.arith == 1, d.gs_blocks, h->stream, a));
+  const bool f32 = d.arith >= 1;
+  const int B = d.gs_base;
+  auto coop = [&](int cb, int ce) {
+    a.c_begin = std::min(cb, ncol);
+    a.c_end = std::min(ce, ncol);
+    if (a.c_end <= a.c_begin) return;
+    CK(cudaMemsetAsync(h->gs_bar, 0, 2 * sizeof(unsigned int), h->stream));
+    CK(launch_gs_sweep(L.d, L.p, f32, d.gs_blocks, h->stream, a));
+  };
+  auto phase = [&](int ph) {
+    if (d.gs_csize == 0) {  // no staged plan (FP64 path, or slabs too large): grid-wide sweep
+      coop(ph * B, (ph + 1) * B);
+      return;
+    }
+    GsStagedArgs g = d.gs_staged;
+    g.c_begin = std::min(ph * B, ncol);
+    g.c_end = std::min((ph + 1) * B, ncol);
+    if (g.c_end <= g.c_begin) return;
+    g.forward = forward ? 1 : 0;
+    g.phase_patches = d.gs_phase_patches[ph];
+    g.patches = d.patches; g.gs_xrange = d.gs_xrange;
+    g.x_col = d.x_col; g.x_val = d.x_val; g.u = d.u; g.err = h->gs_err;
+    CK(launch_gs_staged(L.d, L.p, d.gs_nphase[ph], d.gs_smem, h->stream, g));
+  };
+  auto tail = [&]() { coop(2 * B, ncol); };
+  if (d.gs_csize > 0)  // f of the base-colour entries into their blocks
+    launch_gs_fill_f(d.gs_cptr[std::min(ncol, 2 * B)], h->stream, d.gs_foff, d.gs_pos, d.f, d.gs_pool);
+  if (forward) { phase(0); phase(1); tail(); }
+  else { tail(); phase(1); phase(0); }
 }
 
 // f_{l-1} = P^T r_l (r_l consistent; weights make each shared DoF count once)
@@ -743,8 +959,8 @@ mgiga_status mgiga_create(const mgiga_problem* problem, const mgiga_options* opt
     if (opts) h->opt = *opts; else mgiga_default_options(&h->opt);
     const mgiga_options& o = h->opt;
     if (o.smoother < 0 || o.smoother > 2 || o.nu < 1 || o.mu < 1 || o.mu > 2 || o.outer < 0 || o.outer > 1 ||
-        (o.precision != MGIGA_PREC_FP64 && o.precision != MGIGA_PREC_FP32) || o.max_iter < 0 || !(o.tau > 0.0) || !(o.delta > 0.0) || o.levels < 0)
-      throw SetupError(MGIGA_EINVAL, "invalid options (precision: MGIGA_PREC_FP64 or MGIGA_PREC_FP32)");
+        o.precision < MGIGA_PREC_FP64 || o.precision > MGIGA_PREC_BF16 || o.max_iter < 0 || !(o.tau > 0.0) || !(o.delta > 0.0) || o.levels < 0)
+      throw SetupError(MGIGA_EINVAL, "invalid options");
     h->stream = static_cast<cudaStream_t>(o.stream);
     const int lv = o.levels > 0 ? o.levels : auto_levels(h->pr);
     h->levels = lv;
@@ -799,6 +1015,7 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
     }
     h->arena.reset(new Arena());
     Arena& A = *h->arena;
+    if (h->opt.precision == MGIGA_PREC_TF32 || h->opt.precision == MGIGA_PREC_BF16) CK(prepare_gemm_umma());
     A.budget = h->opt.hbm_budget;
     h->D.assign(lv, DLevel{});
     const int sm = h->opt.smoother;
@@ -808,7 +1025,8 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       d.nloc = L.nloc;
       d.ndof = L.ndof;
       d.K = L.K;
-      d.arith = h->opt.precision == MGIGA_PREC_FP64 ? 0 : 1;
+      d.arith = h->opt.precision == MGIGA_PREC_FP64 ? 0 : h->opt.precision == MGIGA_PREC_FP32 ? 1
+              : h->opt.precision == MGIGA_PREC_TF32 ? 2 : 3;
       d.guard = guard_of(L);
       d.u = A.guarded(L.nloc, d.guard);
       d.f = A.guarded(L.nloc, d.guard);
@@ -850,7 +1068,7 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
         build_fd(L, l, h->opt.delta, h->opt.tau, A, d);
         build_pieces(h->pieces[l], L, A, d, false);
       }
-      if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) build_gs(h->colours[l], L, A, d);
+      if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) build_gs(h->pr, h->colours[l], L, A, d);
     }
     const Level& Lf = h->L[lv - 1];
     const int64_t g = guard_of(Lf);
@@ -1227,7 +1445,7 @@ static void run_stage(mgiga_handle* h, int stage, int level) {
       break;
     case MGIGA_STAGE_FD:
       for (const auto& s : d.fd_steps)
-        launch_gemm(s.second - s.first, d.arith, h->stream, d.fd_tasks, d.fd_items + s.first);
+        run_fd_step(h, d, s);
       break;
     case MGIGA_STAGE_PIECES:
       launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r,

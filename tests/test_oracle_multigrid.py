@@ -100,6 +100,28 @@ def test_colouring_is_valid(coupling, d):
     assert all((r, c) in Sd for r, c in zip(A.row.tolist(), A.col.tolist()))
 
 
+@pytest.mark.parametrize("coupling,d", [("conforming", 2), ("sipg", 2), ("conforming", 3), ("sipg", 3)])
+def test_base_colours_keep_same_parity_patches_uncoupled(coupling, d):
+    # DoFs on base colours (< 2 (p+1)^d) never couple with a DoF owned by
+    # another patch of the same parity; on patch grids with SIPG nothing moves
+    cells = (3, 3) if d == 2 else (2, 2, 2)
+    n = (lambda c, a: 3 if sum(c) % 2 == 0 else 4) if coupling == "sipg" else 3
+    p = 2
+    prob = W.grid_problem(cells, n, p, coupling, jitter=0.05, seed=2)
+    num = discretize.numbering(prob, prob["knots"])
+    col = smoothers.colouring(prob, prob["knots"], num)
+    par = smoothers.patch_parity(prob)
+    own = np.array([k for (k, f) in num["owner"]])
+    S = smoothers.structural_pattern(prob, prob["knots"], num).tocoo()
+    nb = 2 * (p + 1) ** d
+    both_base = (col[S.row] < nb) & (col[S.col] < nb)
+    other = own[S.row] != own[S.col]
+    same_par = np.array(par)[own[S.row]] == np.array(par)[own[S.col]]
+    assert not np.any(both_base & other & same_par)
+    if coupling == "sipg":
+        assert col.max() < nb
+
+
 def test_colouring_conflicts_get_extra_colours():
     # a non-bipartite patch graph (3 patches around a vertex cannot be
     # 2-coloured) is emulated by a 2x2 conforming grid: the shared centre

@@ -355,8 +355,9 @@ __global__ void __launch_bounds__(128) gemm_umma(const GemmTask* __restrict__ ta
   constexpr int KT = UKB / ES;  // K elements per stage
   // dynamic shared memory (kUmmaSmem bytes): two A and two B stage buffers
   extern __shared__ __align__(1024) unsigned char usm[];
-  unsigned char* sA[2] = {usm, usm + UM * UKB};
-  unsigned char* sB[2] = {usm + 2 * UM * UKB, usm + 2 * UM * UKB + UN * UKB};
+  // stage buffer b: A at usm + b * UM * UKB, B at usm + 2 * UM * UKB + b * UN * UKB
+  auto sA = [&](int b) { return usm + b * (UM * UKB); };
+  auto sB = [&](int b) { return usm + 2 * UM * UKB + b * (UN * UKB); };
   __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ unsigned tmem_slot;
   const GemmItem it = items[blockIdx.x];
@@ -393,31 +394,35 @@ __global__ void __launch_bounds__(128) gemm_umma(const GemmTask* __restrict__ ta
       phase_bits ^= 1u << b;
     }
     const int k0 = st * KT;
-    // A: one row per thread; B: half a row per thread
-    {
-      const int m = m0 + tid;
-      for (int kk = 0; kk < KT; ++kk) {
-        const int k = k0 + kk;
-        float v = 0.0f;
-        if (m < g.M && k < g.K)
-          v = ldt<float>(g.A, oA + (g.transA ? (int64_t)k * g.lda + m : (int64_t)m * g.lda + k), g.tA);
-        umma_store<KIND>(sA[b], tid, kk, v);
-      }
-      const int nr = tid >> 1, kh = (tid & 1) * (KT / 2);
-      const int n = n0 + nr;
-      for (int kk = kh; kk < kh + KT / 2; ++kk) {
-        const int k = k0 + kk;
-        float v = 0.0f;
-        if (n < g.N && k < g.K)
-          v = ldt<float>(g.B, oB + (g.transB ? (int64_t)n * g.ldb + k : (int64_t)k * g.ldb + n), g.tB);
-        umma_store<KIND>(sB[b], nr, kk, v);
-      }
+    // coalesced staging: consecutive threads read consecutive global addresses
+    // (along k when it is the contiguous index, else along m / n)
+#pragma unroll 4
+    for (int i = 0; i < (UM * KT) / 128; ++i) {
+      const int e = i * 128 + tid;
+      const int row = g.transA ? e % UM : e / KT;
+      const int kk = g.transA ? e / UM : e % KT;
+      const int m = m0 + row, k = k0 + kk;
+      float v = 0.0f;
+      if (m < g.M && k < g.K)
+        v = ldt<float>(g.A, oA + (g.transA ? (int64_t)k * g.lda + m : (int64_t)m * g.lda + k), g.tA);
+      umma_store<KIND>(sA(b), row, kk, v);
+    }
+#pragma unroll 4
+    for (int i = 0; i < (UN * KT) / 128; ++i) {
+      const int e = i * 128 + tid;
+      const int nr = g.transB ? e / KT : e % UN;
+      const int kk = g.transB ? e % KT : e / UN;
+      const int n = n0 + nr, k = k0 + kk;
+      float v = 0.0f;
+      if (n < g.N && k < g.K)
+        v = ldt<float>(g.B, oB + (g.transB ? (int64_t)n * g.ldb + k : (int64_t)k * g.ldb + n), g.tB);
+      umma_store<KIND>(sB(b), nr, kk, v);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0 && ok) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned a0 = smem_u32(sA[b]), b0 = smem_u32(sB[b]);
+      const unsigned a0 = smem_u32(sA(b)), b0 = smem_u32(sB(b));
 #pragma unroll
       for (int j = 0; j < UKB / 32; ++j) {
         const uint64_t ad = umma_sdesc(a0 + 256 * j), bd = umma_sdesc(b0 + 256 * j);
@@ -653,155 +658,204 @@ __global__ void __launch_bounds__(256) gs_sweep_coop(GsSweepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Base colours of one patch parity, mixed path (FP32 arithmetic): the
-// patch's u lives in shared memory (a slab per CTA of the patch's cluster,
-// neighbouring slabs read through distributed shared memory); for every
-// colour the CTA's rows come as one contiguous block -- FP32 coefficients
-// [o][row], the row's index in the slab, its slot of couplings to the other
-// parity, and f -- copied into shared memory by a bulk asynchronous copy one
-// colour ahead (double buffer, mbarrier completion).  Couplings to patches of
-// the other parity (SIPG flux/penalty terms, further copies of conforming
-// shared DoFs) do not change during the phase and are summed once per slot at
-// its start.  Colours are separated by the hardware cluster barrier.
+// Base colours of one patch parity, mixed path (FP32 arithmetic).  The patch
+// is split along its slowest direction into the slabs of the CTAs of one
+// cluster; a CTA keeps u of its slab plus P slow indices on each side (the
+// halo, refreshed by its neighbours through distributed shared memory) in
+// shared memory, with zero rows beyond the patch and zero guards at both
+// ends, so that every band neighbour of a row is a plain shared-memory read
+// (off-patch columns have zero coefficients).  For every colour the CTA's
+// rows come as one contiguous block -- FP32 coefficients [o][row], the packed
+// slab position, f minus the couplings to the other parity (written by
+// gs_fill_phase before the launch) and the inverse diagonal; consecutive
+// blocks are fetched together as one bulk asynchronous copy ("chunk"), two
+// chunk buffers in flight, mbarrier completion.  Colours are separated by the
+// CTA barrier (one CTA per patch) or the hardware cluster barrier.
 // Every wait on an mbarrier is bounded: on expiry the CTA records the error,
-// stops computing and keeps taking part in the cluster barriers.
+// stops computing and keeps taking part in the barriers.
 // ---------------------------------------------------------------------------
-template <int D, int P, int TPR>
-__global__ void __launch_bounds__(256) gs_patch_staged(GsStagedArgs a) {
+template <int D, int P>
+__global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int W = 2 * P + 1;
   constexpr int NOB = D == 2 ? W : W * W;
   constexpr int NB = NOB * W;
-  constexpr int center = D == 2 ? P * W + P : (P * W + P) * W + P;
   cg::cluster_group cluster = cg::this_cluster();
   const int cs = a.csize;
   const int q = blockIdx.x / cs;
   const int r = (int)cluster.block_rank();
   const int k = a.phase_patches[q];
   const int S = a.slab[k];
+  const int pitch = a.pitch[k];  // shared-memory stride of one slow index (>= plane)
+  const int G = a.guard[k];      // zero floats before and after the extended slab
   const PatchMeta pm = a.patches[k];
-  const int64_t N0 = pm.N[0];
-  const int64_t plane = D == 2 ? N0 : N0 * pm.N[1];
+  const int N0 = pm.N[0];
+  const int plane = D == 2 ? N0 : N0 * pm.N[1];
   const int nslow = D == 2 ? pm.N[1] : pm.N[2];
-  const int64_t cap = (int64_t)S * plane;
   const int s_lo = r * S, s_hi = min(nslow, (r + 1) * S);
-  double* uslab = reinterpret_cast<double*>(smem);
-  float* xsum = reinterpret_cast<float*>(smem + a.off_xsum);
-  unsigned char* const buf0 = smem + a.off_buf;  // buffer b at buf0 + b * buf_bytes
+  const int ext_len = 2 * G + (S + 2 * P) * pitch;  // slow indices s_lo - P .. s_lo + S + P - 1
+  const int H = (P + S - 1) / S;  // CTAs on each side whose halo may hold my indices
+  float* us = reinterpret_cast<float*>(smem);
+  unsigned char* const buf0 = smem + a.off_buf;
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + a.off_mbar);
+  int4* cm = reinterpret_cast<int4*>(smem + a.off_meta);  // per colour: rows, chunk, offset in chunk, Rp
+  int4* ch = cm + a.base;                                  // per chunk: byte offset (lo, hi), bytes, -
   const int tid = threadIdx.x;
-  const int slab_id = k * cs + r;
-  const int nslot = a.slot_ptr[slab_id + 1] - a.slot_ptr[slab_id];
-  const int* slot_e = a.slot_entry + a.slot_ptr[slab_id];
+  const int nthr = blockDim.x;
   const int nc = a.c_end - a.c_begin;
-  auto group_of = [&](int ci) {
-    const int c = a.forward ? a.c_begin + ci : a.c_end - 1 - ci;
-    return ((int64_t)c * a.K + k) * cs + r;
-  };
+  const int dir = a.forward ? 0 : 1;
+  const int ph = a.c_begin / a.base;
+  const int64_t reg = ((((int64_t)dir * 2 + ph) * a.K + k) * cs + r) * a.base;
+  for (int i = tid; i < nc; i += nthr) {
+    cm[i] = a.cmeta[reg + i];
+    ch[i] = a.chunks[reg + i];
+  }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  auto issue = [&](int ci, int b) {  // thread 0: bulk copy of colour ci's block into buffer b
-    const int64_t g = group_of(ci);
-    const unsigned bytes = (unsigned)a.blk_bytes[g];
+  const int nchunk = nc > 0 ? cm[nc - 1].y + 1 : 0;
+  const int nbuf = a.nbuf;
+  auto copy = [&](int j) {  // thread 0: chunk j into its buffer
+    const int b = nbuf == 1 ? 0 : (j & 1);
     const unsigned bar = smem_u32(&mbar[b]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    if (bytes > 0)
+    const int4 c = ch[j];
+    const int64_t off = (int64_t)(unsigned)c.x | ((int64_t)c.y << 32);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(c.z) : "memory");
+    if (c.z > 0)
       asm volatile(
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              smem_u32(buf0 + (size_t)b * a.buf_bytes)),
-          "l"(a.pool + a.blk_off[g]), "r"(bytes), "r"(bar)
+              smem_u32(buf0 + (size_t)b * a.cap)),
+          "l"(a.pool + off), "r"(c.z), "r"(bar)
           : "memory");
   };
-  if (tid == 0 && nc > 0) issue(0, 0);
-  // u slab and the couplings to the other parity (fixed during the phase)
-  for (int64_t i = tid; i < (int64_t)(s_hi - s_lo) * plane; i += blockDim.x)
-    uslab[i] = __ldcg(a.u + pm.off + (int64_t)s_lo * plane + i);
-  for (int t = tid; t < nslot; t += blockDim.x) {
-    const int e = slot_e[t];
-    double v = 0.0;
-    const int2 xr = a.gs_xrange[e];
-    for (int j = xr.x; j < xr.y; ++j) v += a.x_val[j] * __ldcg(a.u + a.x_col[j]);
-    xsum[t] = (float)v;
+  if (tid == 0) {
+    if (nchunk > 0) copy(0);
+    if (nchunk > 1 && nbuf == 2) copy(1);
   }
-  cluster.sync();
+  // u of the extended slab (zero outside the patch and in the guards), four independent loads per thread
+  {
+    const double* ug = a.u + pm.off;
+    const int body = (S + 2 * P) * pitch;
+    for (int i0 = tid; i0 < ext_len; i0 += 4 * nthr) {
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = i0 + j * nthr;
+        v[j] = 0.0f;
+        const int t = i - G;
+        if (i < ext_len && t >= 0 && t < body) {
+          const int row = t / pitch, col = t - row * pitch;
+          const int s = s_lo - P + row;
+          if (s >= 0 && s < nslow && col < plane) v[j] = (float)__ldcg(ug + (int64_t)s * plane + col);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (i0 + j * nthr < ext_len) us[i0 + j * nthr] = v[j];
+    }
+  }
+  // one CTA per patch: the CTA barrier orders everything; else the cluster
+  // barrier (release/acquire) also publishes the halo stores, and here keeps
+  // neighbours from refreshing a halo before it is loaded
+  auto sync_all = [&]() {
+    if (cs == 1) __syncthreads();
+    else cluster.sync();
+  };
+  sync_all();
+  const int TPR = a.tpr;  // threads per row (power of two, <= 32)
   const int lane = tid & 31;
-  const int sub = lane % TPR;
+  const int sub = lane & (TPR - 1);
   const int warp = tid >> 5;
   const int rows_per_warp = 32 / TPR;
-  const int rows_per_cta = blockDim.x / TPR;
+  const int rows_per_cta = nthr / TPR;
   bool ok = true;
-  unsigned phase_bits = 0;
+  int cur = -1;
   for (int ci = 0; ci < nc; ++ci) {
-    const int b = ci & 1;
-    if (ok && !mbar_wait(smem_u32(&mbar[b]), (phase_bits >> b) & 1u)) {
-      ok = false;
-      atomicExch(a.err, 2);
+    const int4 m = cm[ci];  // rows, chunk, offset in chunk, Rp
+    const int b = nbuf == 1 ? 0 : (m.y & 1);
+    if (m.y != cur) {  // first colour of chunk m.y
+      cur = m.y;
+      const unsigned parity = nbuf == 1 ? 0u : (unsigned)((m.y >> 1) & 1);
+      if (ok && !mbar_wait(smem_u32(&mbar[b]), parity)) {
+        ok = false;
+        atomicExch(a.err, 2);
+      }
+      // the other buffer held chunk m.y - 1, released by the barrier that ended its last colour
+      if (tid == 0 && ok && nbuf == 2 && m.y >= 1 && m.y + 1 < nchunk) copy(m.y + 1);
     }
-    phase_bits ^= 1u << b;
-    // the other buffer was released by the barrier that ended colour ci - 1
-    if (tid == 0 && ok && ci + 1 < nc) issue(ci + 1, b ^ 1);
-    const int64_t g = group_of(ci);
-    const int R = a.blk_rows[g];
-    const int Rp = (R + 3) & ~3;
-    const float* coef = reinterpret_cast<const float*>(buf0 + (size_t)b * a.buf_bytes);
-    const int* lidx = reinterpret_cast<const int*>(coef + (int64_t)NB * Rp);
-    const int* slot = lidx + Rp;
-    const float* fval = reinterpret_cast<const float*>(slot + Rp);
+    const int R = m.x, Rp = m.w;
+    const float* coef = reinterpret_cast<const float*>(buf0 + (size_t)b * a.cap + m.z);
+    const int* lidx = reinterpret_cast<const int*>(coef + NB * Rp);
+    const float* fv = reinterpret_cast<const float*>(lidx + Rp);
+    const float* dinv = fv + Rp;
     if (ok) {
       for (int base = warp * rows_per_warp; base < R; base += rows_per_cta) {
         const int row = base + lane / TPR;
         const bool active = row < R;
-        float acc = 0.0f;
-        int li = 0;
+        float acc = 0.0f, acc1 = 0.0f;  // two chains of dependent FMAs
+        int own = 0, srow = 0, rest = 0;
         if (active) {
-          li = lidx[row];  // index in this CTA's slab
-          const int s = s_lo + (int)(li / plane);
-          const int64_t rest = li - (int64_t)(s - s_lo) * plane;
+          const unsigned li = (unsigned)lidx[row];  // (slow index - s_lo) << 20 | index within the plane
+          srow = (int)(li >> 20);
+          rest = (int)(li & 0xFFFFFu);
+          own = G + (srow + P) * pitch + rest;
           for (int ob = sub; ob < NOB; ob += TPR) {
             const int o1 = ob % W, o2 = ob / W;
-            const int sp = s + (D == 2 ? o1 : o2) - P;
-            if (sp < 0 || sp >= nslow) continue;  // zero coefficients
-            const int rp = sp / S;
-            const double* src = rp == r ? uslab : cluster.map_shared_rank(uslab, rp);
-            const int64_t idx0 = (int64_t)(sp - rp * S) * plane + rest + (D == 3 ? (int64_t)(o1 - P) * N0 : 0) - P;
-            const float* cr = coef + (int64_t)ob * W * Rp + row;
+            const float* ur = us + own + (D == 2 ? (o1 - P) * pitch : (o2 - P) * pitch + (o1 - P) * N0) - P;
+            const float* cr = coef + ob * W * Rp + row;
 #pragma unroll
             for (int o0 = 0; o0 < W; ++o0) {
-              int64_t idx = idx0 + o0;
-              idx = idx < 0 ? 0 : (idx >= cap ? cap - 1 : idx);  // off-patch columns carry zero coefficients
-              acc = fmaf(cr[(int64_t)o0 * Rp], (float)src[idx], acc);
+              if (o0 & 1) acc1 = fmaf(cr[o0 * Rp], ur[o0], acc1);
+              else acc = fmaf(cr[o0 * Rp], ur[o0], acc);
             }
           }
         }
-#pragma unroll
+        acc += acc1;
         for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (active && sub == 0) {
-          const int sl = slot[row];
-          if (sl >= 0) acc += xsum[sl];
-          const float diag = coef[(int64_t)center * Rp + row];
-          uslab[li] += (double)((fval[row] - acc) / diag);
+          const float v = us[own] + (fv[row] - acc) * dinv[row];
+          us[own] = v;
+          // refresh the copies of this value in the neighbours' halos
+          const int s = s_lo + srow;
+          for (int rr = max(0, r - H); rr <= min(cs - 1, r + H); ++rr) {
+            const int lo2 = rr * S - P;
+            if (rr == r || s < lo2 || s >= lo2 + S + 2 * P) continue;
+            float* rem = cluster.map_shared_rank(us, rr);
+            rem[G + (s - lo2) * pitch + rest] = v;
+          }
         }
       }
     }
-    cluster.sync();
+    sync_all();
   }
   // the slab back to global memory
-  for (int64_t i = tid; i < (int64_t)(s_hi - s_lo) * plane; i += blockDim.x)
-    a.u[pm.off + (int64_t)s_lo * plane + i] = uslab[i];
+  double* ug = a.u + pm.off;
+  const int n_own = (s_hi - s_lo) * plane;
+  for (int i = tid; i < n_own; i += nthr) {
+    const int row = i / plane, col = i - row * plane;
+    ug[(int64_t)(s_lo + row) * plane + col] = (double)us[G + (row + P) * pitch + col];
+  }
 }
 
-// f of every base-colour entry into its block (before a sweep)
-__global__ void gs_fill_f(int n, const int64_t* __restrict__ f_off, const int64_t* __restrict__ gs_pos,
-                          const double* __restrict__ f, unsigned char* pool) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
+// f minus the couplings to the other parity (SIPG cross-patch terms, from the
+// current u) for the base-colour entries [e0, e0 + n) of one phase, into their blocks
+__global__ void gs_fill_phase(int e0, int n, const int64_t* __restrict__ f_off, const int64_t* __restrict__ gs_pos,
+                              const int2* __restrict__ xrange, const int64_t* __restrict__ x_col,
+                              const double* __restrict__ x_val, const double* __restrict__ f,
+                              const double* __restrict__ u, unsigned char* pool) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int e = e0 + i;
   const int64_t o = f_off[e];
-  if (o >= 0) *reinterpret_cast<float*>(pool + o) = (float)f[gs_pos[e]];
+  if (o < 0) return;
+  double v = f[gs_pos[e]];
+  const int2 xr = xrange[e];
+  for (int j = xr.x; j < xr.y; ++j) v -= x_val[j] * u[x_col[j]];
+  *reinterpret_cast<float*>(pool + o) = (float)v;
 }
 
 // ---------------------------------------------------------------------------
@@ -1021,7 +1075,7 @@ constexpr int kStagedSmemMax = 225 * 1024;
 
 template <int D, int P>
 static void* gs_staged_func() {
-  return (void*)gs_patch_staged<D, P, 4>;
+  return (void*)gs_patch_staged<D, P>;
 }
 
 static void* gs_staged_ptr(int d, int p) {
@@ -1034,7 +1088,7 @@ static void* gs_staged_ptr(int d, int p) {
   }
 }
 
-bool gs_staged_fits(int d, int p, int csize, int smem) {
+bool gs_staged_fits(int d, int p, int csize, int smem, int threads) {
   void* fn = gs_staged_ptr(d, p);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
   // the attribute belongs to the kernel, not to a launch: always allow the
@@ -1046,7 +1100,7 @@ bool gs_staged_fits(int d, int p, int csize, int smem) {
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(csize);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute at;
   at.id = cudaLaunchAttributeClusterDimension;
@@ -1068,7 +1122,7 @@ cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t
   ++g_launches;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nclusters * a.csize);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(a.threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at;
@@ -1083,11 +1137,12 @@ cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t
   return cudaLaunchKernelExC(&cfg, gs_staged_ptr(d, p), args);
 }
 
-void launch_gs_fill_f(int n, cudaStream_t st, const int64_t* f_off, const int64_t* gs_pos, const double* f,
-                      unsigned char* pool) {
+void launch_gs_fill_phase(int e0, int n, cudaStream_t st, const int64_t* f_off, const int64_t* gs_pos,
+                          const int2* xrange, const int64_t* x_col, const double* x_val, const double* f,
+                          const double* u, unsigned char* pool) {
   if (n <= 0) return;
   ++g_launches;
-  gs_fill_f<<<(n + 255) / 256, 256, 0, st>>>(n, f_off, gs_pos, f, pool);
+  gs_fill_phase<<<(n + 255) / 256, 256, 0, st>>>(e0, n, f_off, gs_pos, xrange, x_col, x_val, f, u, pool);
 }
 
 void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,

@@ -38,28 +38,28 @@ int gs_coop_max_blocks(int d, int p, bool f32);
 cudaError_t launch_gs_sweep(int d, int p, bool f32, int blocks, cudaStream_t st, GsSweepArgs a);
 // staged patch-parallel phase of the mixed path (FP32 coefficient blocks)
 struct GsStagedArgs {
-  int c_begin, c_end, forward;  // base colours of the phase
-  int K, csize;                 // patches, CTAs per patch cluster
+  int c_begin, c_end, forward;  // base colours of the phase, sweep direction
+  int K, csize, base;           // patches, CTAs per patch cluster, base colours per parity
+  int nbuf, cap;                // chunk buffers (1: the CTA's whole phase at once, or 2) of cap bytes
+  int threads, tpr;             // CTA size (256, 512 or 1024) and threads per row (4..32, power of two)
   const int* phase_patches;     // cluster q sweeps patch phase_patches[q]
   const int* slab;              // slab height (slow indices) per patch
-  const unsigned char* pool;    // colour blocks, 16-byte aligned
-  const int64_t* blk_off;       // block of group (c K + k) csize + r: byte offset
-  const int* blk_bytes;         //   its size in bytes (multiple of 16)
-  const int* blk_rows;          //   its number of rows
-  const int* slot_ptr;          // slots of slab (k csize + r): [slot_ptr[i], slot_ptr[i+1])
-  const int* slot_entry;        //   gs entry of each slot
-  int off_xsum, off_buf, buf_bytes, off_mbar;  // shared-memory layout
+  const int* pitch;             // shared-memory stride of a slow index per patch (>= its plane)
+  const int* guard;             // zero floats before and after a CTA's extended slab, per patch
+  const unsigned char* pool;    // colour blocks, ordered by (phase, k, r, colour)
+  // per (direction, phase, k, r) = ((dir 2 + phase) K + k) csize + r, times base, in sweep order:
+  const int4* cmeta;            //   per colour: rows, chunk, byte offset in the chunk, padded rows Rp
+  const int4* chunks;           //   per chunk: byte offset in the pool (low, high word), bytes, -
+  int off_buf, off_mbar, off_meta;  // shared-memory layout (u slab at 0; 2 mbarriers; 32 B x base of meta)
   const PatchMeta* patches;
-  const int2* gs_xrange;
-  const int64_t* x_col;
-  const double* x_val;
   double* u;
   int* err;
 };
-bool gs_staged_fits(int d, int p, int csize, int smem);
+bool gs_staged_fits(int d, int p, int csize, int smem, int threads);
 cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t st, const GsStagedArgs& a);
-void launch_gs_fill_f(int n, cudaStream_t st, const int64_t* f_off, const int64_t* gs_pos, const double* f,
-                      unsigned char* pool);
+void launch_gs_fill_phase(int e0, int n, cudaStream_t st, const int64_t* f_off, const int64_t* gs_pos,
+                          const int2* xrange, const int64_t* x_col, const double* x_val, const double* f,
+                          const double* u, unsigned char* pool);
 
 void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
                  const double* band, int64_t nloc, const double* u, const double* f, double* out);

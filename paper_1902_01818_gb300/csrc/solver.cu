@@ -434,61 +434,142 @@ void build_pieces(const std::vector<Piece>& pcs, const Level& L, Arena& A, DLeve
 
 // Colour blocks of the staged patch-parallel sweep (mixed path).  A group is
 // (base colour c, patch k, slab r of the patch's cluster); its block holds
-// float coef[o][Rp], int lidx[Rp], int slot[Rp], float f[Rp] (Rp = rows
-// rounded up to 4) and is copied into shared memory in one piece.
+// float coef[o][Rp], int lidx[Rp] ((slow index - slab start) << 20 | index in
+// the plane), float f[Rp] (f minus the couplings to the other parity, written
+// before each phase) and float dinv[Rp] (1 / diagonal), padded to 16 bytes.
+// Rp >= rows and the shared-memory pitch of a slow index are chosen so that
+// the threads of a warp read distinct banks.  Blocks are ordered by (phase,
+// k, r, colour); runs of consecutive colours (in sweep order) that fit one
+// buffer are fetched as one chunk.
 void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl,
                      const std::vector<int>& order, const std::vector<int64_t>& gpos, const std::vector<int>& gpatch,
-                     const std::vector<int>& gx, int ncol, int B) {
-  const int K = L.K, d = L.d, nb = L.nb;
+                     int ncol, int B) {
+  const int K = L.K, d = L.d, nb = L.nb, P = L.p;
+  const int W = 2 * P + 1, nob = d == 2 ? W : W * W;
+  const int center = d == 2 ? P * W + P : (P * W + P) * W + P;
   const int nbase = std::min(ncol, 2 * B);
   const int nent = nbase > 0 ? dl.gs_cptr[nbase] : 0;
+  if (nent == 0) return;
   auto plane_of = [&](int k) { return d == 2 ? (int64_t)L.N[k][0] : (int64_t)L.N[k][0] * L.N[k][1]; };
   auto nslow_of = [&](int k) { return L.N[k][d - 1]; };
   std::vector<int> cls_of(L.ndof, -1);
   for (size_t c = 0; c + 1 < L.sh_ptr.size(); ++c) cls_of[L.loc2glob[L.sh_pos[L.sh_ptr[c]]]] = (int)c;
   for (int e = 0; e < nent; ++e)
     if (cls_of[order[e]] >= 0) throw SetupError(MGIGA_EINVAL, "shared DoF on a base colour");
-  auto has_slot = [&](int e) { return gx[e] >= 0; };
-  // rows per group and slots per slab for a cluster size
-  struct Plan { int cs; std::vector<int> slab; std::vector<int> grp_of; int64_t max_block; int max_slots; int64_t max_cap; };
-  auto plan_for = [&](int cs) {
-    Plan pl;
+  for (int k = 0; k < K; ++k)
+    if (plane_of(k) >= (1 << 20) || nslow_of(k) >= (1 << 11)) return;  // beyond the packed index: grid-wide sweep
+  // most lanes of one warp that hit one bank (a warp: 32 / tpr rows spaced p + 1 apart, tpr coefficient lines)
+  auto bank_degree = [&](int tpr, auto word) {
+    int cnt[32] = {0}, worst = 0;
+    for (int j = 0; j < 32 / tpr; ++j)
+      for (int q = 0; q < std::min(tpr, nob); ++q) worst = std::max(worst, ++cnt[((word(j, q) % 32) + 32) % 32]);
+    return worst;
+  };
+  const int64_t limit = 225 * 1024;
+  struct Plan {
+    int cs = 0, threads = 0, tpr = 0, nbuf = 0;
+    int64_t cap = 0, total = 0;
+    int off_buf = 0, off_mbar = 0, off_meta = 0;
+    std::vector<int> slab, pitch, guard, grp_of, rows, rp;
+    std::vector<int64_t> bytes;
+  };
+  auto plan_for = [&](int cs, Plan& pl) -> bool {
     pl.cs = cs;
     pl.slab.resize(K);
-    pl.max_cap = 0;
-    for (int k = 0; k < K; ++k) {
-      pl.slab[k] = (nslow_of(k) + cs - 1) / cs;
-      pl.max_cap = std::max<int64_t>(pl.max_cap, (int64_t)pl.slab[k] * plane_of(k));
-    }
+    for (int k = 0; k < K; ++k) pl.slab[k] = (nslow_of(k) + cs - 1) / cs;
+    const int ngrp = nbase * K * cs;
     pl.grp_of.assign(nent, 0);
-    std::vector<int> rows((size_t)nbase * K * cs, 0), slots((size_t)K * cs, 0);
+    pl.rows.assign(ngrp, 0);
     for (int e = 0; e < nent; ++e) {
       const int c = colour[order[e]], k = gpatch[e];
       const int r = (int)((gpos[e] - L.off[k]) / plane_of(k)) / pl.slab[k];
       const int g = (c * K + k) * cs + r;
       pl.grp_of[e] = g;
-      rows[g]++;
-      if (has_slot(e)) slots[k * cs + r]++;
+      pl.rows[g]++;
     }
-    pl.max_block = 0;
-    for (int v : rows) pl.max_block = std::max<int64_t>(pl.max_block, (int64_t)(nb + 3) * ((v + 3) & ~3) * 4);
-    pl.max_slots = 0;
-    for (int v : slots) pl.max_slots = std::max(pl.max_slots, v);
-    return pl;
+    int max_rows = 0;
+    for (int v : pl.rows) max_rows = std::max(max_rows, v);
+    // CTA shape: a row is summed by tpr threads (its coefficient lines split
+    // among them, then a shuffle tree), threads / tpr rows at a time; minimise
+    // the dependent steps of the longest colour
+    double best = 1e30;
+    for (int nt : {256, 512, 1024})
+      for (int tpr : {4, 8, 16, 32}) {
+        const int passes = std::max(1, (max_rows + nt / tpr - 1) / (nt / tpr));
+        const int lines = (nob + tpr - 1) / tpr;
+        const double cost = passes * (lines * (W * 2.0 + 40.0) + 40.0 * std::log2((double)tpr)) + nt / 8.0;
+        if (cost < best) {
+          best = cost;
+          pl.threads = nt;
+          pl.tpr = tpr;
+        }
+      }
+    if (const char* env = std::getenv("MGIGA_GS_SHAPE")) {  // "threads,tpr": manual override for tuning
+      int nt = 0, tp = 0;
+      if (std::sscanf(env, "%d,%d", &nt, &tp) == 2 && (nt == 256 || nt == 512 || nt == 1024) &&
+          (tp == 4 || tp == 8 || tp == 16 || tp == 32)) {
+        pl.threads = nt;
+        pl.tpr = tp;
+      }
+    }
+    const int tpr = pl.tpr;
+    // padded rows: coefficient line q of row j is word q W Rp + j
+    int rp_deg[32], rp_best = 1 << 30;
+    for (int x = 0; x < 32; ++x) {
+      rp_deg[x] = bank_degree(tpr, [&](int j, int q) { return q * W * x + j; });
+      rp_best = std::min(rp_best, rp_deg[x]);
+    }
+    pl.rp.assign(ngrp, 0);
+    pl.bytes.assign(ngrp, 0);
+    for (int g = 0; g < ngrp; ++g) {
+      int x = pl.rows[g];
+      if (x > 0)
+        while (rp_deg[x % 32] != rp_best) ++x;
+      pl.rp[g] = x;
+      pl.bytes[g] = ((int64_t)(nb + 3) * x * 4 + 15) / 16 * 16;
+    }
+    // slab pitch and guards; the extended slab
+    int64_t ext = 0;
+    pl.pitch.resize(K);
+    pl.guard.resize(K);
+    for (int k = 0; k < K; ++k) {
+      const int plane = (int)plane_of(k), N0 = L.N[k][0];
+      int bp = plane, bd = 1 << 30;
+      for (int x = plane; x < plane + 32; ++x) {
+        const int dg = bank_degree(tpr, [&](int j, int q) {
+          return (P + 1) * j + (d == 2 ? q * x : (q % W) * N0 + (q / W) * x);
+        });
+        if (dg < bd) { bd = dg; bp = x; }
+      }
+      pl.pitch[k] = bp;
+      pl.guard[k] = ((d == 2 ? P : P * N0 + P) + 3) / 4 * 4;
+      ext = std::max<int64_t>(ext, 2 * pl.guard[k] + (int64_t)(pl.slab[k] + 2 * P) * bp);
+    }
+    std::vector<int64_t> region((size_t)2 * K * cs, 0);
+    int64_t max_block = 0, max_region = 0;
+    for (int g = 0; g < ngrp; ++g) {
+      const int c = g / (K * cs), kr = g % (K * cs);
+      region[(size_t)(c / B) * K * cs + kr] += pl.bytes[g];
+      max_block = std::max(max_block, pl.bytes[g]);
+    }
+    for (int64_t v : region) max_region = std::max(max_region, v);
+    pl.off_buf = (int)((ext * 4 + 127) / 128 * 128);
+    const int64_t fixed = pl.off_buf + 16 + 32 * (int64_t)B + 16;
+    const int64_t avail = limit - fixed;
+    if (max_region <= avail) {
+      pl.nbuf = 1;
+      pl.cap = (max_region + 15) / 16 * 16;
+    } else {
+      pl.nbuf = 2;
+      pl.cap = avail / 2 / 16 * 16;
+      if (pl.cap < max_block) return false;
+    }
+    pl.off_mbar = (int)((pl.off_buf + pl.nbuf * pl.cap + 15) / 16 * 16);
+    pl.off_meta = pl.off_mbar + 16;
+    pl.total = pl.off_meta + 32 * (int64_t)B;
+    return pl.total <= limit;
   };
-  auto smem_of = [&](const Plan& pl, int& off_xsum, int& off_buf, int& off_mbar) {
-    int64_t o = pl.max_cap * 8;
-    o = (o + 15) / 16 * 16;
-    off_xsum = (int)o;
-    o += (int64_t)std::max(pl.max_slots, 1) * 4;
-    o = (o + 127) / 128 * 128;
-    off_buf = (int)o;
-    o += 2 * pl.max_block;
-    o = (o + 15) / 16 * 16;
-    off_mbar = (int)o;
-    o += 16;
-    return o;
-  };
+  // smallest cluster with about 128 rows of the largest colour per CTA that fits
   int maxrows_pk = 1;
   {
     std::vector<int> cnt((size_t)nbase * K, 0);
@@ -498,94 +579,114 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
   int want = 1;
   while (want < 16 && want * 64 * 2 < maxrows_pk) want *= 2;
   dl.gs_csize = 0;
-  Plan chosen;
-  int off_xsum = 0, off_buf = 0, off_mbar = 0;
-  for (int cs = want; cs <= 16 && nent > 0; cs *= 2) {
-    Plan pl = plan_for(cs);
-    int ox, ob, om;
-    const int64_t smem = smem_of(pl, ox, ob, om);
-    if (smem > 225 * 1024) continue;
-    if (!gs_staged_fits(d, L.p, cs, (int)smem)) continue;
-    chosen = pl;
+  Plan pl;
+  for (int cs = want; cs <= 16; cs *= 2) {
+    Plan t;
+    if (!plan_for(cs, t) || !gs_staged_fits(d, P, cs, (int)t.total, t.threads)) continue;
+    pl = std::move(t);
     dl.gs_csize = cs;
-    dl.gs_smem = (int)smem;
-    off_xsum = ox; off_buf = ob; off_mbar = om;
+    dl.gs_smem = (int)pl.total;
     break;
   }
   if (dl.gs_csize == 0) return;  // the grid-wide sweep handles every colour
   const int cs = dl.gs_csize;
-  // slots per slab
-  std::vector<int> slot_ptr((size_t)K * cs + 1, 0), slot_id(nent, -1);
-  for (int e = 0; e < nent; ++e)
-    if (has_slot(e)) slot_ptr[chosen.grp_of[e] % (K * cs) + 1]++;
-  // grp_of % (K cs) is (k cs + r) because g = (c K + k) cs + r
-  for (size_t i = 1; i < slot_ptr.size(); ++i) slot_ptr[i] += slot_ptr[i - 1];
-  std::vector<int> slot_entry(slot_ptr.back());
-  {
-    std::vector<int> fill(slot_ptr.begin(), slot_ptr.end() - 1);
-    for (int e = 0; e < nent; ++e)
-      if (has_slot(e)) {
-        const int sid = chosen.grp_of[e] % (K * cs);
-        slot_id[e] = fill[sid] - slot_ptr[sid];
-        slot_entry[fill[sid]++] = e;
-      }
-  }
-  // blocks
+  // blocks in (phase, k, r, colour) order
   const int ngrp = nbase * K * cs;
   std::vector<std::vector<int>> members(ngrp);
-  for (int e = 0; e < nent; ++e) members[chosen.grp_of[e]].push_back(e);
-  std::vector<int64_t> blk_off(ngrp);
-  std::vector<int> blk_bytes(ngrp), blk_rows(ngrp);
+  for (int e = 0; e < nent; ++e) members[pl.grp_of[e]].push_back(e);
+  std::vector<int64_t> blk_off(ngrp, 0);
   int64_t total = 0;
-  for (int g = 0; g < ngrp; ++g) {
-    const int R = (int)members[g].size(), Rp = (R + 3) & ~3;
-    blk_off[g] = total;
-    blk_rows[g] = R;
-    blk_bytes[g] = R > 0 ? (nb + 3) * Rp * 4 : 0;
-    total += blk_bytes[g];
-  }
+  for (int ph = 0; ph < 2; ++ph)
+    for (int k = 0; k < K; ++k)
+      for (int r = 0; r < cs; ++r)
+        for (int c = ph * B; c < std::min((ph + 1) * B, nbase); ++c) {
+          const int g = (c * K + k) * cs + r;
+          blk_off[g] = total;
+          total += pl.bytes[g];
+        }
   std::vector<unsigned char> pool((size_t)std::max<int64_t>(total, 16), 0);
   std::vector<int64_t> foff(L.ndof, -1);
   for (int g = 0; g < ngrp; ++g) {
-    const int R = blk_rows[g], Rp = (R + 3) & ~3;
+    const int R = pl.rows[g], Rp = pl.rp[g];
     if (R == 0) continue;
     float* coef = reinterpret_cast<float*>(pool.data() + blk_off[g]);
     int* lidx = reinterpret_cast<int*>(coef + (size_t)nb * Rp);
-    int* slot = lidx + Rp;
+    float* fv = reinterpret_cast<float*>(lidx + Rp);
+    float* dinv = fv + Rp;
     const int k = (g / cs) % K, r = g % cs;
+    const int64_t plane = plane_of(k);
     for (int row = 0; row < R; ++row) {
       const int e = members[g][row];
       const int64_t pos = gpos[e];
       for (int o = 0; o < nb; ++o) coef[(size_t)o * Rp + row] = (float)L.band[(size_t)o * L.nloc + pos];
-      lidx[row] = (int)(pos - L.off[k] - (int64_t)r * chosen.slab[k] * plane_of(k));
-      slot[row] = slot_id[e];
-      foff[e] = blk_off[g] + ((int64_t)nb + 2) * Rp * 4 + (int64_t)row * 4;
+      const int64_t loc = pos - L.off[k];
+      const int s = (int)(loc / plane), rest = (int)(loc % plane);
+      lidx[row] = ((s - r * pl.slab[k]) << 20) | rest;
+      dinv[row] = (float)(1.0 / L.band[(size_t)center * L.nloc + pos]);
+      foff[e] = blk_off[g] + ((int64_t)nb + 1) * Rp * 4 + (int64_t)row * 4;
     }
   }
+  // per (direction, phase, k, r): colours in sweep order grouped into chunks
+  const size_t nreg = (size_t)2 * 2 * K * cs;
+  std::vector<int4> cmeta(nreg * B, make_int4(0, 0, 0, 0)), chunks(nreg * B, make_int4(0, 0, 0, 0));
+  for (int dir = 0; dir < 2; ++dir)
+    for (int ph = 0; ph < 2; ++ph)
+      for (int k = 0; k < K; ++k)
+        for (int r = 0; r < cs; ++r) {
+          const size_t base = ((((size_t)dir * 2 + ph) * K + k) * cs + r) * B;
+          const int c0 = ph * B, nc = std::max(0, std::min((ph + 1) * B, nbase) - c0);
+          std::vector<int> chunk_of(nc);
+          std::vector<int64_t> lo, hi;
+          for (int i = 0; i < nc; ++i) {
+            const int c = dir == 0 ? c0 + i : c0 + nc - 1 - i;
+            const int g = (c * K + k) * cs + r;
+            const int64_t a0 = blk_off[g], a1 = blk_off[g] + pl.bytes[g];
+            if (!lo.empty() && std::max(hi.back(), a1) - std::min(lo.back(), a0) <= pl.cap) {
+              lo.back() = std::min(lo.back(), a0);
+              hi.back() = std::max(hi.back(), a1);
+            } else {
+              lo.push_back(a0);
+              hi.push_back(a1);
+            }
+            chunk_of[i] = (int)lo.size() - 1;
+          }
+          for (int i = 0; i < nc; ++i) {
+            const int c = dir == 0 ? c0 + i : c0 + nc - 1 - i;
+            const int g = (c * K + k) * cs + r;
+            const int j = chunk_of[i];
+            cmeta[base + i] = make_int4(pl.rows[g], j, (int)(blk_off[g] - lo[j]), pl.rp[g]);
+          }
+          for (size_t j = 0; j < lo.size(); ++j)
+            chunks[base + j] = make_int4((int)(uint32_t)(lo[j] & 0xffffffffLL), (int)(lo[j] >> 32),
+                                         (int)(hi[j] - lo[j]), 0);
+        }
   dl.gs_pool = A.upload(pool);
   dl.gs_foff = A.upload(foff);
+  const auto par = patch_parity(pr);
   for (int ph = 0; ph < 2; ++ph) {
-    std::vector<int> pl;
-    const auto par = patch_parity(pr);
+    std::vector<int> pp;
     for (int k = 0; k < K; ++k)
-      if (par[k] == ph) pl.push_back(k);
-    dl.gs_nphase[ph] = (int)pl.size();
-    dl.gs_phase_patches[ph] = A.upload(pl);
+      if (par[k] == ph) pp.push_back(k);
+    dl.gs_nphase[ph] = (int)pp.size();
+    dl.gs_phase_patches[ph] = A.upload(pp);
   }
   GsStagedArgs& a = dl.gs_staged;
   a.K = K;
   a.csize = cs;
-  a.slab = A.upload(chosen.slab);
+  a.base = B;
+  a.nbuf = pl.nbuf;
+  a.cap = (int)pl.cap;
+  a.threads = pl.threads;
+  a.tpr = pl.tpr;
+  a.slab = A.upload(pl.slab);
+  a.pitch = A.upload(pl.pitch);
+  a.guard = A.upload(pl.guard);
   a.pool = dl.gs_pool;
-  a.blk_off = A.upload(blk_off);
-  a.blk_bytes = A.upload(blk_bytes);
-  a.blk_rows = A.upload(blk_rows);
-  a.slot_ptr = A.upload(slot_ptr);
-  a.slot_entry = A.upload(slot_entry);
-  a.off_xsum = off_xsum;
-  a.off_buf = off_buf;
-  a.buf_bytes = (int)chosen.max_block;
-  a.off_mbar = off_mbar;
+  a.cmeta = A.upload(cmeta);
+  a.chunks = A.upload(chunks);
+  a.off_buf = pl.off_buf;
+  a.off_mbar = pl.off_mbar;
+  a.off_meta = pl.off_meta;
 }
 
 void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl) {
@@ -640,15 +741,18 @@ void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L,
   int B = 1;
   for (int a = 0; a < L.d; ++a) B *= L.p + 1;
   dl.gs_base = B;
-  if (f32) build_gs_staged(pr, colour, L, A, dl, order, gpos, gpatch, gx, ncol, B);
+  if (f32) build_gs_staged(pr, colour, L, A, dl, order, gpos, gpatch, ncol, B);
   int maxrows = 1;
   for (size_t c = 0; c + 1 < dl.gs_cptr.size(); ++c) maxrows = std::max(maxrows, dl.gs_cptr[c + 1] - dl.gs_cptr[c]);
   const int coop = gs_coop_max_blocks(L.d, L.p, f32);
   if (coop <= 0) throw CudaError("cooperative launch not available for the Gauss-Seidel sweep");
   dl.gs_blocks = std::max(1, std::min(coop, (maxrows * 8 + 255) / 256));
   if (std::getenv("MGIGA_VERBOSE"))
-    std::fprintf(stderr, "mgiga: gs level ndof %d colours %d base %d cluster %d smem %d grid-blocks %d\n", n, ncol,
-                 B, dl.gs_csize, dl.gs_smem, dl.gs_blocks);
+    std::fprintf(stderr,
+                 "mgiga: gs level ndof %d colours %d base %d cluster %d smem %d buffers %d x %d bytes threads %d "
+                 "tpr %d\n",
+                 n, ncol, B, dl.gs_csize, dl.gs_smem, dl.gs_staged.nbuf, dl.gs_staged.cap, dl.gs_staged.threads,
+                 dl.gs_staged.tpr);
   dl.gs_pos = A.upload(gpos);
   dl.gs_patch = A.upload(gpatch);
   dl.gs_cls = A.upload(gcls);
@@ -733,13 +837,16 @@ void gs_sweep(mgiga_handle* h, int l, bool forward) {
     if (g.c_end <= g.c_begin) return;
     g.forward = forward ? 1 : 0;
     g.phase_patches = d.gs_phase_patches[ph];
-    g.patches = d.patches; g.gs_xrange = d.gs_xrange;
-    g.x_col = d.x_col; g.x_val = d.x_val; g.u = d.u; g.err = h->gs_err;
+    g.patches = d.patches;
+    g.u = d.u;
+    g.err = h->gs_err;
+    // f minus the couplings to the other parity (fixed during the phase) into the blocks
+    const int e0 = d.gs_cptr[g.c_begin], e1 = d.gs_cptr[g.c_end];
+    launch_gs_fill_phase(e0, e1 - e0, h->stream, d.gs_foff, d.gs_pos, d.gs_xrange, d.x_col, d.x_val, d.f, d.u,
+                         d.gs_pool);
     CK(launch_gs_staged(L.d, L.p, d.gs_nphase[ph], d.gs_smem, h->stream, g));
   };
   auto tail = [&]() { coop(2 * B, ncol); };
-  if (d.gs_csize > 0)  // f of the base-colour entries into their blocks
-    launch_gs_fill_f(d.gs_cptr[std::min(ncol, 2 * B)], h->stream, d.gs_foff, d.gs_pos, d.f, d.gs_pool);
   if (forward) { phase(0); phase(1); tail(); }
   else { tail(); phase(1); phase(0); }
 }

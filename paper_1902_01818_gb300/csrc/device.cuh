@@ -48,19 +48,18 @@ struct XferMeta {
 // the split column lets C be the interior block of a 3D patch.
 // batch z adds z * sA, z * sB, z * sC.  tA, tB, tC: element type of A, B, C
 // (0 = double, 1 = float); the arithmetic type is the kernel's.
-// epi 0: C = acc; 1: C = acc / (sigma + lamM[m] + lamN0[n % nl0] + lamN1[n / nl0]);
-//     2: C += alpha * acc.
+// epi 0: C = acc; 1: C = acc dinv[m ldd + n] (dinv: the inverse eigenvalue
+//     sums of the fast diagonalisation, in the arithmetic type); 2: C += alpha acc.
 struct GemmTask {
   int M, N, K, transA, transB, batch, ndiv, epi;
   const void* A;
   const void* B;
   void* C;
   int64_t lda, ldb, ldc, nhi, sA, sB, sC;
-  double alpha, sigma;
-  const double* lamM;
-  const double* lamN0;
-  const double* lamN1;
-  int nl0, tA, tB, tC;
+  double alpha;
+  const void* dinv;
+  int64_t ldd;
+  int tA, tB, tC;
 };
 
 struct GemmItem {

@@ -12,6 +12,7 @@
 //   gs_sweep_coop   a whole multicolour Gauss-Seidel sweep, one cooperative launch (a4)
 //   dot / cg_*      deterministic reductions and vector updates of PCG (a8)
 #include <cstdio>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
@@ -220,79 +221,120 @@ __device__ __forceinline__ T ldt(const void* p, int64_t i, int t) {
 }
 
 // BM x BM output tile per CTA of 256 threads (16 x 16), each thread a
-// (BM/16) x (BM/16) micro-tile; Acc is the arithmetic type (double: the FP64
-// path, float: the FP32 path of the mixed-precision cycle).  In FP64 the FMA
-// pipe (2 DFMA/clk/SM on this part) is the bound, so BM = 32 (more tiles in
-// flight, less work on ragged edges); FP32 uses BM = 64 for reuse.
-template <int BM, typename Acc>
+// (BM/16) x (BM/16) micro-tile of rows ty T.. and columns tx T.. (T = BM/16);
+// Acc is the arithmetic type (double: the FP64 path, float: the FP32 path of
+// the mixed-precision cycle), TA / TB the element types of A / B in memory
+// (the first step of the FP32 path reads the FP64 residual).  K is consumed
+// in slabs of GBK, staged into shared memory by element-wise asynchronous
+// copies (zero-filled outside the matrix) through a ring of kGemmStages
+// slabs, so that the global-memory latency of slab k + 2 overlaps the FMAs of
+// slab k.  In FP64 the FMA pipe (2 DFMA/clk/SM on this part) is the bound, so
+// BM = 32 (more tiles in flight, less work on ragged edges); FP32 uses BM = 64
+// for reuse.
+constexpr int kGemmStages = 3;
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
+               "r"(valid ? BYTES : 0)
+               : "memory");
+}
+
+template <int BM, typename Acc, typename TA, typename TB>
 __global__ void __launch_bounds__(256) gemm_tiled(const GemmTask* __restrict__ tasks,
                                                   const GemmItem* __restrict__ items) {
   constexpr int T = BM / 16;
-  __shared__ Acc As[GBK][BM + 1];
-  __shared__ Acc Bs[GBK][BM + 1];
+  constexpr int PA = BM + 16 / (int)sizeof(TA);  // row pitches: 16-byte multiples
+  constexpr int PB = BM + 16 / (int)sizeof(TB);
+  constexpr bool CVT = !std::is_same<TA, Acc>::value;  // A converted once per slab into Ac
+  constexpr int PC = BM + 16 / (int)sizeof(Acc);
+  __shared__ __align__(16) TA As[kGemmStages][GBK][PA];
+  __shared__ __align__(16) TB Bs[kGemmStages][GBK][PB];
+  __shared__ __align__(16) Acc Ac[CVT ? 2 : 1][CVT ? GBK : 1][PC];
   const GemmItem it = items[blockIdx.x];
   const GemmTask g = tasks[it.task];
-  const int64_t oA = it.z * g.sA, oB = it.z * g.sB, oC = it.z * g.sC;
+  const TA* Ag = static_cast<const TA*>(g.A) + it.z * g.sA;
+  const TB* Bg = static_cast<const TB*>(g.B) + it.z * g.sB;
+  const int64_t oC = it.z * g.sC;
   const int m0 = it.tm * BM, n0 = it.tn * BM;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int nk = (g.K + GBK - 1) / GBK;
+  // this thread's elements of a slab: A element l at (mA + l dmA, kA + l dkA), B element l at (nB + l dnB, kB + l dkB)
+  int mA, kA, dmA, dkA, nB, kB, dnB, dkB;
+  if (g.transA) { mA = tid % BM; kA = tid / BM; dmA = 0; dkA = 256 / BM; }
+  else { kA = tid & 15; mA = tid >> 4; dmA = 16; dkA = 0; }
+  if (g.transB) { kB = tid & 15; nB = tid >> 4; dnB = 16; dkB = 0; }
+  else { nB = tid % BM; kB = tid / BM; dnB = 0; dkB = 256 / BM; }
+  const int64_t sAm = g.transA ? 1 : g.lda, sAk = g.transA ? g.lda : 1;
+  const int64_t sBn = g.transB ? g.ldb : 1, sBk = g.transB ? 1 : g.ldb;
+  auto load = [&](int s, int kt) {
+    const int k0 = kt * GBK;
+#pragma unroll
+    for (int l = 0; l < T; ++l) {
+      {
+        const int mm = mA + l * dmA, kk = kA + l * dkA;
+        const int m = m0 + mm, k = k0 + kk;
+        const bool ok = m < g.M && k < g.K;
+        cp_async_elem<sizeof(TA)>(&As[s][kk][mm], ok ? Ag + m * sAm + k * sAk : Ag, ok);
+      }
+      {
+        const int nn = nB + l * dnB, kk = kB + l * dkB;
+        const int n = n0 + nn, k = k0 + kk;
+        const bool ok = n < g.N && k < g.K;
+        cp_async_elem<sizeof(TB)>(&Bs[s][kk][nn], ok ? Bg + n * sBn + k * sBk : Bg, ok);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+#pragma unroll
+  for (int s = 0; s < kGemmStages - 1; ++s) {
+    if (s < nk) load(s, s);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   Acc acc[T][T];
 #pragma unroll
   for (int i = 0; i < T; ++i)
 #pragma unroll
     for (int j = 0; j < T; ++j) acc[i][j] = 0;
-  for (int k0 = 0; k0 < g.K; k0 += GBK) {
+  for (int kt = 0; kt < nk; ++kt) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kGemmStages - 2) : "memory");
+    const int s = kt % kGemmStages;
+    if constexpr (CVT) {  // this thread's own elements of slab kt have landed: convert them once
 #pragma unroll
-    for (int l = 0; l < T; ++l) {
-      const int e = tid + l * 256;  // 0 .. 16 BM - 1
-      {
-        int mm, kk;
-        if (g.transA) { mm = e % BM; kk = e / BM; } else { kk = e & 15; mm = e >> 4; }
-        const int m = m0 + mm, k = k0 + kk;
-        Acc v = 0;
-        if (m < g.M && k < g.K)
-          v = ldt<Acc>(g.A, oA + (g.transA ? (int64_t)k * g.lda + m : (int64_t)m * g.lda + k), g.tA);
-        As[kk][mm] = v;
-      }
-      {
-        int nn, kk;
-        if (g.transB) { kk = e & 15; nn = e >> 4; } else { nn = e % BM; kk = e / BM; }
-        const int n = n0 + nn, k = k0 + kk;
-        Acc v = 0;
-        if (n < g.N && k < g.K)
-          v = ldt<Acc>(g.B, oB + (g.transB ? (int64_t)n * g.ldb + k : (int64_t)k * g.ldb + n), g.tB);
-        Bs[kk][nn] = v;
+      for (int l = 0; l < T; ++l) {
+        const int mm = mA + l * dmA, kk = kA + l * dkA;
+        Ac[kt & 1][kk][mm] = (Acc)As[s][kk][mm];
       }
     }
-    __syncthreads();
+    __syncthreads();  // slab kt visible to all; slab kt - 1 no longer read
+    const int nxt = kt + kGemmStages - 1;
+    if (nxt < nk) load(nxt % kGemmStages, nxt);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll
     for (int kk = 0; kk < GBK; ++kk) {
       Acc a[T], b[T];
 #pragma unroll
-      for (int i = 0; i < T; ++i) a[i] = As[kk][ty * T + i];
+      for (int i = 0; i < T; ++i) a[i] = CVT ? (Acc)Ac[kt & 1][kk][ty * T + i] : (Acc)As[s][kk][ty * T + i];
 #pragma unroll
-      for (int j = 0; j < T; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < T; ++j) b[j] = (Acc)Bs[s][kk][tx * T + j];
 #pragma unroll
       for (int i = 0; i < T; ++i)
 #pragma unroll
         for (int j = 0; j < T; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
-    __syncthreads();
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < T; ++i) {
     const int m = m0 + ty * T + i;
     if (m >= g.M) continue;
 #pragma unroll
     for (int j = 0; j < T; ++j) {
-      const int n = n0 + tx + 16 * j;
+      const int n = n0 + tx * T + j;
       if (n >= g.N) continue;
       const int64_t ci = oC + (int64_t)m * g.ldc + gcol(g, n);
       Acc v = acc[i][j];
-      if (g.epi == 1) {
-        double den = g.sigma + g.lamM[m] + g.lamN0[n % g.nl0];
-        if (g.lamN1) den += g.lamN1[n / g.nl0];
-        v = (Acc)((double)v / den);
-      }
+      if (g.epi == 1) v *= static_cast<const Acc*>(g.dinv)[(int64_t)m * g.ldd + n];
       if (g.tC) {
         float* c = static_cast<float*>(g.C) + ci;
         *c = g.epi == 2 ? *c + (float)(g.alpha * v) : (float)v;
@@ -472,11 +514,7 @@ __global__ void __launch_bounds__(128) gemm_umma(const GemmTask* __restrict__ ta
           if (n >= g.N) continue;
           float acc = __uint_as_float(v[i]);
           const int64_t ci = oC + (int64_t)m * g.ldc + gcol(g, n);
-          if (g.epi == 1) {
-            double den = g.sigma + g.lamM[m] + g.lamN0[n % g.nl0];
-            if (g.lamN1) den += g.lamN1[n / g.nl0];
-            acc = (float)((double)acc / den);
-          }
+          if (g.epi == 1) acc *= static_cast<const float*>(g.dinv)[(int64_t)m * g.ldd + n];
           if (g.tC) {
             float* c = static_cast<float*>(g.C) + ci;
             *c = g.epi == 2 ? *c + (float)(g.alpha * acc) : acc;
@@ -1034,11 +1072,15 @@ cudaError_t prepare_gemm_umma() {
   return cudaFuncSetAttribute(gemm_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
 }
 
-void launch_gemm(int nitems, int arith, cudaStream_t st, const GemmTask* tasks, const GemmItem* items) {
-  if (nitems == 0) return;
+void launch_gemm(int nitems, int arith, int tA, cudaStream_t st, const GemmTask* tasks, const GemmItem* items) {
+  if (nitems <= 0) return;
   ++g_launches;
-  if (arith == 1) gemm_tiled<64, float><<<nitems, 256, 0, st>>>(tasks, items);
-  else gemm_tiled<32, double><<<nitems, 256, 0, st>>>(tasks, items);
+  if (arith == 1) {
+    if (tA == 0) gemm_tiled<64, float, double, float><<<nitems, 256, 0, st>>>(tasks, items);
+    else gemm_tiled<64, float, float, float><<<nitems, 256, 0, st>>>(tasks, items);
+  } else {
+    gemm_tiled<32, double, double, double><<<nitems, 256, 0, st>>>(tasks, items);
+  }
 }
 
 template <int D, int P>

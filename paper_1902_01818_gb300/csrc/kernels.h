@@ -75,7 +75,8 @@ void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const
                     double* u);
 // arith 0: FP64 arithmetic (32 x 32 tiles), 1: FP32 arithmetic (64 x 64 tiles)
 int gemm_tile(int arith);
-void launch_gemm(int nitems, int arith, cudaStream_t st, const GemmTask* tasks, const GemmItem* items);
+// tA: element type of A in the step (0 double, 1 float); B is of the arithmetic type
+void launch_gemm(int nitems, int arith, int tA, cudaStream_t st, const GemmTask* tasks, const GemmItem* items);
 // tensor-core tiles (128 x 64, items built with these tile sizes): kind 0 TF32, 1 BF16
 void launch_gemm_umma(int nitems, int kind, cudaStream_t st, const GemmTask* tasks, const GemmItem* items, int* err);
 cudaError_t prepare_gemm_umma();

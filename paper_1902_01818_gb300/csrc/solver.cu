@@ -104,6 +104,7 @@ struct DLevel {
   GemmTask* fd_tasks = nullptr;
   GemmItem* fd_items = nullptr;
   std::vector<std::pair<int, int>> fd_steps;  // item range per step
+  std::vector<int> fd_step_ta;                 // element type of A per step (0 double, 1 float)
   // pieces (interface pieces on levels >= 1, the coarse solve on level 0)
   PieceMeta* pieces = nullptr;
   PieceItem* piece_items = nullptr;
@@ -266,9 +267,9 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   std::vector<FDData> fd(L.K);
 #pragma omp parallel for schedule(dynamic)
   for (int k = 0; k < L.K; ++k) fd[k] = fd_setup(L, k, delta);
-  // U and lambda pool
-  Vec Upool, lampool;
-  std::vector<std::array<int64_t, 3>> uoff(L.K), loff(L.K);
+  // U pool
+  Vec Upool;
+  std::vector<std::array<int64_t, 3>> uoff(L.K);
   int64_t tsize = 0;
   std::vector<int64_t> toff(L.K);
   for (int k = 0; k < L.K; ++k) {
@@ -276,8 +277,6 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     for (int a = 0; a < d; ++a) {
       uoff[k][a] = (int64_t)Upool.size();
       Upool.insert(Upool.end(), fd[k].U[a].begin(), fd[k].U[a].end());
-      loff[k][a] = (int64_t)lampool.size();
-      lampool.insert(lampool.end(), fd[k].lam[a].begin(), fd[k].lam[a].end());
       sz *= fd[k].n[a];
     }
     toff[k] = tsize;
@@ -294,15 +293,37 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   } else {
     dU = reinterpret_cast<char*>(A.upload(Upool));
   }
-  double* dlam = A.upload(lampool);
+  // inverse eigenvalue sums 1 / (sigma + lambda_{d-1}[i_{d-1}] + .. + lambda_0[i_0]) in interior flat
+  // order (i_0 fastest), in the arithmetic type
+  Vec dinv((size_t)std::max<int64_t>(tsize, 1), 0.0);
+#pragma omp parallel for schedule(dynamic)
+  for (int k = 0; k < L.K; ++k) {
+    const int n0 = fd[k].n[0], n1 = fd[k].n[1], n2 = d == 3 ? fd[k].n[2] : 1;
+    for (int i2 = 0; i2 < n2; ++i2)
+      for (int i1 = 0; i1 < n1; ++i1)
+        for (int i0 = 0; i0 < n0; ++i0) {
+          double den = d == 2 ? fd[k].sigma + fd[k].lam[1][i1] + fd[k].lam[0][i0]
+                              : fd[k].sigma + fd[k].lam[2][i2] + fd[k].lam[0][i0] + fd[k].lam[1][i1];
+          dinv[(size_t)toff[k] + ((size_t)i2 * n1 + i1) * n0 + i0] = 1.0 / den;
+        }
+  }
+  char* dD;
+  if (f32) {
+    std::vector<float> df(dinv.begin(), dinv.end());
+    dD = reinterpret_cast<char*>(A.upload(df));
+  } else {
+    dD = reinterpret_cast<char*>(A.upload(dinv));
+  }
   char* T1 = reinterpret_cast<char*>(A.alloc<double>((size_t)std::max<int64_t>(tsize, 1)));
   char* T2 = reinterpret_cast<char*>(A.alloc<double>((size_t)std::max<int64_t>(tsize, 1)));
   const int tU = f32 ? 1 : 0;
   std::vector<GemmTask> tasks;
   std::vector<GemmItem> items;
   dl.fd_steps.clear();
+  dl.fd_step_ta.clear();
   auto add_step = [&](const std::vector<GemmTask>& st) {
     const int i0 = (int)items.size();
+    dl.fd_step_ta.push_back(st.empty() ? 0 : st[0].tA);  // one element type per step
     for (const auto& g : st) {
       const int id = (int)tasks.size();
       tasks.push_back(g);
@@ -322,9 +343,8 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     g.nhi = 0;
     g.sA = g.sB = g.sC = 0;
     g.alpha = 1.0;
-    g.sigma = 0.0;
-    g.lamM = g.lamN0 = g.lamN1 = nullptr;
-    g.nl0 = 1;
+    g.dinv = nullptr;
+    g.ldd = 0;
     g.tA = g.tB = g.tC = 0;
     return g;
   };
@@ -340,6 +360,7 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     const void* U2 = d == 3 ? dU + uoff[k][2] * esz : nullptr;
     void* Tk = T1 + toff[k] * esz;
     void* Xk = T2 + toff[k] * esz;
+    const void* Dk = dD + toff[k] * esz;
     GemmTask g{};
     // element types: U and temporaries tU; r (first input) and u (last output) double
     auto types = [&](GemmTask& t, int ta, int tb, int tc) { t.tA = ta; t.tB = tb; t.tC = tc; };
@@ -349,8 +370,8 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
       g.C = Tk; g.ldc = n0; g.ndiv = n0; types(g, 0, tU, tU); steps[0].push_back(g);
       // 2) X = U1^T T, divided by lambda1[m] + lambda0[n] + sigma
       g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.transA = 1; g.lda = n1; g.B = Tk; g.ldb = n0;
-      g.C = Xk; g.ldc = n0; g.ndiv = n0; g.epi = 1; g.sigma = fd[k].sigma; g.lamM = dlam + loff[k][1];
-      g.lamN0 = dlam + loff[k][0]; g.nl0 = n0; types(g, tU, tU, tU); steps[1].push_back(g);
+      g.C = Xk; g.ldc = n0; g.ndiv = n0; g.epi = 1; g.dinv = Dk; g.ldd = n0; types(g, tU, tU, tU);
+      steps[1].push_back(g);
       // 3) Y1 = X U0^T
       g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = Xk; g.lda = n0; g.B = U0; g.transB = 1; g.ldb = n0;
       g.C = Tk; g.ldc = n0; g.ndiv = n0; types(g, tU, tU, tU); steps[2].push_back(g);
@@ -367,8 +388,8 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
       g.sB = plane; g.C = Xk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; types(g, tU, tU, tU); steps[1].push_back(g);
       // 3) T = U2^T X  (n2 x n1 n0), divided by the eigenvalue sums
       g = base(g); g.M = n2; g.N = (int)plane; g.K = n2; g.A = U2; g.transA = 1; g.lda = n2; g.B = Xk; g.ldb = plane;
-      g.C = Tk; g.ldc = plane; g.ndiv = (int)plane; g.epi = 1; g.sigma = fd[k].sigma; g.lamM = dlam + loff[k][2];
-      g.lamN0 = dlam + loff[k][0]; g.lamN1 = dlam + loff[k][1]; g.nl0 = n0; types(g, tU, tU, tU); steps[2].push_back(g);
+      g.C = Tk; g.ldc = plane; g.ndiv = (int)plane; g.epi = 1; g.dinv = Dk; g.ldd = plane; types(g, tU, tU, tU);
+      steps[2].push_back(g);
       // 4) X = T U0^T  (n2 n1 x n0)
       g = base(g); g.M = n2 * n1; g.N = n0; g.K = n0; g.A = Tk; g.lda = n0; g.B = U0; g.transB = 1; g.ldb = n0;
       g.C = Xk; g.ldc = n0; g.ndiv = n0; types(g, tU, tU, tU); steps[3].push_back(g);
@@ -781,18 +802,18 @@ void matvec(mgiga_handle* h, int l, const double* u, double* out) {
 }
 
 // one step of the fast diagonalisation: SIMT tiles (FP64 / FP32) or tensor-core tiles (TF32 / BF16)
-void run_fd_step(mgiga_handle* h, DLevel& d, const std::pair<int, int>& s) {
+void run_fd_step(mgiga_handle* h, DLevel& d, size_t i) {
+  const auto& s = d.fd_steps[i];
   if (d.arith >= 2)
     launch_gemm_umma(s.second - s.first, d.arith - 2, h->stream, d.fd_tasks, d.fd_items + s.first, h->gs_err);
   else
-    launch_gemm(s.second - s.first, d.arith, h->stream, d.fd_tasks, d.fd_items + s.first);
+    launch_gemm(s.second - s.first, d.arith, d.fd_step_ta[i], h->stream, d.fd_tasks, d.fd_items + s.first);
 }
 
 // u += tau sum_T P_T L_T^{-1} P_T^T r  (Eq. Ldef), r in d.r
 void smooth(mgiga_handle* h, int l) {
   DLevel& d = h->D[l];
-  for (const auto& s : d.fd_steps)
-    run_fd_step(h, d, s);
+  for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
   launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r, d.u,
                h->opt.tau, 0);
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, d.u, nullptr, 2);
@@ -1551,8 +1572,7 @@ static void run_stage(mgiga_handle* h, int stage, int level) {
       launch_band(L.d, L.p, 1, d.ntiles, h->stream, d.tiles, d.patches, d.band, d.nloc, d.u, nullptr, d.r);
       break;
     case MGIGA_STAGE_FD:
-      for (const auto& s : d.fd_steps)
-        run_fd_step(h, d, s);
+      for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
       break;
     case MGIGA_STAGE_PIECES:
       launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r,

@@ -193,10 +193,15 @@ mgiga_status mgiga_solve_d(mgiga_handle* h, const double* rhs, double* u, double
  *   MGIGA_OP_GS_BWD     out = b + L^{-T}(a - A_l b)      (backward sweep)
  *   MGIGA_OP_RESTRICT   out = P_l^T a   (out on level l-1)
  *   MGIGA_OP_PROLONG    out = P_l a     (a on level l-1, out on level l)
- *   MGIGA_OP_COARSE     out = A_0^{-1} a  (level must be 0) */
+ *   MGIGA_OP_COARSE     out = A_0^{-1} a  (level must be 0)
+ *   MGIGA_OP_CYCLE_RESIDUAL  out = a - A_l b as the V-cycle computes it on
+ *                       level >= 1: with the FP32 band coefficients and FP32
+ *                       arithmetic (FP64 result) unless the precision is FP64;
+ *                       the error is bounded by FP32 rounding of the band sum */
 enum {
   MGIGA_OP_RESIDUAL = 0, MGIGA_OP_MATVEC = 1, MGIGA_OP_SMOOTH = 2, MGIGA_OP_GS_FWD = 3,
-  MGIGA_OP_GS_BWD = 4, MGIGA_OP_RESTRICT = 5, MGIGA_OP_PROLONG = 6, MGIGA_OP_COARSE = 7
+  MGIGA_OP_GS_BWD = 4, MGIGA_OP_RESTRICT = 5, MGIGA_OP_PROLONG = 6, MGIGA_OP_COARSE = 7,
+  MGIGA_OP_CYCLE_RESIDUAL = 8
 };
 mgiga_status mgiga_apply(mgiga_handle* h, int op, int level, const double* a, const double* b,
                          double* out);
@@ -236,9 +241,11 @@ mgiga_status mgiga_residual_noalloc_d(mgiga_handle* h, int level, const double* 
  * a stage on `level`, measured with CUDA events on the handle's stream over
  * `reps` back-to-back applications after one warm-up, on the handle's own
  * device buffers (their contents are overwritten).
- * mgiga_stage_work: algorithmic FP64 flops and HBM bytes of one application
+ * mgiga_stage_work: algorithmic flops and HBM bytes of one application
  * (BAND: 2 nnz(A_l) flops, 8 nnz(A_l) + 24 N_l bytes; FD: 4 d n per interior
- * DoF flops, 24 bytes per interior DoF; GS: as BAND). */
+ * DoF flops, 24 bytes per interior DoF; GS: as BAND, with 4 bytes per nonzero
+ * when the smoothers run in FP32 (precision other than FP64); RESIDUAL: as
+ * BAND, 4 bytes per nonzero on the mixed path). */
 enum {
   MGIGA_STAGE_BAND = 0,     /* band product A_l u (a1) */
   MGIGA_STAGE_FD = 1,       /* interior fast diagonalisation (a2) */
@@ -247,7 +254,9 @@ enum {
   MGIGA_STAGE_RESTRICT = 4, /* a5 */
   MGIGA_STAGE_PROLONG = 5,  /* a6 */
   MGIGA_STAGE_COARSE = 6,   /* a7 (level 0) */
-  MGIGA_STAGE_VCYCLE = 7    /* a whole cycle from `level` down */
+  MGIGA_STAGE_VCYCLE = 7,   /* a whole cycle from `level` down */
+  MGIGA_STAGE_RESIDUAL = 8  /* residual f - A u inside the cycle (level >= 1): FP32 band
+                               coefficients and arithmetic unless the precision is FP64 */
 };
 mgiga_status mgiga_kernel_launches(const mgiga_handle* h, long long* n);
 mgiga_status mgiga_time_stage(mgiga_handle* h, int stage, int level, int reps, double* ms);

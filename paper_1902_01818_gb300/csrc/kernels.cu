@@ -60,6 +60,72 @@ __global__ void __launch_bounds__(kTile) band_apply(const Tile* __restrict__ til
   else out[pos] = acc;
 }
 
+// a1 in FP32, for the residuals inside the mixed-precision cycle (they feed
+// the FP32 smoothers and the restriction): out = f - A u with FP32
+// coefficients band32[o * nloc + pos] and FP32 arithmetic, out in FP64.  A
+// row group is kRowsF32 consecutive rows of a tile; for every (o2, o1) line a
+// thread reads the W + kRowsF32 - 1 consecutive u values the group needs,
+// converts each once, and applies the W coefficients of each row.  G threads
+// share a group (lines j, j + G, ..; thread index = j 64 + group, so a warp
+// reads 32 consecutive groups), their sums added in a fixed order through
+// shared memory.  band32 carries kRowsF32 padding floats at its end; u has
+// zero guards.
+constexpr int kRowsF32 = 4;
+template <int D, int P, int G>
+__global__ void __launch_bounds__(kTile / kRowsF32 * G) band_residual_f32(const Tile* __restrict__ tiles,
+                                                                      const PatchMeta* __restrict__ patches,
+                                                                      const float* __restrict__ band32,
+                                                                      int64_t nloc, const double* __restrict__ u,
+                                                                      const double* __restrict__ f,
+                                                                      double* __restrict__ out) {
+  constexpr int NG = kTile / kRowsF32;  // row groups per tile
+  __shared__ float red[G > 1 ? G - 1 : 1][NG][kRowsF32];
+  const Tile t = tiles[blockIdx.x];
+  const int rg = threadIdx.x % NG, j = threadIdx.x / NG;
+  const int r0 = rg * kRowsF32;
+  const bool live = r0 < t.count;
+  const int64_t pos0 = t.start + (live ? r0 : 0);
+  const PatchMeta pm = patches[t.patch];
+  const int64_t s1 = pm.N[0], s2 = (int64_t)pm.N[0] * pm.N[1];
+  constexpr int W = 2 * P + 1;
+  constexpr int U = W + kRowsF32 - 1;
+  constexpr int NL = D == 3 ? W * W : W;  // (o2, o1) lines
+  float acc[kRowsF32];
+#pragma unroll
+  for (int q = 0; q < kRowsF32; ++q) acc[q] = 0.0f;
+  if (live) {
+    const float* b = band32 + pos0;
+    const double* uc = u + pos0;
+#pragma unroll 1
+    for (int line = j; line < NL; line += G) {
+      const int o1 = line % W, o2 = line / W;
+      const double* ur = uc + (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
+      float uf[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) uf[i] = (float)__ldg(ur + i);
+      const float* br = b + (int64_t)(line * W) * nloc;
+#pragma unroll
+      for (int o0 = 0; o0 < W; ++o0)
+#pragma unroll
+        for (int q = 0; q < kRowsF32; ++q) acc[q] = fmaf(__ldg(br + (int64_t)o0 * nloc + q), uf[q + o0], acc[q]);
+    }
+  }
+  if (G > 1) {
+    if (j > 0)
+#pragma unroll
+      for (int q = 0; q < kRowsF32; ++q) red[j - 1][rg][q] = acc[q];
+    __syncthreads();
+    if (j > 0) return;
+#pragma unroll
+    for (int jj = 0; jj < G - 1; ++jj)
+#pragma unroll
+      for (int q = 0; q < kRowsF32; ++q) acc[q] += red[jj][rg][q];
+  }
+  if (!live) return;
+  const int nq = min(kRowsF32, t.count - r0);
+  for (int q = 0; q < nq; ++q) out[pos0 + q] = f[pos0 + q] - (double)acc[q];
+}
+
 // a1': out[row] -= (MODE 0) or += (MODE 1) sum_j C[row, j] u[j]; a warp per row
 template <int MODE>
 __global__ void cross_apply(int nx, const int64_t* __restrict__ x_row, const int* __restrict__ x_ptr,
@@ -1018,6 +1084,31 @@ void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile
   } else {
     if (mode == 0) launch_band_p<3, 0>(p, ntiles, st, tiles, pm, band, nloc, u, f, out);
     else launch_band_p<3, 1>(p, ntiles, st, tiles, pm, band, nloc, u, f, out);
+  }
+}
+
+void launch_band_residual_f32(int d, int p, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
+                              const float* band32, int64_t nloc, const double* u, const double* f, double* out) {
+  if (ntiles == 0) return;
+  ++g_launches;
+  // four threads per row group unless the level alone fills the GPU with one
+  const bool split = nloc < 400000;
+  constexpr int NG = kTile / kRowsF32;
+  switch (p) {
+#define MG_LAUNCH(DD, PP, GG) \
+  band_residual_f32<DD, PP, GG><<<ntiles, NG * GG, 0, st>>>(tiles, pm, band32, nloc, u, f, out)
+#define MG_CASE(PP)                                                  \
+  case PP:                                                           \
+    if (d == 2) {                                                    \
+      if (split) MG_LAUNCH(2, PP, 4); else MG_LAUNCH(2, PP, 1);      \
+    } else {                                                         \
+      if (split) MG_LAUNCH(3, PP, 4); else MG_LAUNCH(3, PP, 1);      \
+    }                                                                \
+    break;
+    MG_CASE(1) MG_CASE(2) MG_CASE(3) MG_CASE(4) MG_CASE(5) MG_CASE(6) MG_CASE(7) MG_CASE(8)
+#undef MG_CASE
+#undef MG_LAUNCH
+    default: break;
   }
 }
 

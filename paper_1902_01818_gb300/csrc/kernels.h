@@ -63,6 +63,9 @@ void launch_gs_fill_phase(int e0, int n, cudaStream_t st, const int64_t* f_off, 
 
 void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
                  const double* band, int64_t nloc, const double* u, const double* f, double* out);
+// out = f - A u with FP32 coefficients (band32: nb x nloc + 4 floats) and FP32 arithmetic
+void launch_band_residual_f32(int d, int p, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
+                              const float* band32, int64_t nloc, const double* u, const double* f, double* out);
 void launch_cross(int mode, int nx, cudaStream_t st, const int64_t* x_row, const int* x_ptr, const int64_t* x_col,
                   const double* x_val, const double* u, double* out);
 void launch_shared(int nsh, cudaStream_t st, const int* sh_ptr, const int64_t* sh_pos, double* v, const double* f,

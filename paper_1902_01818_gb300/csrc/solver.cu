@@ -117,6 +117,7 @@ struct DLevel {
   int* gs_cls = nullptr;
   int* gs_x = nullptr;
   double* gs_band = nullptr;  // band rows of the owner copies in colour order
+  float* band32 = nullptr;    // FP32 band (mixed path): residuals inside the cycle
   int* gs_cptr_d = nullptr;
   int gs_blocks = 0;
   std::vector<int> gs_cptr;
@@ -793,6 +794,20 @@ void residual(mgiga_handle* h, int l, const double* u, const double* f, double* 
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, out, f, 0);
 }
 
+// residual inside the cycle: feeds the smoothers and the restriction, so on
+// the mixed path the band part runs with FP32 coefficients and arithmetic
+void cycle_residual(mgiga_handle* h, int l, const double* u, const double* f, double* out) {
+  const Level& L = h->L[l];
+  DLevel& d = h->D[l];
+  if (!d.band32) {
+    residual(h, l, u, f, out);
+    return;
+  }
+  launch_band_residual_f32(L.d, L.p, d.ntiles, h->stream, d.tiles, d.patches, d.band32, d.nloc, u, f, out);
+  launch_cross(0, d.nx, h->stream, d.x_row, d.x_ptr, d.x_col, d.x_val, u, out);
+  if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, out, f, 0);
+}
+
 void matvec(mgiga_handle* h, int l, const double* u, double* out) {
   const Level& L = h->L[l];
   DLevel& d = h->D[l];
@@ -916,20 +931,20 @@ void vcycle(mgiga_handle* h, int l) {
   if (sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID) {
     for (int i = 0; i < nu; ++i) {
       if (zero) CK(cudaMemcpyAsync(d.r, d.f, d.nloc * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-      else residual(h, l, d.u, d.f, d.r);
+      else cycle_residual(h, l, d.u, d.f, d.r);
       smooth(h, l);
       zero = false;
     }
   }
   for (int m = 0; m < std::max(1, h->opt.mu); ++m) {
-    residual(h, l, d.u, d.f, d.r);
+    cycle_residual(h, l, d.u, d.f, d.r);
     restrict_to(h, l, d.r);
     vcycle(h, l - 1);
     prolong_from(h, l, h->D[l - 1].u, d.u);
   }
   if (sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID) {
     for (int i = 0; i < nu; ++i) {
-      residual(h, l, d.u, d.f, d.r);
+      cycle_residual(h, l, d.u, d.f, d.r);
       smooth(h, l);
     }
   }
@@ -1160,6 +1175,11 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       d.f = A.guarded(L.nloc, d.guard);
       d.r = A.guarded(L.nloc, d.guard);
       d.band = A.upload(L.band);
+      if (d.arith >= 1 && l > 0) {  // FP32 copy for the residuals inside the mixed-precision cycle
+        std::vector<float> b32(L.band.size() + 4, 0.0f);
+        for (size_t i = 0; i < L.band.size(); ++i) b32[i] = (float)L.band[i];
+        d.band32 = A.upload(b32);
+      }
       std::vector<PatchMeta> pm(L.K);
       for (int k = 0; k < L.K; ++k) {
         pm[k].off = L.off[k];
@@ -1251,6 +1271,13 @@ static mgiga_status apply_impl(mgiga_handle* h, int op, int level, const double*
         launch_scatter(d.nloc, st, d.loc2glob, a, d.f);
         launch_scatter(d.nloc, st, d.loc2glob, b, d.u);
         residual(h, level, d.u, d.f, d.r);
+        launch_gather(d.ndof, st, d.owner, d.r, out);
+        break;
+      case MGIGA_OP_CYCLE_RESIDUAL:
+        if (level == 0) throw SetupError(MGIGA_EINVAL, "the cycle computes residuals on levels >= 1");
+        launch_scatter(d.nloc, st, d.loc2glob, a, d.f);
+        launch_scatter(d.nloc, st, d.loc2glob, b, d.u);
+        cycle_residual(h, level, d.u, d.f, d.r);
         launch_gather(d.ndof, st, d.owner, d.r, out);
         break;
       case MGIGA_OP_MATVEC:
@@ -1571,6 +1598,9 @@ static void run_stage(mgiga_handle* h, int stage, int level) {
     case MGIGA_STAGE_BAND:
       launch_band(L.d, L.p, 1, d.ntiles, h->stream, d.tiles, d.patches, d.band, d.nloc, d.u, nullptr, d.r);
       break;
+    case MGIGA_STAGE_RESIDUAL:
+      cycle_residual(h, level, d.u, d.f, d.r);
+      break;
     case MGIGA_STAGE_FD:
       for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
       break;
@@ -1595,7 +1625,7 @@ static bool stage_valid(const mgiga_handle* h, int stage, int level) {
     case MGIGA_STAGE_BAND: case MGIGA_STAGE_VCYCLE: return true;
     case MGIGA_STAGE_FD: case MGIGA_STAGE_PIECES: return scms && level >= 1;
     case MGIGA_STAGE_GS: return gs && level >= 1;
-    case MGIGA_STAGE_RESTRICT: case MGIGA_STAGE_PROLONG: return level >= 1;
+    case MGIGA_STAGE_RESTRICT: case MGIGA_STAGE_PROLONG: case MGIGA_STAGE_RESIDUAL: return level >= 1;
     case MGIGA_STAGE_COARSE: return level == 0;
     default: return false;
   }
@@ -1631,11 +1661,12 @@ mgiga_status mgiga_stage_work(const mgiga_handle* h, int stage, int level, doubl
   if (!stage_valid(h, stage, level)) return MGIGA_EINVAL;
   const Level& L = h->L[level];
   double fl = 0.0, by = 0.0;
-  if (stage == MGIGA_STAGE_BAND) {
+  if (stage == MGIGA_STAGE_BAND || stage == MGIGA_STAGE_RESIDUAL) {
+    // every nonzero once (FP32 coefficients for the residual of the mixed path), u and f read, out written
     double nnz = 0.0;
     for (double v : L.band) nnz += v != 0.0;
     fl = 2.0 * nnz;
-    by = 8.0 * nnz + 24.0 * (double)L.nloc;
+    by = (stage == MGIGA_STAGE_RESIDUAL && h->D[level].band32 ? 4.0 : 8.0) * nnz + 24.0 * (double)L.nloc;
   } else if (stage == MGIGA_STAGE_FD) {
     for (int k = 0; k < L.K; ++k) {
       double nint = 1.0, sum = 0.0;
@@ -1644,10 +1675,11 @@ mgiga_status mgiga_stage_work(const mgiga_handle* h, int stage, int level, doubl
       by += 24.0 * nint;
     }
   } else if (stage == MGIGA_STAGE_GS) {
+    // every nonzero once (FP32 coefficients on the mixed path), u read and written, f read
     double nnz = 0.0;
     for (double v : L.band) nnz += v != 0.0;
     fl = 2.0 * nnz;
-    by = 8.0 * nnz + 24.0 * (double)L.nloc;
+    by = (h->D[level].arith >= 1 ? 4.0 : 8.0) * nnz + 24.0 * (double)L.nloc;
   } else {
     return MGIGA_EINVAL;
   }

@@ -27,9 +27,10 @@ CONFORMING, SIPG = 0, 1
 SMOOTHER = {"scms": 0, "gs": 1, "hybrid": 2}
 OUTER = {"pcg": 0, "direct": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
-STAGE = {"band": 0, "fd": 1, "pieces": 2, "gs": 3, "restrict": 4, "prolong": 5, "coarse": 6, "vcycle": 7}
+STAGE = {"band": 0, "fd": 1, "pieces": 2, "gs": 3, "restrict": 4, "prolong": 5, "coarse": 6, "vcycle": 7,
+         "residual": 8}
 OP = {"residual": 0, "matvec": 1, "smooth": 2, "gs_fwd": 3, "gs_bwd": 4, "restrict": 5, "prolong": 6,
-      "coarse": 7}
+      "coarse": 7, "cycle_residual": 8}
 
 
 class MgigaError(RuntimeError):

@@ -95,3 +95,34 @@ def test_mixed_smoothers_match_fp64_to_their_rounding(name, precision):
             got = lib.apply(op, l, f, u)
             assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref - u), (l, op)
     lib.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_cycle_residual_within_fp32_rounding(name):
+    """The residual inside the mixed cycle (FP32 band, FP32 sums) against f - A u.
+
+    Row i sums m = copies x (2p+1)^d products of FP32-rounded coefficients and
+    FP32-rounded u; the standard bound for such a sum is
+    |fl(s) - s| <= gamma_{m+2} sum_j |a_ij| |u_j|, gamma_k = k u / (1 - k u),
+    u = 2^-24 (the SIPG cross-patch terms stay FP64).
+    """
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    lib = binding().Solver(prob, levels=levels, smoother="hybrid", precision="fp32", **opt)
+    orc = omg.Multigrid(prob, levels=levels, smoother="hybrid", **opt)
+    d, p = prob["dim"], prob["degree"]
+    copies = 2 ** d if prob["coupling"] == "conforming" else 1
+    m = copies * (2 * p + 1) ** d
+    unit = 2.0 ** -24
+    gamma = (m + 2) * unit / (1 - (m + 2) * unit)
+    rng = np.random.default_rng(11)
+    for l in range(1, levels):
+        A = orc.h["A"][l]
+        n = A.shape[0]
+        u, f = rng.standard_normal(n), rng.standard_normal(n)
+        ref = f - A @ u
+        got = lib.apply("cycle_residual", l, f, u)
+        bound = gamma * (abs(A) @ np.abs(u)) + 4 * 2.0 ** -53 * (np.abs(f) + abs(A) @ np.abs(u))
+        assert np.all(np.abs(got - ref) <= bound), (l, float(np.max(np.abs(got - ref) / bound)))
+        # FP64 precision keeps the FP64 residual
+    lib.close()

@@ -143,7 +143,8 @@ FDData fd_setup(const Level& L, int k, double delta);
 // dense matrix of A restricted to the given global DoFs (row-major)
 Vec restrict_dense(const Level& L, const std::vector<int>& dofs);
 // inverse of an SPD matrix through its Cholesky factor (throws ENOTSPD)
-Vec spd_inverse(const Vec& A, int n);
+// A^{-1} of the SPD n x n A (row-major); `par`: OpenMP inside (one large matrix at a time)
+Vec spd_inverse(const Vec& A, int n, bool par = false);
 // generalised eigenproblem K u = lambda M u, M SPD; U^T M U = I
 void gen_eig(const Vec& K, const Vec& M, int n, Vec& U, Vec& lam);
 

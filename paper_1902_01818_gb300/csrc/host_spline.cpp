@@ -224,49 +224,97 @@ void geo_eval(const Problem& pr, int k, const double* xi, double* X, double* J) 
 // dense linear algebra (row-major)
 // ---------------------------------------------------------------------------
 
-// Cholesky A = L L^T in place (lower triangle); false if a pivot is not positive
-static bool cholesky(Vec& A, int n) {
-  for (int j = 0; j < n; ++j) {
-    double s = A[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) s -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
-    if (!(s > 0.0)) return false;
-    const double ljj = std::sqrt(s);
-    A[(size_t)j * n + j] = ljj;
-    for (int i = j + 1; i < n; ++i) {
-      double v = A[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) v -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
-      A[(size_t)i * n + j] = v / ljj;
-    }
-  }
-  return true;
+// Cholesky A = L L^T in place (lower triangle); false if a pivot is not
+// positive.  Blocked left-looking: a panel of kChol columns is first updated
+// with all earlier columns (row dot products, the panel's rows stay in cache),
+// then factored column by column; rows run in parallel when `par`.
+constexpr int kChol = 64;
+
+// sum_k a[k] b[k] with eight independent partial sums (fixed order, vectorisable)
+static inline double dot8(const double* a, const double* b, int n) {
+  double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int k = 0;
+  for (; k + 8 <= n; k += 8)
+    for (int t = 0; t < 8; ++t) s[t] += a[k + t] * b[k + t];
+  double r = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+  for (; k < n; ++k) r += a[k] * b[k];
+  return r;
 }
 
-// W = L^{-1} for the lower-triangular L (row-major), by forward substitution
-static Vec lower_inverse(const Vec& L, int n) {
-  Vec W((size_t)n * n, 0.0);
-  for (int c = 0; c < n; ++c) {
-    for (int i = c; i < n; ++i) {
-      double v = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) v -= L[(size_t)i * n + k] * W[(size_t)k * n + c];
-      W[(size_t)i * n + c] = v / L[(size_t)i * n + i];
+static bool cholesky(Vec& A, int n, bool par = false) {
+  bool ok = true;
+  for (int jb = 0; jb < n && ok; jb += kChol) {
+    const int je = std::min(n, jb + kChol);
+    if (jb > 0) {
+#pragma omp parallel for schedule(static) if (par && n - jb > 128)
+      for (int i = jb; i < n; ++i) {
+        double* ri = &A[(size_t)i * n];
+        const int jmax = std::min(je, i + 1);
+        for (int j = jb; j < jmax; ++j) ri[j] -= dot8(ri, &A[(size_t)j * n], jb);
+      }
+    }
+    for (int j = jb; j < je; ++j) {
+      double* rj = &A[(size_t)j * n];
+      const double s = rj[j] - dot8(rj + jb, rj + jb, j - jb);
+      if (!(s > 0.0)) { ok = false; break; }
+      const double ljj = std::sqrt(s);
+      rj[j] = ljj;
+#pragma omp parallel for schedule(static) if (par && n - j > 256)
+      for (int i = j + 1; i < n; ++i) {
+        double* ri = &A[(size_t)i * n];
+        ri[j] = (ri[j] - dot8(ri + jb, rj + jb, j - jb)) / ljj;
+      }
     }
   }
-  return W;
+  return ok;
 }
 
-Vec spd_inverse(const Vec& A, int n) {
+// Wt = (L^{-1})^T for the lower-triangular L (row-major): row c of Wt is
+// column c of L^{-1}, by forward substitution.  Columns are solved kInvCols at
+// a time so that each row of L is read once per group (in parallel over
+// groups when `par`).
+constexpr int kInvCols = 64;
+
+static Vec lower_inverse_t(const Vec& L, int n, bool par = false) {
+  Vec Wt((size_t)n * n, 0.0);
+  const int ngroups = (n + kInvCols - 1) / kInvCols;
+#pragma omp parallel for schedule(dynamic) if (par && n > 256)
+  for (int g = 0; g < ngroups; ++g) {
+    const int c0 = g * kInvCols, c1 = std::min(n, c0 + kInvCols);
+    for (int i = c0; i < n; ++i) {
+      const double* li = &L[(size_t)i * n];
+      for (int c = c0; c < std::min(c1, i + 1); ++c) {
+        double* w = &Wt[(size_t)c * n];
+        w[i] = ((i == c ? 1.0 : 0.0) - dot8(li + c, w + c, i - c)) / li[i];
+      }
+    }
+  }
+  return Wt;
+}
+
+// A^{-1} = L^{-T} L^{-1} = W^T W for the SPD A; the factorisation and the
+// products run in parallel (OpenMP) when `par` -- for large pieces processed
+// one at a time
+Vec spd_inverse(const Vec& A, int n, bool par) {
   Vec L = A;
-  if (!cholesky(L, n)) throw SetupError(4, "Cholesky factorisation broke down (matrix not SPD)");
-  const Vec W = lower_inverse(L, n);
-  // A^{-1} = W^T W
+  if (!cholesky(L, n, par)) throw SetupError(4, "Cholesky factorisation broke down (matrix not SPD)");
+  const Vec Wt = lower_inverse_t(L, n, par);
+  // Z[i][j] = sum_{k >= max(i, j)} Wt[i][k] Wt[j][k], j <= i; a block of kInvCols rows i stays
+  // in cache while every row j is read once per block
   Vec Z((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j <= i; ++j) {
-      double s = 0.0;
-      for (int k = i; k < n; ++k) s += W[(size_t)k * n + i] * W[(size_t)k * n + j];
-      Z[(size_t)i * n + j] = s;
-      Z[(size_t)j * n + i] = s;
+  const int nblk = (n + kInvCols - 1) / kInvCols;
+#pragma omp parallel for schedule(dynamic) if (par && n > 256)
+  for (int b = 0; b < nblk; ++b) {
+    const int i0 = b * kInvCols, i1 = std::min(n, i0 + kInvCols);
+    for (int j = 0; j < i1; ++j) {
+      const double* wj = &Wt[(size_t)j * n];
+      for (int i = std::max(i0, j); i < i1; ++i) {
+        const double s = dot8(&Wt[(size_t)i * n] + i, wj + i, n - i);
+        Z[(size_t)i * n + j] = s;
+        Z[(size_t)j * n + i] = s;
+      }
     }
+  }
   return Z;
 }
 
@@ -275,7 +323,10 @@ Vec spd_inverse(const Vec& A, int n) {
 void gen_eig(const Vec& K, const Vec& M, int n, Vec& U, Vec& lam) {
   Vec L = M;
   if (!cholesky(L, n)) throw SetupError(4, "mass matrix not SPD");
-  const Vec W = lower_inverse(L, n);
+  const Vec Wt = lower_inverse_t(L, n);
+  Vec W((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) W[(size_t)i * n + j] = Wt[(size_t)j * n + i];
   // C = W K W^T
   Vec T((size_t)n * n, 0.0), C((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i)

@@ -419,13 +419,25 @@ void build_pieces(const std::vector<Piece>& pcs, const Level& L, Arena& A, DLeve
   Z.resize(use.size());
   int err = 0;
   std::string msg;
+  // small pieces side by side, large ones one at a time with the threads inside the factorisation
+  constexpr int kLargePiece = 1024;
 #pragma omp parallel for schedule(dynamic)
   for (int i = 0; i < (int)use.size(); ++i) {
+    if ((int)use[i]->dofs.size() >= kLargePiece) continue;
     try {
       Z[i] = spd_inverse(restrict_dense(L, use[i]->dofs), (int)use[i]->dofs.size());
     } catch (const SetupError& e) {
 #pragma omp critical
       { err = e.status; msg = e.what(); }
+    }
+  }
+  for (int i = 0; i < (int)use.size() && !err; ++i) {
+    if ((int)use[i]->dofs.size() < kLargePiece) continue;
+    try {
+      Z[i] = spd_inverse(restrict_dense(L, use[i]->dofs), (int)use[i]->dofs.size(), true);
+    } catch (const SetupError& e) {
+      err = e.status;
+      msg = e.what();
     }
   }
   if (err) throw SetupError(err, msg);

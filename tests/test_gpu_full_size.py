@@ -1,0 +1,93 @@
+"""Full-size runs of the benchmark layout (2D SIPG 3x3, 192/288 intervals) and
+of the 3D cube (2x2x2 patches, 48 intervals), in the launch configuration the
+benchmark times (automatic levels, hybrid smoother, V-cycle-preconditioned CG).
+
+At these sizes the oracle does not solve; it supplies what it computes point
+by point: the DoF numbering (integer work, bit-exact against the library), the
+B-spline basis and the geometry map at sampled parameter points.  The library's
+solution must
+  (a) meet the FP64 stopping rule ||f - A u|| <= 1e-8 ||f|| (A u by the FP64
+      band product, itself pinned element by element at small sizes),
+  (b) agree with the exact solution prod sin(pi x_a) of the manufactured
+      problem at sampled points within the discretisation error
+      (~ (pi h)^{p+1}, here far below the 1e-4 bound; a wrong solution is off
+      by O(1)), and
+  (c) on the mixed paths take at most a few more iterations than FP64.
+"""
+import numpy as np
+import pytest
+
+from oracle import bspline, discretize, geometry
+from paper_1902_01818_gb300 import workloads as W
+from lib_fixture import binding
+
+pytestmark = pytest.mark.gpu
+
+
+def _sample_error(prob, lib, u, npts=6, seed=7):
+    """max |u_h - u| over npts random parameter points in every patch."""
+    d, p = prob["dim"], prob["degree"]
+    knots = prob["knots"]
+    patch, local = lib.dof_map()
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    shapes = [discretize.shape_of(kn, p) for kn in knots]
+    coeffs = [np.zeros(int(np.prod(s))) for s in shapes]
+    for g in range(len(u)):  # owner copies; conforming copies are filled below
+        coeffs[patch[g]][local[g]] = u[g]
+    if prob["coupling"] == "conforming":
+        num = discretize.numbering(prob, knots)
+        coeffs = discretize.global_to_local_vectors(num, u)
+    for k in range(len(knots)):
+        xi = rng.uniform(0.05, 0.95, size=(npts, d))
+        uh = discretize.evaluate(prob, knots, coeffs[k], k, xi)
+        X, _ = geometry.eval_points(prob["geo_degree"], prob["geo_knots"][k], prob["geo_ctrl"][k], xi)
+        worst = max(worst, float(np.max(np.abs(uh - W.exact_sinprod(X)))))
+    return worst
+
+
+def _numbering_matches(prob, lib):
+    num = discretize.numbering(prob, prob["knots"])
+    patch, local = lib.dof_map()
+    assert lib.ndof() == num["ndof"]
+    owner = np.array(num["owner"])
+    assert np.array_equal(patch, owner[:, 0]) and np.array_equal(local, owner[:, 1])
+
+
+def _solve(prob, opts, precision):
+    lib = binding().Solver(prob, levels=opts.get("levels", 0), smoother=opts["smoother"], tau=opts["tau"],
+                           delta=opts["delta"], precision=precision)
+    f = lib.load_sinprod()
+    u, it, rel, st = lib.solve(f, tol=1e-8)
+    r = f - lib.apply("matvec", -1, u)
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(f) * 1.0001, (precision, np.linalg.norm(r) / np.linalg.norm(f))
+    return lib, u, it
+
+
+@pytest.mark.parametrize("p", [2, 6])
+def test_benchmark_layout_full_size(p):
+    prob, opts = W.sipg_3x3(p, scale=3, smoother="hybrid")
+    lib64, u64, it64 = _solve(prob, opts, "fp64")
+    _numbering_matches(prob, lib64)
+    assert lib64.ndof() > 500_000
+    assert _sample_error(prob, lib64, u64) <= 1e-4
+    lib64.close()
+    lib32, u32, it32 = _solve(prob, opts, "fp32")
+    assert it32 <= it64 + 2, (it32, it64)
+    assert _sample_error(prob, lib32, u32) <= 1e-4
+    lib32.close()
+
+
+@pytest.mark.parametrize("coupling", ["conforming", "sipg"])
+def test_cube_full_size(coupling):
+    prob, opts = W.cube_2x2x2(3, coupling)
+    lib64, u64, it64 = _solve(prob, opts, "fp64")
+    _numbering_matches(prob, lib64)
+    assert lib64.ndof() > 900_000
+    assert _sample_error(prob, lib64, u64, npts=4) <= 1e-4
+    lib64.close()
+    for prec, extra in (("tf32", 3), ("bf16", 6)):
+        lib, u, it = _solve(prob, opts, prec)
+        assert it <= it64 + extra, (prec, it, it64)
+        assert _sample_error(prob, lib, u, npts=4) <= 1e-4
+        lib.close()

@@ -599,32 +599,35 @@ __global__ void __launch_bounds__(128) gemm_umma(const GemmTask* __restrict__ ta
 
 // ---------------------------------------------------------------------------
 // a3 / a7: dense solves with precomputed inverses, z = Z r_T, u_T += tau z
-// (mode 0) or u_T = z (mode 1)
+// (mode 0) or u_T = z (mode 1).  T: element type of Z and of the arithmetic
+// (double; float for the interface pieces of the mixed-precision smoother).
 // ---------------------------------------------------------------------------
 constexpr int kPieceRows = 64;
 
+template <typename T>
 __global__ void __launch_bounds__(256) piece_apply(const PieceItem* __restrict__ items,
                                                    const PieceMeta* __restrict__ pieces,
-                                                   const double* __restrict__ zpool,
+                                                   const T* __restrict__ zpool,
                                                    const int64_t* __restrict__ piece_pos,
                                                    const double* __restrict__ r, double* __restrict__ u,
                                                    double tau, int mode) {
-  extern __shared__ double rs[];
+  extern __shared__ __align__(16) unsigned char piece_smem[];
+  T* rs = reinterpret_cast<T*>(piece_smem);
   const PieceItem it = items[blockIdx.x];
   const PieceMeta pm = pieces[it.piece];
   const int64_t* pp = piece_pos + pm.dof_off;
-  for (int i = threadIdx.x; i < pm.n; i += blockDim.x) rs[i] = r[pp[i]];
+  for (int i = threadIdx.x; i < pm.n; i += blockDim.x) rs[i] = (T)r[pp[i]];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rend = min(pm.n, it.row0 + kPieceRows);
   for (int row = it.row0 + warp; row < rend; row += 8) {
-    const double* z = zpool + pm.z_off + (int64_t)row * pm.n;
-    double s = 0.0;
+    const T* z = zpool + pm.z_off + (int64_t)row * pm.n;
+    T s = 0;
     for (int j = lane; j < pm.n; j += 32) s = fma(z[j], rs[j], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
-      if (mode == 0) u[pp[row]] += tau * s;
-      else u[pp[row]] = s;
+      if (mode == 0) u[pp[row]] += tau * (double)s;
+      else u[pp[row]] = (double)s;
     }
   }
 }
@@ -769,11 +772,11 @@ __global__ void __launch_bounds__(256) gs_sweep_coop(GsSweepArgs a) {
 // shared memory, with zero rows beyond the patch and zero guards at both
 // ends, so that every band neighbour of a row is a plain shared-memory read
 // (off-patch columns have zero coefficients).  For every colour the CTA's
-// rows come as one contiguous block -- FP32 coefficients [o][row], the packed
-// slab position, f minus the couplings to the other parity (written by
-// gs_fill_phase before the launch) and the inverse diagonal; consecutive
-// blocks are fetched together as one bulk asynchronous copy ("chunk"), two
-// chunk buffers in flight, mbarrier completion.  Colours are separated by the
+// rows come as one or more contiguous blocks ("items") -- FP32 coefficients
+// [o][row], the packed slab position, f minus the couplings to the other
+// parity (written by gs_fill_phase before the launch) and the inverse
+// diagonal; consecutive items are fetched together as one bulk asynchronous
+// copy ("chunk"), two chunk buffers in flight, mbarrier completion.  Colours are separated by the
 // CTA barrier (one CTA per patch) or the hardware cluster barrier.
 // Every wait on an mbarrier is bounded: on expiry the CTA records the error,
 // stops computing and keeps taking part in the barriers.
@@ -803,17 +806,18 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
   float* us = reinterpret_cast<float*>(smem);
   unsigned char* const buf0 = smem + a.off_buf;
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + a.off_mbar);
-  int4* cm = reinterpret_cast<int4*>(smem + a.off_meta);  // per colour: rows, chunk, offset in chunk, Rp
-  int4* ch = cm + a.base;                                  // per chunk: byte offset (lo, hi), bytes, -
+  int4* cm = reinterpret_cast<int4*>(smem + a.off_meta);  // per item: rows, chunk, offset in chunk, Rp | end flag
+  int4* ch = cm + a.max_items;                             // per chunk: byte offset (lo, hi), bytes, -
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
-  const int nc = a.c_end - a.c_begin;
   const int dir = a.forward ? 0 : 1;
   const int ph = a.c_begin / a.base;
-  const int64_t reg = ((((int64_t)dir * 2 + ph) * a.K + k) * cs + r) * a.base;
+  const int64_t reg = (((int64_t)dir * 2 + ph) * a.K + k) * cs + r;
+  const int64_t ibase = a.item_ptr[reg];
+  const int nc = (int)(a.item_ptr[reg + 1] - ibase);  // items (sub-blocks of colours) in sweep order
   for (int i = tid; i < nc; i += nthr) {
-    cm[i] = a.cmeta[reg + i];
-    ch[i] = a.chunks[reg + i];
+    cm[i] = a.cmeta[ibase + i];
+    ch[i] = a.chunks[ibase + i];
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
@@ -879,7 +883,7 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
   bool ok = true;
   int cur = -1;
   for (int ci = 0; ci < nc; ++ci) {
-    const int4 m = cm[ci];  // rows, chunk, offset in chunk, Rp
+    const int4 m = cm[ci];  // rows, chunk, offset in chunk, Rp | (last item of its colour) << 30
     const int b = nbuf == 1 ? 0 : (m.y & 1);
     if (m.y != cur) {  // first colour of chunk m.y
       cur = m.y;
@@ -891,7 +895,7 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
       // the other buffer held chunk m.y - 1, released by the barrier that ended its last colour
       if (tid == 0 && ok && nbuf == 2 && m.y >= 1 && m.y + 1 < nchunk) copy(m.y + 1);
     }
-    const int R = m.x, Rp = m.w;
+    const int R = m.x, Rp = m.w & ((1 << 30) - 1);
     const float* coef = reinterpret_cast<const float*>(buf0 + (size_t)b * a.cap + m.z);
     const int* lidx = reinterpret_cast<const int*>(coef + NB * Rp);
     const float* fv = reinterpret_cast<const float*>(lidx + Rp);
@@ -934,7 +938,7 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
         }
       }
     }
-    sync_all();
+    if (m.w >> 30) sync_all();  // rows of one colour never couple: a barrier after its last item only
   }
   // the slab back to global memory
   double* ug = a.u + pm.off;
@@ -1279,16 +1283,25 @@ void launch_gs_fill_phase(int e0, int n, cudaStream_t st, const int64_t* f_off, 
 }
 
 void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,
-                  const double* zpool, const int64_t* piece_pos, const double* r, double* u, double tau, int mode) {
+                  const void* zpool, bool zf32, const int64_t* piece_pos, const double* r, double* u, double tau,
+                  int mode) {
   if (nitems == 0) return;
   ++g_launches;
-  piece_apply<<<nitems, 256, (size_t)max_n * sizeof(double), st>>>(items, pieces, zpool, piece_pos, r, u, tau, mode);
+  if (zf32)
+    piece_apply<float><<<nitems, 256, (size_t)max_n * sizeof(float), st>>>(
+        items, pieces, static_cast<const float*>(zpool), piece_pos, r, u, tau, mode);
+  else
+    piece_apply<double><<<nitems, 256, (size_t)max_n * sizeof(double), st>>>(
+        items, pieces, static_cast<const double*>(zpool), piece_pos, r, u, tau, mode);
 }
 
 cudaError_t prepare_piece_kernel(int max_n) {
   const size_t bytes = (size_t)max_n * sizeof(double);
-  if (bytes > 48 * 1024)
-    return cudaFuncSetAttribute(piece_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(piece_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(piece_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
   return cudaSuccess;
 }
 

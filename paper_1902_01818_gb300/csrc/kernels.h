@@ -46,11 +46,14 @@ struct GsStagedArgs {
   const int* slab;              // slab height (slow indices) per patch
   const int* pitch;             // shared-memory stride of a slow index per patch (>= its plane)
   const int* guard;             // zero floats before and after a CTA's extended slab, per patch
-  const unsigned char* pool;    // colour blocks, ordered by (phase, k, r, colour)
-  // per (direction, phase, k, r) = ((dir 2 + phase) K + k) csize + r, times base, in sweep order:
-  const int4* cmeta;            //   per colour: rows, chunk, byte offset in the chunk, padded rows Rp
-  const int4* chunks;           //   per chunk: byte offset in the pool (low, high word), bytes, -
-  int off_buf, off_mbar, off_meta;  // shared-memory layout (u slab at 0; 2 mbarriers; 32 B x base of meta)
+  const unsigned char* pool;    // item blocks, ordered by (phase, k, r, colour, item)
+  // per region (direction, phase, k, r) = ((dir 2 + phase) K + k) csize + r, entries
+  // [item_ptr[region], item_ptr[region + 1]), in sweep order:
+  const int64_t* item_ptr;
+  const int4* cmeta;            //   per item: rows, chunk, byte offset in the chunk, Rp | (last of its colour) << 30
+  const int4* chunks;           //   per chunk (indexed like the items): pool offset (low, high word), bytes, -
+  int max_items;                // most items of a region (shared-memory meta: 32 B each)
+  int off_buf, off_mbar, off_meta;  // shared-memory layout (u slab at 0; 2 mbarriers; meta)
   const PatchMeta* patches;
   double* u;
   int* err;
@@ -83,8 +86,10 @@ void launch_gemm(int nitems, int arith, int tA, cudaStream_t st, const GemmTask*
 // tensor-core tiles (128 x 64, items built with these tile sizes): kind 0 TF32, 1 BF16
 void launch_gemm_umma(int nitems, int kind, cudaStream_t st, const GemmTask* tasks, const GemmItem* items, int* err);
 cudaError_t prepare_gemm_umma();
+// zpool: double, or float when zf32 (the interface pieces of the mixed-precision smoother)
 void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,
-                  const double* zpool, const int64_t* piece_pos, const double* r, double* u, double tau, int mode);
+                  const void* zpool, bool zf32, const int64_t* piece_pos, const double* r, double* u, double tau,
+                  int mode);
 cudaError_t prepare_piece_kernel(int max_n);
 void launch_dot(int64_t n, cudaStream_t st, const double* a, const double* b, const double* w, double* partials,
                 double* scal, unsigned int* counter, int slot, int op);

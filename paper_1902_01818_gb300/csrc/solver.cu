@@ -109,7 +109,8 @@ struct DLevel {
   PieceMeta* pieces = nullptr;
   PieceItem* piece_items = nullptr;
   int npiece_items = 0, piece_max_n = 0;
-  double* zpool = nullptr;
+  void* zpool = nullptr;         // dense inverses: double, or float (zpool_f32) for the pieces of the mixed path
+  bool zpool_f32 = false;
   int64_t* piece_pos = nullptr;
   // Gauss-Seidel
   int64_t* gs_pos = nullptr;
@@ -461,20 +462,28 @@ void build_pieces(const std::vector<Piece>& pcs, const Level& L, Arena& A, DLeve
   dl.piece_items = A.upload(items);
   dl.npiece_items = (int)items.size();
   dl.piece_max_n = maxn;
-  dl.zpool = A.upload(zpool);
+  // the coarse solve stays FP64; the interface pieces of the mixed-precision smoother run in FP32
+  dl.zpool_f32 = !coarse && dl.arith >= 1;
+  if (dl.zpool_f32) {
+    std::vector<float> zf(zpool.begin(), zpool.end());
+    dl.zpool = A.upload(zf);
+  } else {
+    dl.zpool = A.upload(zpool);
+  }
   dl.piece_pos = A.upload(pos);
   if (maxn > 0) CK(prepare_piece_kernel(maxn));
 }
 
 // Colour blocks of the staged patch-parallel sweep (mixed path).  A group is
-// (base colour c, patch k, slab r of the patch's cluster); its block holds
-// float coef[o][Rp], int lidx[Rp] ((slow index - slab start) << 20 | index in
-// the plane), float f[Rp] (f minus the couplings to the other parity, written
-// before each phase) and float dinv[Rp] (1 / diagonal), padded to 16 bytes.
-// Rp >= rows and the shared-memory pitch of a slow index are chosen so that
-// the threads of a warp read distinct banks.  Blocks are ordered by (phase,
-// k, r, colour); runs of consecutive colours (in sweep order) that fit one
-// buffer are fetched as one chunk.
+// (base colour c, patch k, slab r of the patch's cluster); its rows are split
+// into as few items as keep two item buffers in shared memory, each item a
+// block of float coef[o][Rp], int lidx[Rp] ((slow index - slab start) << 20 |
+// index in the plane), float f[Rp] (f minus the couplings to the other parity,
+// written before each phase) and float dinv[Rp] (1 / diagonal), padded to 16
+// bytes.  Rp >= rows and the shared-memory pitch of a slow index are chosen so
+// that the threads of a warp read distinct banks.  Items are ordered by
+// (phase, k, r, colour, item); runs of consecutive items (in sweep order) that
+// fit one buffer are fetched as one chunk.
 void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl,
                      const std::vector<int>& order, const std::vector<int64_t>& gpos, const std::vector<int>& gpatch,
                      int ncol, int B) {
@@ -500,12 +509,18 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
     return worst;
   };
   const int64_t limit = 225 * 1024;
+  auto item_bytes = [&](int rp) { return ((int64_t)(nb + 3) * rp * 4 + 15) / 16 * 16; };
   struct Plan {
-    int cs = 0, threads = 0, tpr = 0, nbuf = 0;
+    int cs = 0, threads = 0, tpr = 0, nbuf = 0, max_items = 0;
     int64_t cap = 0, total = 0;
     int off_buf = 0, off_mbar = 0, off_meta = 0;
-    std::vector<int> slab, pitch, guard, grp_of, rows, rp;
-    std::vector<int64_t> bytes;
+    std::vector<int> slab, pitch, guard, grp_of, rows, nsub, rp_deg;
+    int rp_best = 0;
+    int rp_of(int x) const {  // padded rows: smallest Rp >= x with the fewest bank conflicts
+      if (x <= 0) return 0;
+      while (rp_deg[x % 32] != rp_best) ++x;
+      return x;
+    }
   };
   auto plan_for = [&](int cs, Plan& pl) -> bool {
     pl.cs = cs;
@@ -548,19 +563,11 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
     }
     const int tpr = pl.tpr;
     // padded rows: coefficient line q of row j is word q W Rp + j
-    int rp_deg[32], rp_best = 1 << 30;
+    pl.rp_deg.assign(32, 0);
+    pl.rp_best = 1 << 30;
     for (int x = 0; x < 32; ++x) {
-      rp_deg[x] = bank_degree(tpr, [&](int j, int q) { return q * W * x + j; });
-      rp_best = std::min(rp_best, rp_deg[x]);
-    }
-    pl.rp.assign(ngrp, 0);
-    pl.bytes.assign(ngrp, 0);
-    for (int g = 0; g < ngrp; ++g) {
-      int x = pl.rows[g];
-      if (x > 0)
-        while (rp_deg[x % 32] != rp_best) ++x;
-      pl.rp[g] = x;
-      pl.bytes[g] = ((int64_t)(nb + 3) * x * 4 + 15) / 16 * 16;
+      pl.rp_deg[x] = bank_degree(tpr, [&](int j, int q) { return q * W * x + j; });
+      pl.rp_best = std::min(pl.rp_best, pl.rp_deg[x]);
     }
     // slab pitch and guards; the extended slab
     int64_t ext = 0;
@@ -579,42 +586,68 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
       pl.guard[k] = ((d == 2 ? P : P * N0 + P) + 3) / 4 * 4;
       ext = std::max<int64_t>(ext, 2 * pl.guard[k] + (int64_t)(pl.slab[k] + 2 * P) * bp);
     }
+    pl.off_buf = (int)((ext * 4 + 127) / 128 * 128);
+    // whole phase regions resident (one buffer, no splitting) if they fit
     std::vector<int64_t> region((size_t)2 * K * cs, 0);
-    int64_t max_block = 0, max_region = 0;
     for (int g = 0; g < ngrp; ++g) {
       const int c = g / (K * cs), kr = g % (K * cs);
-      region[(size_t)(c / B) * K * cs + kr] += pl.bytes[g];
-      max_block = std::max(max_block, pl.bytes[g]);
+      region[(size_t)(c / B) * K * cs + kr] += item_bytes(pl.rp_of(pl.rows[g]));
     }
+    int64_t max_region = 0;
     for (int64_t v : region) max_region = std::max(max_region, v);
-    pl.off_buf = (int)((ext * 4 + 127) / 128 * 128);
-    const int64_t fixed = pl.off_buf + 16 + 32 * (int64_t)B + 16;
-    const int64_t avail = limit - fixed;
-    if (max_region <= avail) {
+    pl.nsub.assign(ngrp, 1);
+    const int64_t resident_room = limit - pl.off_buf - 16 - 32 * (int64_t)B;
+    if (max_region <= resident_room) {
       pl.nbuf = 1;
       pl.cap = (max_region + 15) / 16 * 16;
+      pl.max_items = B;
     } else {
+      // two buffers; groups larger than a buffer split into near-equal items
       pl.nbuf = 2;
-      pl.cap = avail / 2 / 16 * 16;
-      if (pl.cap < max_block) return false;
+      for (int extra = 1; extra <= 8; extra *= 2) {  // meta room for up to extra x B items
+        const int64_t cap = (limit - pl.off_buf - 16 - 32 * (int64_t)B * extra) / 2 / 16 * 16;
+        int rmax = 0;
+        while (item_bytes(pl.rp_of(rmax + 1)) <= cap) ++rmax;
+        if (rmax < 1) return false;
+        std::vector<int> items((size_t)2 * K * cs, 0);
+        for (int g = 0; g < ngrp; ++g) {
+          pl.nsub[g] = std::max(1, (pl.rows[g] + rmax - 1) / rmax);
+          const int c = g / (K * cs), kr = g % (K * cs);
+          items[(size_t)(c / B) * K * cs + kr] += pl.nsub[g];
+        }
+        int mi = 0;
+        for (int v : items) mi = std::max(mi, v);
+        if (mi <= extra * B) {
+          pl.cap = cap;
+          pl.max_items = mi;
+          break;
+        }
+      }
+      if (pl.cap == 0) return false;
     }
     pl.off_mbar = (int)((pl.off_buf + pl.nbuf * pl.cap + 15) / 16 * 16);
     pl.off_meta = pl.off_mbar + 16;
-    pl.total = pl.off_meta + 32 * (int64_t)B;
+    pl.total = pl.off_meta + 32 * (int64_t)pl.max_items;
     return pl.total <= limit;
   };
-  // smallest cluster with about 128 rows of the largest colour per CTA that fits
+  // cluster size: the largest (16 CTAs, slabs of a patch side by side) once a
+  // colour holds >= 64 rows of a patch, else one CTA per patch (the CTA barrier
+  // is cheaper than the cluster barrier and the colour's work is small);
+  // measured on the SIPG 3x3 layout, p = 2..6, all levels
   int maxrows_pk = 1;
   {
     std::vector<int> cnt((size_t)nbase * K, 0);
     for (int e = 0; e < nent; ++e) cnt[(size_t)colour[order[e]] * K + gpatch[e]]++;
     for (int v : cnt) maxrows_pk = std::max(maxrows_pk, v);
   }
-  int want = 1;
-  while (want < 16 && want * 64 * 2 < maxrows_pk) want *= 2;
+  std::vector<int> sizes = maxrows_pk >= 64 ? std::vector<int>{16, 8, 4, 2, 1} : std::vector<int>{1, 2, 4, 8, 16};
+  if (const char* env = std::getenv("MGIGA_GS_CS")) {  // manual cluster size for tuning
+    const int v = std::atoi(env);
+    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) sizes.insert(sizes.begin(), v);
+  }
   dl.gs_csize = 0;
   Plan pl;
-  for (int cs = want; cs <= 16; cs *= 2) {
+  for (int cs : sizes) {
     Plan t;
     if (!plan_for(cs, t) || !gs_staged_fits(d, P, cs, (int)t.total, t.threads)) continue;
     pl = std::move(t);
@@ -624,57 +657,85 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
   }
   if (dl.gs_csize == 0) return;  // the grid-wide sweep handles every colour
   const int cs = dl.gs_csize;
-  // blocks in (phase, k, r, colour) order
+  // items in (phase, k, r, colour, item) order; an item takes a contiguous share of its group's rows
   const int ngrp = nbase * K * cs;
   std::vector<std::vector<int>> members(ngrp);
   for (int e = 0; e < nent; ++e) members[pl.grp_of[e]].push_back(e);
-  std::vector<int64_t> blk_off(ngrp, 0);
+  std::vector<int> sub_ptr(ngrp + 1, 0);
+  for (int g = 0; g < ngrp; ++g) sub_ptr[g + 1] = sub_ptr[g] + pl.nsub[g];
+  const int nitems_all = sub_ptr[ngrp];
+  std::vector<int> it_r0(nitems_all), it_rows(nitems_all), it_rp(nitems_all);
+  std::vector<int64_t> it_off(nitems_all, 0), it_bytes(nitems_all, 0);
+  for (int g = 0; g < ngrp; ++g)
+    for (int j = 0; j < pl.nsub[g]; ++j) {
+      const int i = sub_ptr[g] + j, R = pl.rows[g];
+      it_r0[i] = (int)((int64_t)R * j / pl.nsub[g]);
+      it_rows[i] = (int)((int64_t)R * (j + 1) / pl.nsub[g]) - it_r0[i];
+      it_rp[i] = pl.rp_of(it_rows[i]);
+      it_bytes[i] = it_rows[i] > 0 ? item_bytes(it_rp[i]) : 0;
+    }
   int64_t total = 0;
   for (int ph = 0; ph < 2; ++ph)
     for (int k = 0; k < K; ++k)
       for (int r = 0; r < cs; ++r)
         for (int c = ph * B; c < std::min((ph + 1) * B, nbase); ++c) {
           const int g = (c * K + k) * cs + r;
-          blk_off[g] = total;
-          total += pl.bytes[g];
+          for (int i = sub_ptr[g]; i < sub_ptr[g + 1]; ++i) {
+            it_off[i] = total;
+            total += it_bytes[i];
+          }
         }
   std::vector<unsigned char> pool((size_t)std::max<int64_t>(total, 16), 0);
   std::vector<int64_t> foff(L.ndof, -1);
   for (int g = 0; g < ngrp; ++g) {
-    const int R = pl.rows[g], Rp = pl.rp[g];
-    if (R == 0) continue;
-    float* coef = reinterpret_cast<float*>(pool.data() + blk_off[g]);
-    int* lidx = reinterpret_cast<int*>(coef + (size_t)nb * Rp);
-    float* fv = reinterpret_cast<float*>(lidx + Rp);
-    float* dinv = fv + Rp;
     const int k = (g / cs) % K, r = g % cs;
     const int64_t plane = plane_of(k);
-    for (int row = 0; row < R; ++row) {
-      const int e = members[g][row];
-      const int64_t pos = gpos[e];
-      for (int o = 0; o < nb; ++o) coef[(size_t)o * Rp + row] = (float)L.band[(size_t)o * L.nloc + pos];
-      const int64_t loc = pos - L.off[k];
-      const int s = (int)(loc / plane), rest = (int)(loc % plane);
-      lidx[row] = ((s - r * pl.slab[k]) << 20) | rest;
-      dinv[row] = (float)(1.0 / L.band[(size_t)center * L.nloc + pos]);
-      foff[e] = blk_off[g] + ((int64_t)nb + 1) * Rp * 4 + (int64_t)row * 4;
+    for (int i = sub_ptr[g]; i < sub_ptr[g + 1]; ++i) {
+      const int R = it_rows[i], Rp = it_rp[i];
+      if (R == 0) continue;
+      float* coef = reinterpret_cast<float*>(pool.data() + it_off[i]);
+      int* lidx = reinterpret_cast<int*>(coef + (size_t)nb * Rp);
+      float* fv = reinterpret_cast<float*>(lidx + Rp);
+      float* dinv = fv + Rp;
+      for (int row = 0; row < R; ++row) {
+        const int e = members[g][it_r0[i] + row];
+        const int64_t pos = gpos[e];
+        for (int o = 0; o < nb; ++o) coef[(size_t)o * Rp + row] = (float)L.band[(size_t)o * L.nloc + pos];
+        const int64_t loc = pos - L.off[k];
+        const int s = (int)(loc / plane), rest = (int)(loc % plane);
+        lidx[row] = ((s - r * pl.slab[k]) << 20) | rest;
+        dinv[row] = (float)(1.0 / L.band[(size_t)center * L.nloc + pos]);
+        foff[e] = it_off[i] + ((int64_t)nb + 1) * Rp * 4 + (int64_t)row * 4;
+      }
     }
   }
-  // per (direction, phase, k, r): colours in sweep order grouped into chunks
+  // per (direction, phase, k, r): items in sweep order grouped into chunks
   const size_t nreg = (size_t)2 * 2 * K * cs;
-  std::vector<int4> cmeta(nreg * B, make_int4(0, 0, 0, 0)), chunks(nreg * B, make_int4(0, 0, 0, 0));
+  std::vector<int64_t> item_ptr(nreg + 1, 0);
+  std::vector<int4> cmeta, chunks;
+  cmeta.reserve((size_t)2 * nitems_all);
+  chunks.reserve((size_t)2 * nitems_all);
   for (int dir = 0; dir < 2; ++dir)
     for (int ph = 0; ph < 2; ++ph)
       for (int k = 0; k < K; ++k)
         for (int r = 0; r < cs; ++r) {
-          const size_t base = ((((size_t)dir * 2 + ph) * K + k) * cs + r) * B;
+          const size_t reg = (((size_t)dir * 2 + ph) * K + k) * cs + r;
           const int c0 = ph * B, nc = std::max(0, std::min((ph + 1) * B, nbase) - c0);
-          std::vector<int> chunk_of(nc);
-          std::vector<int64_t> lo, hi;
-          for (int i = 0; i < nc; ++i) {
-            const int c = dir == 0 ? c0 + i : c0 + nc - 1 - i;
+          std::vector<int> seq;  // items in sweep order; last item of each colour flagged
+          std::vector<char> last;
+          for (int ci = 0; ci < nc; ++ci) {
+            const int c = dir == 0 ? c0 + ci : c0 + nc - 1 - ci;
             const int g = (c * K + k) * cs + r;
-            const int64_t a0 = blk_off[g], a1 = blk_off[g] + pl.bytes[g];
+            const int n_i = sub_ptr[g + 1] - sub_ptr[g];
+            for (int j = 0; j < n_i; ++j) {
+              seq.push_back(dir == 0 ? sub_ptr[g] + j : sub_ptr[g + 1] - 1 - j);
+              last.push_back(j == n_i - 1);
+            }
+          }
+          std::vector<int> chunk_of(seq.size());
+          std::vector<int64_t> lo, hi;
+          for (size_t q = 0; q < seq.size(); ++q) {
+            const int64_t a0 = it_off[seq[q]], a1 = a0 + it_bytes[seq[q]];
             if (!lo.empty() && std::max(hi.back(), a1) - std::min(lo.back(), a0) <= pl.cap) {
               lo.back() = std::min(lo.back(), a0);
               hi.back() = std::max(hi.back(), a1);
@@ -682,18 +743,23 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
               lo.push_back(a0);
               hi.push_back(a1);
             }
-            chunk_of[i] = (int)lo.size() - 1;
+            chunk_of[q] = (int)lo.size() - 1;
           }
-          for (int i = 0; i < nc; ++i) {
-            const int c = dir == 0 ? c0 + i : c0 + nc - 1 - i;
-            const int g = (c * K + k) * cs + r;
-            const int j = chunk_of[i];
-            cmeta[base + i] = make_int4(pl.rows[g], j, (int)(blk_off[g] - lo[j]), pl.rp[g]);
+          item_ptr[reg] = (int64_t)cmeta.size();
+          for (size_t q = 0; q < seq.size(); ++q) {
+            const int i = seq[q], j = chunk_of[q];
+            cmeta.push_back(make_int4(it_rows[i], j, (int)(it_off[i] - lo[j]), it_rp[i] | (last[q] ? 1 << 30 : 0)));
           }
-          for (size_t j = 0; j < lo.size(); ++j)
-            chunks[base + j] = make_int4((int)(uint32_t)(lo[j] & 0xffffffffLL), (int)(lo[j] >> 32),
-                                         (int)(hi[j] - lo[j]), 0);
+          for (size_t q = 0; q < seq.size(); ++q)
+            chunks.push_back(q < lo.size() ? make_int4((int)(uint32_t)(lo[q] & 0xffffffffLL), (int)(lo[q] >> 32),
+                                                       (int)(hi[q] - lo[q]), 0)
+                                           : make_int4(0, 0, 0, 0));
+          item_ptr[reg + 1] = (int64_t)cmeta.size();
         }
+  if (cmeta.empty()) {
+    cmeta.push_back(make_int4(0, 0, 0, 0));
+    chunks.push_back(make_int4(0, 0, 0, 0));
+  }
   dl.gs_pool = A.upload(pool);
   dl.gs_foff = A.upload(foff);
   const auto par = patch_parity(pr);
@@ -716,8 +782,10 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
   a.pitch = A.upload(pl.pitch);
   a.guard = A.upload(pl.guard);
   a.pool = dl.gs_pool;
+  a.item_ptr = A.upload(item_ptr);
   a.cmeta = A.upload(cmeta);
   a.chunks = A.upload(chunks);
+  a.max_items = pl.max_items;
   a.off_buf = pl.off_buf;
   a.off_mbar = pl.off_mbar;
   a.off_meta = pl.off_meta;
@@ -841,7 +909,7 @@ void run_fd_step(mgiga_handle* h, DLevel& d, size_t i) {
 void smooth(mgiga_handle* h, int l) {
   DLevel& d = h->D[l];
   for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
-  launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r, d.u,
+  launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.zpool_f32, d.piece_pos, d.r, d.u,
                h->opt.tau, 0);
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, d.u, nullptr, 2);
 }
@@ -923,7 +991,7 @@ void coarse_solve(mgiga_handle* h) {
     CK(cudaMemsetAsync(d.u, 0, d.nloc * sizeof(double), h->stream));
     return;
   }
-  launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.f, d.u,
+  launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.zpool_f32, d.piece_pos, d.f, d.u,
                1.0, 1);
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, d.u, nullptr, 2);
 }
@@ -1617,7 +1685,7 @@ static void run_stage(mgiga_handle* h, int stage, int level) {
       for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
       break;
     case MGIGA_STAGE_PIECES:
-      launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.piece_pos, d.r,
+      launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.zpool_f32, d.piece_pos, d.r,
                    d.u, h->opt.tau, 0);
       break;
     case MGIGA_STAGE_GS: gs_sweep(h, level, true); break;

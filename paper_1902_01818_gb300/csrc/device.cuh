@@ -76,6 +76,17 @@ struct PieceItem {
   int piece, row0;
 };
 
+// one 2D patch interior for the fused small fast diagonalisation: U_0 (n0 x
+// n0), U_1 (n1 x n1) row-major and the inverse eigenvalue sums (n1 x n0) in
+// the arithmetic type; the interior starts at ibase with row stride N0
+struct FdSmall {
+  int64_t ibase;
+  int n0, n1, N0, pad;
+  const void* U0;
+  const void* U1;
+  const void* dinv;
+};
+
 // scalar slots of the CG state in device memory
 enum { S_RZ = 0, S_PQ, S_ALPHA, S_RR, S_RZNEW, S_BETA, S_FF, S_TMP, S_RZOLD, S_COUNT };
 

@@ -413,6 +413,89 @@ __global__ void __launch_bounds__(256) gemm_tiled(const GemmTask* __restrict__ t
 }
 
 // ---------------------------------------------------------------------------
+// a2 for small 2D patches (the coarse levels): the four contractions of one
+// patch interior in one CTA, operands and intermediates in shared memory
+// (row pitches odd, so that the strided operand reads hit distinct banks).
+// A warp computes 4 rows x 128 columns (lane + 32 j) of a product per task.
+// ---------------------------------------------------------------------------
+template <typename T, typename FA, typename FB, typename FE>
+__device__ __forceinline__ void cta_gemm(int M, int N, int K, FA a_at, FB b_at, FE epi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int mb = (M + 3) / 4, nbk = (N + 127) / 128;
+  for (int t = warp; t < mb * nbk; t += nw) {
+    const int m0 = (t / nbk) * 4, nb0 = (t % nbk) * 128 + lane;
+    int mi[4], nj[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mi[i] = min(m0 + i, M - 1);  // clamped: valid reads, results dropped
+#pragma unroll
+    for (int j = 0; j < 4; ++j) nj[j] = min(nb0 + 32 * j, N - 1);
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int k = 0; k < K; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = a_at(mi[i], k);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = b_at(k, nj[j]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (m0 + i < M && nb0 + 32 * j < N) epi(m0 + i, nb0 + 32 * j, acc[i][j]);
+  }
+}
+
+__host__ __device__ constexpr int odd_pitch(int n) { return n | 1; }
+
+template <typename T>
+__global__ void __launch_bounds__(512) fd_small_2d(const FdSmall* __restrict__ patches, const double* __restrict__ r,
+                                                   double* __restrict__ u, double tau) {
+  extern __shared__ __align__(16) unsigned char fd_smem[];
+  const FdSmall q = patches[blockIdx.x];
+  const int n0 = q.n0, n1 = q.n1, N0 = q.N0;
+  const int pu0 = odd_pitch(n0), pu1 = odd_pitch(n1), ps = odd_pitch(n0);
+  T* U0 = reinterpret_cast<T*>(fd_smem);
+  T* U1 = U0 + n0 * pu0;
+  T* S1 = U1 + n1 * pu1;
+  T* S2 = S1 + n1 * ps;
+  const T* gU0 = static_cast<const T*>(q.U0);
+  const T* gU1 = static_cast<const T*>(q.U1);
+  const T* dinv = static_cast<const T*>(q.dinv);
+  const double* rg = r + q.ibase;
+  double* ug = u + q.ibase;
+  for (int i = threadIdx.x; i < n0 * n0; i += blockDim.x) U0[(i / n0) * pu0 + i % n0] = gU0[i];
+  for (int i = threadIdx.x; i < n1 * n1; i += blockDim.x) U1[(i / n1) * pu1 + i % n1] = gU1[i];
+  for (int i = threadIdx.x; i < n1 * n0; i += blockDim.x) {
+    const int i1 = i / n0, i0 = i % n0;
+    S2[i1 * ps + i0] = (T)rg[(int64_t)i1 * N0 + i0];
+  }
+  __syncthreads();
+  // 1) S1 = R U0
+  cta_gemm<T>(n1, n0, n0, [&](int m, int k) { return S2[m * ps + k]; }, [&](int k, int n) { return U0[k * pu0 + n]; },
+              [&](int m, int n, T v) { S1[m * ps + n] = v; });
+  __syncthreads();
+  // 2) S2 = (U1^T S1) * dinv
+  cta_gemm<T>(n1, n0, n1, [&](int m, int k) { return U1[k * pu1 + m]; }, [&](int k, int n) { return S1[k * ps + n]; },
+              [&](int m, int n, T v) { S2[m * ps + n] = v * dinv[m * n0 + n]; });
+  __syncthreads();
+  // 3) S1 = S2 U0^T
+  cta_gemm<T>(n1, n0, n0, [&](int m, int k) { return S2[m * ps + k]; }, [&](int k, int n) { return U0[n * pu0 + k]; },
+              [&](int m, int n, T v) { S1[m * ps + n] = v; });
+  __syncthreads();
+  // 4) u_interior += tau U1 S1
+  cta_gemm<T>(n1, n0, n1, [&](int m, int k) { return U1[m * pu1 + k]; }, [&](int k, int n) { return S1[k * ps + n]; },
+              [&](int m, int n, T v) { ug[(int64_t)m * N0 + n] += tau * (double)v; });
+}
+
+// ---------------------------------------------------------------------------
 // a2 on the 5th-generation tensor cores: one 128 x 64 tile of a GemmTask per
 // CTA (4 warps).  Operands are staged by all threads into shared memory in
 // the K-major, non-swizzled core-matrix layout (8 rows x 16 bytes per core
@@ -1153,6 +1236,25 @@ void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const
 }
 
 int gemm_tile(int arith) { return arith == 1 ? 64 : 32; }
+
+int fd_small_smem(int n0, int n1, bool f32) {
+  const size_t e = f32 ? sizeof(float) : sizeof(double);
+  return (int)(e * ((size_t)n0 * odd_pitch(n0) + (size_t)n1 * odd_pitch(n1) + 2 * (size_t)n1 * odd_pitch(n0)));
+}
+
+cudaError_t prepare_fd_small() {
+  cudaError_t e = cudaFuncSetAttribute(fd_small_2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFdSmallSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fd_small_2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFdSmallSmem);
+}
+
+void launch_fd_small(int npatch, int smem, bool f32, cudaStream_t st, const FdSmall* patches, const double* r,
+                     double* u, double tau) {
+  if (npatch == 0) return;
+  ++g_launches;
+  if (f32) fd_small_2d<float><<<npatch, 512, smem, st>>>(patches, r, u, tau);
+  else fd_small_2d<double><<<npatch, 512, smem, st>>>(patches, r, u, tau);
+}
 
 void launch_gemm_umma(int nitems, int kind, cudaStream_t st, const GemmTask* tasks, const GemmItem* items, int* err) {
   if (nitems == 0) return;

@@ -81,6 +81,12 @@ void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const
                     double* u);
 // arith 0: FP64 arithmetic (32 x 32 tiles), 1: FP32 arithmetic (64 x 64 tiles)
 int gemm_tile(int arith);
+// fused fast diagonalisation of small 2D patch interiors: one CTA per patch
+constexpr int kFdSmallSmem = 200 * 1024;
+int fd_small_smem(int n0, int n1, bool f32);  // shared memory of one patch (must be <= kFdSmallSmem)
+cudaError_t prepare_fd_small();
+void launch_fd_small(int npatch, int smem, bool f32, cudaStream_t st, const FdSmall* patches, const double* r,
+                     double* u, double tau);
 // tA: element type of A in the step (0 double, 1 float); B is of the arithmetic type
 void launch_gemm(int nitems, int arith, int tA, cudaStream_t st, const GemmTask* tasks, const GemmItem* items);
 // tensor-core tiles (128 x 64, items built with these tile sizes): kind 0 TF32, 1 BF16

@@ -105,6 +105,8 @@ struct DLevel {
   GemmItem* fd_items = nullptr;
   std::vector<std::pair<int, int>> fd_steps;  // item range per step
   std::vector<int> fd_step_ta;                 // element type of A per step (0 double, 1 float)
+  FdSmall* fd_small = nullptr;                 // fused path (small 2D patches): one CTA per patch
+  int fd_small_n = 0, fd_small_smem = 0;
   // pieces (interface pieces on levels >= 1, the coarse solve on level 0)
   PieceMeta* pieces = nullptr;
   PieceItem* piece_items = nullptr;
@@ -405,6 +407,38 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   }
   for (auto& s : steps) add_step(s);
   (void)lvl;
+  // small 2D interiors: all four contractions of a patch in one CTA (shared memory), unless
+  // MGIGA_FD_FUSE=0 (kept for testing the batched-GEMM path on small problems)
+  const char* fuse_env = std::getenv("MGIGA_FD_FUSE");
+  if (d == 2 && !(fuse_env && fuse_env[0] == '0')) {
+    std::vector<FdSmall> fs;
+    int smem = 0;
+    bool fits = true;
+    for (int k = 0; k < L.K && fits; ++k) {
+      const int n0 = fd[k].n[0], n1 = fd[k].n[1];
+      if (n0 <= 0 || n1 <= 0) continue;
+      const int b = fd_small_smem(n0, n1, f32);
+      // one CTA does 4 n^3 multiply-adds: beyond n = 48 the batched steps over all SMs win
+      // (measured on the SIPG 3x3 layout: n ~ 30-45 fused 0.023 ms vs 0.039; n ~ 60-93 0.062 vs 0.048)
+      if (b > kFdSmallSmem || std::max(n0, n1) > 48) { fits = false; break; }
+      smem = std::max(smem, b);
+      FdSmall q{};
+      q.ibase = L.off[k] + 1 + L.N[k][0];
+      q.n0 = n0;
+      q.n1 = n1;
+      q.N0 = L.N[k][0];
+      q.U0 = dU + uoff[k][0] * esz;
+      q.U1 = dU + uoff[k][1] * esz;
+      q.dinv = dD + toff[k] * esz;
+      fs.push_back(q);
+    }
+    if (fits && !fs.empty()) {
+      CK(prepare_fd_small());
+      dl.fd_small = A.upload(fs);
+      dl.fd_small_n = (int)fs.size();
+      dl.fd_small_smem = smem;
+    }
+  }
   dl.fd_tasks = A.upload(tasks);
   dl.fd_items = A.upload(items);
 }
@@ -905,10 +939,19 @@ void run_fd_step(mgiga_handle* h, DLevel& d, size_t i) {
     launch_gemm(s.second - s.first, d.arith, d.fd_step_ta[i], h->stream, d.fd_tasks, d.fd_items + s.first);
 }
 
+// the interior part of the smoother: fused per patch on small 2D levels, else the batched GEMM steps
+void run_fd(mgiga_handle* h, DLevel& d) {
+  if (d.fd_small) {
+    launch_fd_small(d.fd_small_n, d.fd_small_smem, d.arith >= 1, h->stream, d.fd_small, d.r, d.u, h->opt.tau);
+    return;
+  }
+  for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
+}
+
 // u += tau sum_T P_T L_T^{-1} P_T^T r  (Eq. Ldef), r in d.r
 void smooth(mgiga_handle* h, int l) {
   DLevel& d = h->D[l];
-  for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
+  run_fd(h, d);
   launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.zpool_f32, d.piece_pos, d.r, d.u,
                h->opt.tau, 0);
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, d.u, nullptr, 2);
@@ -1682,7 +1725,7 @@ static void run_stage(mgiga_handle* h, int stage, int level) {
       cycle_residual(h, level, d.u, d.f, d.r);
       break;
     case MGIGA_STAGE_FD:
-      for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
+      run_fd(h, d);
       break;
     case MGIGA_STAGE_PIECES:
       launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.zpool_f32, d.piece_pos, d.r,

@@ -109,6 +109,26 @@ def test_scms_smoother_every_level(name):
         assert _rel(got, ref) <= 1e-11, (l, _rel(got, ref))
 
 
+@pytest.mark.parametrize("name", ["conf2d_p2", "sipg2d_p3", "single_patch_p4"])
+def test_scms_smoother_batched_gemm_path(name, monkeypatch):
+    """2D interiors this small take the fused one-CTA-per-patch path; the batched
+    GEMM steps used on large levels must agree with the oracle too."""
+    monkeypatch.setenv("MGIGA_FD_FUSE", "0")
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    lib = binding().Solver(prob, levels=levels, smoother="hybrid", **opt)
+    orc = _pair(name, "hybrid")[2]
+    rng = np.random.default_rng(3)
+    for l in range(1, lib.levels):
+        A = orc.h["A"][l]
+        n = A.shape[0]
+        u, f = rng.standard_normal(n), rng.standard_normal(n)
+        ref = u + orc.scms[l].apply(f - A @ u)
+        got = lib.apply("smooth", l, f, u)
+        assert _rel(got, ref) <= 1e-11, (l, _rel(got, ref))
+    lib.close()
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_gauss_seidel_sweeps_every_level(name):
     prob, lib, orc = _pair(name, "hybrid")

@@ -165,8 +165,10 @@ __global__ void shared_reduce(int nsh, const int* __restrict__ sh_ptr, const int
 // a5 / a6: transfers, tensor products of the 1D knot-insertion matrices
 // ---------------------------------------------------------------------------
 // f_c[I] = sum_{i} prod_a P_a[i_a, I_a] (w r)[i], children i_a of I_a from the
-// tables; coarse Dirichlet entries are left 0.
-template <int D>
+// tables; coarse Dirichlet entries are left 0.  T: arithmetic type (double;
+// float inside the mixed-precision cycle, where the transfers only feed the
+// preconditioner -- FP64 runs at 1/64 of the FP32 rate on this part).
+template <int D, typename T>
 __global__ void __launch_bounds__(kTile) restrict_band(
     const Tile* __restrict__ tiles, const PatchMeta* __restrict__ pc, const PatchMeta* __restrict__ pf,
     const XferMeta* __restrict__ xm, const int* __restrict__ ch_start, const double* __restrict__ ch_val,
@@ -188,30 +190,32 @@ __global__ void __launch_bounds__(kTile) restrict_band(
     st[a] = ch_start[x.ch_off + I[a]];
     cv[a] = ch_val + (x.ch_off + I[a]) * cw;
   }
-  double s = 0.0;
+  T s = 0;
   for (int t2 = 0; t2 < (D == 3 ? cw : 1); ++t2) {
-    const double c2 = D == 3 ? cv[2][t2] : 1.0;
-    if (c2 == 0.0) continue;
+    const T c2 = D == 3 ? (T)cv[2][t2] : (T)1;
+    if (c2 == (T)0) continue;
     const int i2 = D == 3 ? st[2] + t2 : 0;
     for (int t1 = 0; t1 < cw; ++t1) {
-      const double c1 = cv[1][t1] * c2;
-      if (c1 == 0.0) continue;
+      const T c1 = (T)cv[1][t1] * c2;
+      if (c1 == (T)0) continue;
       const int i1 = st[1] + t1;
       const int64_t rowb = mf.off + (int64_t)mf.N[0] * (i1 + (int64_t)mf.N[1] * i2);
+      T s1 = 0;
       for (int t0 = 0; t0 < cw; ++t0) {
-        const double c0 = cv[0][t0];
-        if (c0 == 0.0) continue;
+        const T c0 = (T)cv[0][t0];
+        if (c0 == (T)0) continue;
         const int64_t fp = rowb + st[0] + t0;
-        const double v = w ? w[fp] * r[fp] : r[fp];
-        s = fma(c0 * c1, v, s);
+        const T v = (T)(w ? w[fp] * r[fp] : r[fp]);
+        s1 = fma(c0, v, s1);
       }
+      s = fma(c1, s1, s);
     }
   }
-  out[pos] = s;
+  out[pos] = (double)s;
 }
 
-// u_f[i] += sum_I prod_a P_a[i_a, I_a] e_c[I]
-template <int D>
+// u_f[i] += sum_I prod_a P_a[i_a, I_a] e_c[I]  (T: arithmetic type, as for the restriction)
+template <int D, typename T>
 __global__ void __launch_bounds__(kTile) prolong_band(
     const Tile* __restrict__ tiles, const PatchMeta* __restrict__ pf, const PatchMeta* __restrict__ pc,
     const XferMeta* __restrict__ xm, const int* __restrict__ par_start, const double* __restrict__ par_val,
@@ -231,24 +235,26 @@ __global__ void __launch_bounds__(kTile) prolong_band(
     st[a] = par_start[x.par_off + i[a]];
     pv[a] = par_val + (x.par_off + i[a]) * pw;
   }
-  double s = 0.0;
+  T s = 0;
   for (int t2 = 0; t2 < (D == 3 ? pw : 1); ++t2) {
-    const double c2 = D == 3 ? pv[2][t2] : 1.0;
-    if (c2 == 0.0) continue;
+    const T c2 = D == 3 ? (T)pv[2][t2] : (T)1;
+    if (c2 == (T)0) continue;
     const int I2 = D == 3 ? st[2] + t2 : 0;
     for (int t1 = 0; t1 < pw; ++t1) {
-      const double c1 = pv[1][t1] * c2;
-      if (c1 == 0.0) continue;
+      const T c1 = (T)pv[1][t1] * c2;
+      if (c1 == (T)0) continue;
       const int I1 = st[1] + t1;
       const int64_t rowb = mc.off + (int64_t)mc.N[0] * (I1 + (int64_t)mc.N[1] * I2);
+      T s1 = 0;
       for (int t0 = 0; t0 < pw; ++t0) {
-        const double c0 = pv[0][t0];
-        if (c0 == 0.0) continue;
-        s = fma(c0 * c1, e[rowb + st[0] + t0], s);
+        const T c0 = (T)pv[0][t0];
+        if (c0 == (T)0) continue;
+        s1 = fma(c0, (T)e[rowb + st[0] + t0], s1);
       }
+      s = fma(c1, s1, s);
     }
   }
-  u[pos] += s;
+  u[pos] += (double)s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1033,20 +1039,34 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
 }
 
 // f minus the couplings to the other parity (SIPG cross-patch terms, from the
-// current u) for the base-colour entries [e0, e0 + n) of one phase, into their blocks
-__global__ void gs_fill_phase(int e0, int n, const int64_t* __restrict__ f_off, const int64_t* __restrict__ gs_pos,
-                              const int2* __restrict__ xrange, const int64_t* __restrict__ x_col,
-                              const double* __restrict__ x_val, const double* __restrict__ f,
-                              const double* __restrict__ u, unsigned char* pool) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int e = e0 + i;
-  const int64_t o = f_off[e];
-  if (o < 0) return;
-  double v = f[gs_pos[e]];
+// current u) for the base-colour entries [e0, e0 + n) of one phase, into their
+// blocks: entries without such terms one thread each (the first n threads),
+// the nx entries with them (xent) one warp each, lanes over the couplings
+__global__ void gs_fill_phase(int e0, int n, int nx, const int* __restrict__ xent, const int64_t* __restrict__ f_off,
+                              const int64_t* __restrict__ gs_pos, const int2* __restrict__ xrange,
+                              const int64_t* __restrict__ x_col, const double* __restrict__ x_val,
+                              const double* __restrict__ f, const double* __restrict__ u, unsigned char* pool) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ncopy = ((int64_t)n + 31) / 32 * 32;
+  if (tid < ncopy) {
+    if (tid >= n) return;
+    const int e = e0 + (int)tid;
+    const int64_t o = f_off[e];
+    const int2 xr = xrange[e];
+    if (o < 0 || xr.y > xr.x) return;  // entries with couplings: their warp below
+    *reinterpret_cast<float*>(pool + o) = (float)f[gs_pos[e]];
+    return;
+  }
+  const int64_t w = (tid - ncopy) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nx) return;
+  const int e = xent[w];
   const int2 xr = xrange[e];
-  for (int j = xr.x; j < xr.y; ++j) v -= x_val[j] * u[x_col[j]];
-  *reinterpret_cast<float*>(pool + o) = (float)v;
+  double v = 0.0;
+  for (int j = xr.x + lane; j < xr.y; j += 32) v += x_val[j] * u[x_col[j]];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int64_t o = f_off[e];
+  if (lane == 0 && o >= 0) *reinterpret_cast<float*>(pool + o) = (float)(f[gs_pos[e]] - v);
 }
 
 // ---------------------------------------------------------------------------
@@ -1215,24 +1235,34 @@ void launch_shared(int nsh, cudaStream_t st, const int* sh_ptr, const int64_t* s
   shared_reduce<<<(nsh + 255) / 256, 256, 0, st>>>(nsh, sh_ptr, sh_pos, v, f, mode);
 }
 
-void launch_restrict(int d, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pc, const PatchMeta* pf,
-                     const XferMeta* xm, const int* ch_start, const double* ch_val, int cw, const double* r,
-                     const double* w, const int* c_l2g, double* out) {
+void launch_restrict(int d, bool f32, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pc,
+                     const PatchMeta* pf, const XferMeta* xm, const int* ch_start, const double* ch_val, int cw,
+                     const double* r, const double* w, const int* c_l2g, double* out) {
   if (ntiles == 0) return;
   ++g_launches;
-  if (d == 2)
-    restrict_band<2><<<ntiles, kTile, 0, st>>>(tiles, pc, pf, xm, ch_start, ch_val, cw, r, w, c_l2g, out);
-  else
-    restrict_band<3><<<ntiles, kTile, 0, st>>>(tiles, pc, pf, xm, ch_start, ch_val, cw, r, w, c_l2g, out);
+#define MG_RESTRICT(DD, TT) \
+  restrict_band<DD, TT><<<ntiles, kTile, 0, st>>>(tiles, pc, pf, xm, ch_start, ch_val, cw, r, w, c_l2g, out)
+  if (d == 2) {
+    if (f32) MG_RESTRICT(2, float); else MG_RESTRICT(2, double);
+  } else {
+    if (f32) MG_RESTRICT(3, float); else MG_RESTRICT(3, double);
+  }
+#undef MG_RESTRICT
 }
 
-void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pf, const PatchMeta* pc,
-                    const XferMeta* xm, const int* par_start, const double* par_val, int pw, const double* e,
-                    double* u) {
+void launch_prolong(int d, bool f32, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pf,
+                    const PatchMeta* pc, const XferMeta* xm, const int* par_start, const double* par_val, int pw,
+                    const double* e, double* u) {
   if (ntiles == 0) return;
   ++g_launches;
-  if (d == 2) prolong_band<2><<<ntiles, kTile, 0, st>>>(tiles, pf, pc, xm, par_start, par_val, pw, e, u);
-  else prolong_band<3><<<ntiles, kTile, 0, st>>>(tiles, pf, pc, xm, par_start, par_val, pw, e, u);
+#define MG_PROLONG(DD, TT) \
+  prolong_band<DD, TT><<<ntiles, kTile, 0, st>>>(tiles, pf, pc, xm, par_start, par_val, pw, e, u)
+  if (d == 2) {
+    if (f32) MG_PROLONG(2, float); else MG_PROLONG(2, double);
+  } else {
+    if (f32) MG_PROLONG(3, float); else MG_PROLONG(3, double);
+  }
+#undef MG_PROLONG
 }
 
 int gemm_tile(int arith) { return arith == 1 ? 64 : 32; }
@@ -1376,12 +1406,14 @@ cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t
   return cudaLaunchKernelExC(&cfg, gs_staged_ptr(d, p), args);
 }
 
-void launch_gs_fill_phase(int e0, int n, cudaStream_t st, const int64_t* f_off, const int64_t* gs_pos,
-                          const int2* xrange, const int64_t* x_col, const double* x_val, const double* f,
-                          const double* u, unsigned char* pool) {
+void launch_gs_fill_phase(int e0, int n, int nx, const int* xent, cudaStream_t st, const int64_t* f_off,
+                          const int64_t* gs_pos, const int2* xrange, const int64_t* x_col, const double* x_val,
+                          const double* f, const double* u, unsigned char* pool) {
   if (n <= 0) return;
   ++g_launches;
-  gs_fill_phase<<<(n + 255) / 256, 256, 0, st>>>(e0, n, f_off, gs_pos, xrange, x_col, x_val, f, u, pool);
+  const int64_t threads = ((int64_t)n + 31) / 32 * 32 + 32 * (int64_t)nx;
+  gs_fill_phase<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(e0, n, nx, xent, f_off, gs_pos, xrange, x_col,
+                                                                  x_val, f, u, pool);
 }
 
 void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,

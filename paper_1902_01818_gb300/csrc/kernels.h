@@ -60,9 +60,10 @@ struct GsStagedArgs {
 };
 bool gs_staged_fits(int d, int p, int csize, int smem, int threads);
 cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t st, const GsStagedArgs& a);
-void launch_gs_fill_phase(int e0, int n, cudaStream_t st, const int64_t* f_off, const int64_t* gs_pos,
-                          const int2* xrange, const int64_t* x_col, const double* x_val, const double* f,
-                          const double* u, unsigned char* pool);
+// xent: the nx entries of [e0, e0 + n) with couplings to the other parity
+void launch_gs_fill_phase(int e0, int n, int nx, const int* xent, cudaStream_t st, const int64_t* f_off,
+                          const int64_t* gs_pos, const int2* xrange, const int64_t* x_col, const double* x_val,
+                          const double* f, const double* u, unsigned char* pool);
 
 void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
                  const double* band, int64_t nloc, const double* u, const double* f, double* out);
@@ -73,12 +74,13 @@ void launch_cross(int mode, int nx, cudaStream_t st, const int64_t* x_row, const
                   const double* x_val, const double* u, double* out);
 void launch_shared(int nsh, cudaStream_t st, const int* sh_ptr, const int64_t* sh_pos, double* v, const double* f,
                    int mode);
-void launch_restrict(int d, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pc, const PatchMeta* pf,
-                     const XferMeta* xm, const int* ch_start, const double* ch_val, int cw, const double* r,
-                     const double* w, const int* c_l2g, double* out);
-void launch_prolong(int d, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pf, const PatchMeta* pc,
-                    const XferMeta* xm, const int* par_start, const double* par_val, int pw, const double* e,
-                    double* u);
+// f32: FP32 arithmetic (inside the mixed-precision cycle), else FP64
+void launch_restrict(int d, bool f32, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pc,
+                     const PatchMeta* pf, const XferMeta* xm, const int* ch_start, const double* ch_val, int cw,
+                     const double* r, const double* w, const int* c_l2g, double* out);
+void launch_prolong(int d, bool f32, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pf,
+                    const PatchMeta* pc, const XferMeta* xm, const int* par_start, const double* par_val, int pw,
+                    const double* e, double* u);
 // arith 0: FP64 arithmetic (32 x 32 tiles), 1: FP32 arithmetic (64 x 64 tiles)
 int gemm_tile(int arith);
 // fused fast diagonalisation of small 2D patch interiors: one CTA per patch

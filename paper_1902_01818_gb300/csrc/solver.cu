@@ -138,6 +138,8 @@ struct DLevel {
   GsStagedArgs gs_staged{};        // everything but colours, direction, u
   unsigned char* gs_pool = nullptr;
   int64_t* gs_foff = nullptr;      // byte offset of each entry's f in the pool (-1: none)
+  int* gs_xent[2] = {nullptr, nullptr};  // per phase: base-colour entries with couplings to the other parity
+  int gs_nxent[2] = {0, 0};
 };
 
 }  // namespace
@@ -520,7 +522,8 @@ void build_pieces(const std::vector<Piece>& pcs, const Level& L, Arena& A, DLeve
 // fit one buffer are fetched as one chunk.
 void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl,
                      const std::vector<int>& order, const std::vector<int64_t>& gpos, const std::vector<int>& gpatch,
-                     int ncol, int B) {
+                     const std::vector<int>& gx, int ncol, int B) {
+  auto gxr_of = [&](int e) { return gx[e] >= 0 && L.x_ptr[gx[e] + 1] > L.x_ptr[gx[e]]; };
   const int K = L.K, d = L.d, nb = L.nb, P = L.p;
   const int W = 2 * P + 1, nob = d == 2 ? W : W * W;
   const int center = d == 2 ? P * W + P : (P * W + P) * W + P;
@@ -796,6 +799,14 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
   }
   dl.gs_pool = A.upload(pool);
   dl.gs_foff = A.upload(foff);
+  for (int ph = 0; ph < 2; ++ph) {
+    std::vector<int> xe;
+    const int e_lo = dl.gs_cptr[std::min(ph * B, nbase)], e_hi = dl.gs_cptr[std::min((ph + 1) * B, nbase)];
+    for (int e = e_lo; e < e_hi; ++e)
+      if (gxr_of(e)) xe.push_back(e);
+    dl.gs_nxent[ph] = (int)xe.size();
+    dl.gs_xent[ph] = xe.empty() ? nullptr : A.upload(xe);
+  }
   const auto par = patch_parity(pr);
   for (int ph = 0; ph < 2; ++ph) {
     std::vector<int> pp;
@@ -877,7 +888,7 @@ void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L,
   int B = 1;
   for (int a = 0; a < L.d; ++a) B *= L.p + 1;
   dl.gs_base = B;
-  if (f32) build_gs_staged(pr, colour, L, A, dl, order, gpos, gpatch, ncol, B);
+  if (f32) build_gs_staged(pr, colour, L, A, dl, order, gpos, gpatch, gx, ncol, B);
   int maxrows = 1;
   for (size_t c = 0; c + 1 < dl.gs_cptr.size(); ++c) maxrows = std::max(maxrows, dl.gs_cptr[c + 1] - dl.gs_cptr[c]);
   const int coop = gs_coop_max_blocks(L.d, L.p, f32);
@@ -1001,8 +1012,8 @@ void gs_sweep(mgiga_handle* h, int l, bool forward) {
     g.err = h->gs_err;
     // f minus the couplings to the other parity (fixed during the phase) into the blocks
     const int e0 = d.gs_cptr[g.c_begin], e1 = d.gs_cptr[g.c_end];
-    launch_gs_fill_phase(e0, e1 - e0, h->stream, d.gs_foff, d.gs_pos, d.gs_xrange, d.x_col, d.x_val, d.f, d.u,
-                         d.gs_pool);
+    launch_gs_fill_phase(e0, e1 - e0, d.gs_nxent[ph], d.gs_xent[ph], h->stream, d.gs_foff, d.gs_pos, d.gs_xrange,
+                         d.x_col, d.x_val, d.f, d.u, d.gs_pool);
     CK(launch_gs_staged(L.d, L.p, d.gs_nphase[ph], d.gs_smem, h->stream, g));
   };
   auto tail = [&]() { coop(2 * B, ncol); };
@@ -1010,21 +1021,22 @@ void gs_sweep(mgiga_handle* h, int l, bool forward) {
   else { tail(); phase(1); phase(0); }
 }
 
-// f_{l-1} = P^T r_l (r_l consistent; weights make each shared DoF count once)
-void restrict_to(mgiga_handle* h, int l, const double* r) {
+// f_{l-1} = P^T r_l (r_l consistent; weights make each shared DoF count once).
+// cycle: inside the V-cycle, where the mixed path transfers in FP32 arithmetic
+void restrict_to(mgiga_handle* h, int l, const double* r, bool cycle = false) {
   const Level& Lc = h->L[l - 1];
   DLevel& df = h->D[l];
   DLevel& dc = h->D[l - 1];
-  launch_restrict(Lc.d, dc.ntiles, h->stream, dc.tiles, dc.patches, df.patches, df.xm, df.ch_start, df.ch_val,
+  launch_restrict(Lc.d, cycle && df.arith >= 1, dc.ntiles, h->stream, dc.tiles, dc.patches, df.patches, df.xm, df.ch_start, df.ch_val,
                   df.cw, r, df.weight, dc.loc2glob, dc.f);
   if (conforming(h)) launch_shared(dc.nsh, h->stream, dc.sh_ptr, dc.sh_pos, dc.f, nullptr, 1);
 }
 
-void prolong_from(mgiga_handle* h, int l, const double* e, double* u) {
+void prolong_from(mgiga_handle* h, int l, const double* e, double* u, bool cycle = false) {
   const Level& Lf = h->L[l];
   DLevel& df = h->D[l];
   DLevel& dc = h->D[l - 1];
-  launch_prolong(Lf.d, df.ntiles, h->stream, df.tiles, df.patches, dc.patches, df.xm, df.par_start, df.par_val,
+  launch_prolong(Lf.d, cycle && df.arith >= 1, df.ntiles, h->stream, df.tiles, df.patches, dc.patches, df.xm, df.par_start, df.par_val,
                  df.pw, e, u);
 }
 
@@ -1061,9 +1073,9 @@ void vcycle(mgiga_handle* h, int l) {
   }
   for (int m = 0; m < std::max(1, h->opt.mu); ++m) {
     cycle_residual(h, l, d.u, d.f, d.r);
-    restrict_to(h, l, d.r);
+    restrict_to(h, l, d.r, true);
     vcycle(h, l - 1);
-    prolong_from(h, l, h->D[l - 1].u, d.u);
+    prolong_from(h, l, h->D[l - 1].u, d.u, true);
   }
   if (sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID) {
     for (int i = 0; i < nu; ++i) {
@@ -1732,8 +1744,8 @@ static void run_stage(mgiga_handle* h, int stage, int level) {
                    d.u, h->opt.tau, 0);
       break;
     case MGIGA_STAGE_GS: gs_sweep(h, level, true); break;
-    case MGIGA_STAGE_RESTRICT: restrict_to(h, level, d.r); break;
-    case MGIGA_STAGE_PROLONG: prolong_from(h, level, h->D[level - 1].u, d.u); break;
+    case MGIGA_STAGE_RESTRICT: restrict_to(h, level, d.r, true); break;
+    case MGIGA_STAGE_PROLONG: prolong_from(h, level, h->D[level - 1].u, d.u, true); break;
     case MGIGA_STAGE_COARSE: coarse_solve(h); break;
     case MGIGA_STAGE_VCYCLE: vcycle(h, level); break;
     default: throw SetupError(MGIGA_EINVAL, "unknown stage");

@@ -43,6 +43,22 @@ def hbm_peak_gbs():
         return 6800.0, "of fallback"
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one application of a stage on the
+# finest level, per degree, from one ncu capture of this build on a GB300 (profiles/
+# traffic_sipg3x3_finest_level.md gives the command and the per-kernel figures).  Used only for the
+# default workload (scale 3, hybrid, FP32 smoothers); None elsewhere or when a stage's kernels change.
+DRAM_TRAFFIC = {}
+
+
+def dram_traffic(stage, degrees, args, f32):
+    if not (f32 and args.scale == 3 and args.smoother == "hybrid"):
+        return None
+    vals = [DRAM_TRAFFIC.get((stage, p)) for p in degrees]
+    if any(v is None for v in vals):
+        return None
+    return sum(vals) / len(vals)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,11 +331,21 @@ def main():
         plain = {"value": total_dof / (ms64 / 1e3), "unit": "DoF/s", "ms_per_step": ms64,
                  "iterations": [x[0] for x in info64], "final_relres": [x[1] for x in info64]}
 
-    # roofline per stage on the finest level; the dominant one (largest share
-    # of a PCG iteration) is reported
+    # roofline per stage on the finest level of every degree (times summed over the degrees); the
+    # stage with the largest share of a PCG iteration (count x time) is reported.  Per PCG iteration
+    # on the finest level: one FP64 band product (CG), three residuals inside the cycle (FP32 band on
+    # the mixed path), two fast diagonalisations and, with the hybrid smoother, two Gauss-Seidel sweeps.
     hbm, hbm_src = hbm_peak_gbs()
     f32 = args.precision == "fp32"
-    counts = {"band": 4, "fd": 2, "gs": 2 if args.smoother == "hybrid" else 0}
+    hybrid = args.smoother == "hybrid"
+    counts = ({"band": 1, "residual": 3, "fd": 2, "gs": 2 if hybrid else 0} if f32 else
+              {"band": 4, "fd": 2, "gs": 2 if hybrid else 0})
+    names = {"band": "band_apply (FP64 band product)",
+             "residual": "band_residual_f32 + cross_apply (residual inside the cycle, FP32 band)",
+             "fd": ("gemm_tiled (fast diagonalisation, FP32)" if f32 else
+                    "gemm_tiled (fast diagonalisation, FP64)"),
+             "gs": ("gs_fill_phase + gs_patch_staged (one Gauss-Seidel sweep, FP32)" if f32 else
+                    "gs_sweep_coop (one Gauss-Seidel sweep, FP64)")}
     stages = {}
     for st, count in counts.items():
         if count == 0:
@@ -330,7 +356,7 @@ def main():
             a_fl, a_by = s.stage_work(st, -1)
             fl += a_fl
             by += a_by
-        if st == "band" or not f32:
+        if st in ("band", "fd") and not (st == "fd" and f32):
             rec = {"bound": "alu", "achieved": fl / (t_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
         elif st == "fd":
@@ -341,15 +367,13 @@ def main():
                    "peak_source": hbm_src}
         rec["frac"] = rec["achieved"] / rec["peak"]
         rec["ms_per_application"] = t_ms / len(solvers)
+        rec["algorithmic_bytes_per_application"] = by / len(solvers)
         rec["share_weight_ms"] = count * t_ms
+        rec["kernel"] = names[st]
+        rec["traffic"] = dram_traffic(st, degrees, args, f32)
         stages[st] = rec
     dom = max(stages, key=lambda k: stages[k]["share_weight_ms"])
-    names = {"band": "band_apply (FP64 residual/product)",
-             "fd": "gemm_tiled (fast diagonalisation, %s)" % ("FP32" if f32 else "FP64"),
-             "gs": ("gs_fill_phase + gs_patch_staged (one Gauss-Seidel sweep, FP32)" if f32 else
-                    "gs_sweep_coop (one Gauss-Seidel sweep, FP64)")}
     roof = dict(stages[dom])
-    roof.update({"kernel": names[dom], "traffic": None})
     roof["stages"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                       for k, v in stages.items()}
 

@@ -148,6 +148,18 @@ def test_one_cycle(name, smoother):
     assert _rel(lib.vcycle(r), orc.precondition(r)) <= 1e-11
 
 
+@pytest.mark.parametrize("name", ["conf2d_p2", "sipg2d_p3", "sipg3d_p2"])
+def test_one_w_cycle_and_two_smoothing_steps(name):
+    """mu = 2 (W-cycle) and nu = 2 against the oracle's cycle with the same options."""
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    lib = binding().Solver(prob, levels=levels, smoother="hybrid", mu=2, nu=2, **opt)
+    orc = omg.Multigrid(prob, levels=levels, smoother="hybrid", mu=2, nu=2, **opt)
+    r = np.random.default_rng(6).standard_normal(lib.ndof())
+    assert _rel(lib.vcycle(r), orc.precondition(r)) <= 1e-11
+    lib.close()
+
+
 @pytest.mark.parametrize("smoother", ["scms", "hybrid"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_pcg_iterates_and_iteration_count(name, smoother):

@@ -60,6 +60,9 @@ struct GemmTask {
   const void* dinv;
   int64_t ldd;
   int tA, tB, tC;
+  // vec: A (transA 0) and B (transB 1) FP32, K contiguous, rows 16-byte aligned and zero beyond K
+  // up to the next multiple of 4 (16-byte copies); ctrans: C[m][n] stored at n ldc + m
+  int vec, ctrans;
 };
 
 struct GemmItem {

@@ -303,7 +303,9 @@ __device__ __forceinline__ T ldt(const void* p, int64_t i, int t) {
 // slab k.  In FP64 the FMA pipe (2 DFMA/clk/SM on this part) is the bound, so
 // BM = 32 (more tiles in flight, less work on ragged edges); FP32 uses BM = 64
 // for reuse.
-constexpr int kGemmStages = 3;
+// Stages: FP64 3 (the FMA pipe is the bound), FP32 6 (~1 us of global latency
+// covered by 5 slabs in flight).
+constexpr int kGemmStagesF64 = 3, kGemmStagesF32 = 6;
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool valid) {
@@ -312,17 +314,30 @@ __device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool v
                : "memory");
 }
 
-template <int BM, typename Acc, typename TA, typename TB>
+template <int BM, typename Acc, typename TA, typename TB, int STAGES>
+struct GemmSmem {
+  static constexpr int PA = BM + 16 / (int)sizeof(TA);  // row pitches: 16-byte multiples
+  static constexpr int PB = BM + 16 / (int)sizeof(TB);
+  static constexpr int PC = BM + 16 / (int)sizeof(Acc);
+  static constexpr bool CVT = !std::is_same<TA, Acc>::value;  // A converted once per slab into Ac
+  static constexpr size_t a_bytes = (size_t)STAGES * GBK * PA * sizeof(TA);
+  static constexpr size_t b_bytes = (size_t)STAGES * GBK * PB * sizeof(TB);
+  static constexpr size_t c_bytes = CVT ? (size_t)2 * GBK * PC * sizeof(Acc) : 0;
+  static constexpr size_t bytes = a_bytes + b_bytes + c_bytes;
+};
+
+template <int BM, typename Acc, typename TA, typename TB, int STAGES>
 __global__ void __launch_bounds__(256) gemm_tiled(const GemmTask* __restrict__ tasks,
                                                   const GemmItem* __restrict__ items) {
+  constexpr int kGemmStages = STAGES;
+  using SM = GemmSmem<BM, Acc, TA, TB, STAGES>;
   constexpr int T = BM / 16;
-  constexpr int PA = BM + 16 / (int)sizeof(TA);  // row pitches: 16-byte multiples
-  constexpr int PB = BM + 16 / (int)sizeof(TB);
-  constexpr bool CVT = !std::is_same<TA, Acc>::value;  // A converted once per slab into Ac
-  constexpr int PC = BM + 16 / (int)sizeof(Acc);
-  __shared__ __align__(16) TA As[kGemmStages][GBK][PA];
-  __shared__ __align__(16) TB Bs[kGemmStages][GBK][PB];
-  __shared__ __align__(16) Acc Ac[CVT ? 2 : 1][CVT ? GBK : 1][PC];
+  constexpr int PA = SM::PA, PB = SM::PB, PC = SM::PC;
+  constexpr bool CVT = SM::CVT;
+  extern __shared__ __align__(16) unsigned char gemm_smem[];
+  auto As = reinterpret_cast<TA(*)[GBK][PA]>(gemm_smem);
+  auto Bs = reinterpret_cast<TB(*)[GBK][PB]>(gemm_smem + SM::a_bytes);
+  auto Ac = reinterpret_cast<Acc(*)[GBK][PC]>(gemm_smem + SM::a_bytes + SM::b_bytes);
   const GemmItem it = items[blockIdx.x];
   const GemmTask g = tasks[it.task];
   const TA* Ag = static_cast<const TA*>(g.A) + it.z * g.sA;
@@ -684,6 +699,224 @@ __global__ void __launch_bounds__(128) gemm_umma(const GemmTask* __restrict__ ta
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UN) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// a2 on the tensor cores, TF32 with FP32 operands in memory: the same 128 x 64
+// tile and core-matrix layout as gemm_umma, but the operands are copied
+// element by element into shared memory by asynchronous copies (TF32 reads
+// the FP32 bit patterns, so nothing passes through registers), through a ring
+// of kUmmaStages slabs: the copies of slab s + 3 are in flight while the MMAs
+// of slab s run.  A slab's buffer is refilled after the commit of the MMAs that
+// read it has arrived on its mbarrier.  256 threads: all stage, thread 0
+// issues the MMAs, the epilogue reads the accumulator with warp w taking TMEM
+// lanes 32 (w mod 4).. and columns 32 (w / 4)...  Every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int kUmmaStages = 4;
+constexpr int kUmmaTf32Smem = kUmmaStages * (UM + UN) * UKB;
+
+__global__ void __launch_bounds__(256) gemm_umma_tf32(const GemmTask* __restrict__ tasks,
+                                                      const GemmItem* __restrict__ items, int* err) {
+  constexpr int KT = UKB / 4;  // K elements per slab
+  extern __shared__ __align__(1024) unsigned char usm[];
+  auto sA = [&](int b) { return usm + b * (UM * UKB); };
+  auto sB = [&](int b) { return usm + kUmmaStages * UM * UKB + b * (UN * UKB); };
+  __shared__ __align__(8) unsigned long long mbar[kUmmaStages];
+  __shared__ unsigned tmem_slot;
+  const GemmItem it = items[blockIdx.x];
+  const GemmTask g = tasks[it.task];
+  const float* Ag = static_cast<const float*>(g.A) + it.z * g.sA;
+  const float* Bg = static_cast<const float*>(g.B) + it.z * g.sB;
+  const int64_t oC = it.z * g.sC;
+  const int m0 = it.tm * UM, n0 = it.tn * UN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(UN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < kUmmaStages; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_slot;
+  const unsigned idesc = umma_idesc<0>();
+  const int nst = (g.K + KT - 1) / KT;
+  const int64_t sAm = g.transA ? 1 : g.lda, sAk = g.transA ? g.lda : 1;
+  const int64_t sBn = g.transB ? g.ldb : 1, sBk = g.transB ? 1 : g.ldb;
+  // element (row, kk) of a slab in the core-matrix layout: 8-row groups of 1024 B, 16-byte column groups
+  auto cm_off = [](int row, int kk) { return (row >> 3) * 1024 + (kk >> 2) * 128 + (row & 7) * 16 + (kk & 3) * 4; };
+  auto load = [&](int st) {
+    const int b = st % kUmmaStages, k0 = st * KT;
+    unsigned char* a = sA(b);
+    unsigned char* bb = sB(b);
+    if (g.vec) {  // 16-byte copies: one core-matrix row segment (4 consecutive k) each
+#pragma unroll
+      for (int i = 0; i < (UM * KT / 4) / 256; ++i) {
+        const int e = i * 256 + tid;
+        const int row = e / (KT / 4), kq = e % (KT / 4);
+        const int m = m0 + row, k = k0 + 4 * kq;
+        const bool ok = m < g.M && k < g.K;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(a + cm_off(row, 4 * kq))),
+                     "l"(ok ? Ag + (int64_t)m * g.lda + k : Ag), "r"(ok ? 16 : 0)
+                     : "memory");
+      }
+#pragma unroll
+      for (int i = 0; i < (UN * KT / 4) / 256; ++i) {
+        const int e = i * 256 + tid;
+        const int nr = e / (KT / 4), kq = e % (KT / 4);
+        const int n = n0 + nr, k = k0 + 4 * kq;
+        const bool ok = n < g.N && k < g.K;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(bb + cm_off(nr, 4 * kq))),
+                     "l"(ok ? Bg + (int64_t)n * g.ldb + k : Bg), "r"(ok ? 16 : 0)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      return;
+    }
+#pragma unroll 4
+    for (int i = 0; i < (UM * KT) / 256; ++i) {  // consecutive threads: consecutive global addresses
+      const int e = i * 256 + tid;
+      const int row = g.transA ? e % UM : e / KT, kk = g.transA ? e / UM : e % KT;
+      const int m = m0 + row, k = k0 + kk;
+      const bool ok = m < g.M && k < g.K;
+      cp_async_elem<4>(a + cm_off(row, kk), ok ? Ag + m * sAm + k * sAk : Ag, ok);
+    }
+#pragma unroll 4
+    for (int i = 0; i < (UN * KT) / 256; ++i) {
+      const int e = i * 256 + tid;
+      const int nr = g.transB ? e / KT : e % UN, kk = g.transB ? e % KT : e / UN;
+      const int n = n0 + nr, k = k0 + kk;
+      const bool ok = n < g.N && k < g.K;
+      cp_async_elem<4>(bb + cm_off(nr, kk), ok ? Bg + n * sBn + k * sBk : Bg, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  for (int st = 0; st < kUmmaStages - 1; ++st) {
+    if (st < nst) load(st);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  bool ok = true;
+  unsigned phase_bits = 0;
+  for (int st = 0; st < nst; ++st) {
+    const int b = st % kUmmaStages;
+    asm volatile("cp.async.wait_group %0;" ::"n"(kUmmaStages - 2) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> tensor cores
+    __syncthreads();
+    if (tid == 0 && ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned a0 = smem_u32(sA(b)), b0 = smem_u32(sB(b));
+#pragma unroll
+      for (int j = 0; j < UKB / 32; ++j) {
+        const uint64_t ad = umma_sdesc(a0 + 256 * j), bd = umma_sdesc(b0 + 256 * j);
+        const unsigned acc = (st > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar[b]))
+                   : "memory");
+    }
+    // refill the buffer of slab st - 1 once its MMAs are done
+    const int nxt = st + kUmmaStages - 1;
+    if (nxt < nst) {
+      if (st >= 1) {
+        const int pb = (st - 1) % kUmmaStages;
+        if (ok && !mbar_wait(smem_u32(&mbar[pb]), (phase_bits >> pb) & 1u)) {
+          ok = false;
+          atomicExch(err, 3);
+        }
+        phase_bits ^= 1u << pb;
+      }
+      load(nxt);
+    } else {
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  // the commits of the last slabs were not consumed in the loop: wait for them in order (slab t is
+  // use t / kUmmaStages of its buffer; every earlier use of that buffer has been waited for)
+  for (int t = max(0, nst - kUmmaStages); t < nst; ++t) {
+    const int tb = t % kUmmaStages;
+    const unsigned par = (unsigned)((t / kUmmaStages) & 1);
+    if (!mbar_wait(smem_u32(&mbar[tb]), par)) {
+      if (ok) atomicExch(err, 3);
+      ok = false;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // epilogue: accumulator -> shared memory (the stage buffers are free: every MMA has completed and
+  // every copy has landed) -> global memory with consecutive threads on consecutive addresses
+  constexpr int TP = UN + 1;  // tile pitch in floats (odd: conflict-free column reads)
+  float* tile = reinterpret_cast<float*>(usm);
+  __syncthreads();
+  if (ok && nst > 0) {
+    const int q = warp & 3, h = warp >> 2;
+    const int row = q * 32 + lane;
+#pragma unroll
+    for (int c0 = h * 32; c0 < h * 32 + 32; c0 += 16) {
+      unsigned v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((unsigned)(q * 32) << 16) + (unsigned)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < 16; ++i) tile[row * TP + c0 + i] = __uint_as_float(v[i]);
+    }
+  }
+  __syncthreads();
+  if (ok && nst > 0) {
+    for (int idx = tid; idx < UM * UN; idx += 256) {
+      const int r = g.ctrans ? idx % UM : idx / UN, c = g.ctrans ? idx / UM : idx % UN;
+      const int m = m0 + r, n = n0 + c;
+      if (m >= g.M || n >= g.N) continue;
+      float acc = tile[r * TP + c];
+      const int64_t ci = oC + (g.ctrans ? (int64_t)n * g.ldc + m : (int64_t)m * g.ldc + gcol(g, n));
+      if (g.epi == 1) acc *= static_cast<const float*>(g.dinv)[(int64_t)m * g.ldd + n];
+      if (g.tC) {
+        float* cp = static_cast<float*>(g.C) + ci;
+        *cp = g.epi == 2 ? *cp + (float)(g.alpha * acc) : acc;
+      } else {
+        double* cp = static_cast<double*>(g.C) + ci;
+        *cp = g.epi == 2 ? *cp + g.alpha * (double)acc : (double)acc;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UN) : "memory");
+}
+
+// the interiors of all patches of r as compact FP32 blocks: patch k's row i1 of n0 values at
+// dst + d_off[k] + i1 * d_ld[k] (the padding columns stay 0); one thread per element
+__global__ void gather_interior_f32(int npatch, const int64_t* __restrict__ e_ptr, const int64_t* __restrict__ ibase,
+                                    const int* __restrict__ n0s, const int* __restrict__ N0s,
+                                    const int64_t* __restrict__ d_off, const int* __restrict__ d_ld,
+                                    const double* __restrict__ r, float* __restrict__ dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= e_ptr[npatch]) return;
+  int k = 0;
+  while (e >= e_ptr[k + 1]) ++k;  // few patches
+  const int64_t loc = e - e_ptr[k];
+  const int n0 = n0s[k];
+  const int64_t i1 = loc / n0, i0 = loc % n0;
+  dst[d_off[k] + i1 * d_ld[k] + i0] = (float)r[ibase[k] + i1 * N0s[k] + i0];
+}
+
+// FP64 -> FP32 copy of a vector (the residual for the tensor-core contractions)
+__global__ void to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -1296,17 +1529,57 @@ void launch_gemm_umma(int nitems, int kind, cudaStream_t st, const GemmTask* tas
 cudaError_t prepare_gemm_umma() {
   cudaError_t e = cudaFuncSetAttribute(gemm_umma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gemm_umma_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaTf32Smem);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(gemm_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+}
+
+void launch_gemm_umma_tf32(int nitems, cudaStream_t st, const GemmTask* tasks, const GemmItem* items, int* err) {
+  if (nitems == 0) return;
+  ++g_launches;
+  gemm_umma_tf32<<<nitems, 256, kUmmaTf32Smem, st>>>(tasks, items, err);
+}
+
+void launch_gather_interior_f32(int npatch, int64_t total, cudaStream_t st, const int64_t* e_ptr,
+                                const int64_t* ibase, const int* n0s, const int* N0s, const int64_t* d_off,
+                                const int* d_ld, const double* r, float* dst) {
+  if (total <= 0) return;
+  ++g_launches;
+  gather_interior_f32<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(npatch, e_ptr, ibase, n0s, N0s, d_off, d_ld,
+                                                                       r, dst);
+}
+
+void launch_to_f32(int64_t n, cudaStream_t st, const double* x, float* y) {
+  if (n <= 0) return;
+  ++g_launches;
+  to_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, y);
+}
+
+using GemmF64 = GemmSmem<32, double, double, double, kGemmStagesF64>;
+using GemmF32A64 = GemmSmem<64, float, double, float, kGemmStagesF32>;
+using GemmF32 = GemmSmem<64, float, float, float, kGemmStagesF32>;
+
+cudaError_t prepare_gemm() {
+  cudaError_t e = cudaFuncSetAttribute(gemm_tiled<64, float, double, float, kGemmStagesF32>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmF32A64::bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gemm_tiled<64, float, float, float, kGemmStagesF32>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmF32::bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(gemm_tiled<32, double, double, double, kGemmStagesF64>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmF64::bytes);
 }
 
 void launch_gemm(int nitems, int arith, int tA, cudaStream_t st, const GemmTask* tasks, const GemmItem* items) {
   if (nitems <= 0) return;
   ++g_launches;
   if (arith == 1) {
-    if (tA == 0) gemm_tiled<64, float, double, float><<<nitems, 256, 0, st>>>(tasks, items);
-    else gemm_tiled<64, float, float, float><<<nitems, 256, 0, st>>>(tasks, items);
+    if (tA == 0)
+      gemm_tiled<64, float, double, float, kGemmStagesF32><<<nitems, 256, GemmF32A64::bytes, st>>>(tasks, items);
+    else
+      gemm_tiled<64, float, float, float, kGemmStagesF32><<<nitems, 256, GemmF32::bytes, st>>>(tasks, items);
   } else {
-    gemm_tiled<32, double, double, double><<<nitems, 256, 0, st>>>(tasks, items);
+    gemm_tiled<32, double, double, double, kGemmStagesF64><<<nitems, 256, GemmF64::bytes, st>>>(tasks, items);
   }
 }
 

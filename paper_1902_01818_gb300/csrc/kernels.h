@@ -89,11 +89,20 @@ int fd_small_smem(int n0, int n1, bool f32);  // shared memory of one patch (mus
 cudaError_t prepare_fd_small();
 void launch_fd_small(int npatch, int smem, bool f32, cudaStream_t st, const FdSmall* patches, const double* r,
                      double* u, double tau);
+cudaError_t prepare_gemm();  // shared-memory attributes of the SIMT GEMM (once per process)
 // tA: element type of A in the step (0 double, 1 float); B is of the arithmetic type
 void launch_gemm(int nitems, int arith, int tA, cudaStream_t st, const GemmTask* tasks, const GemmItem* items);
 // tensor-core tiles (128 x 64, items built with these tile sizes): kind 0 TF32, 1 BF16
 void launch_gemm_umma(int nitems, int kind, cudaStream_t st, const GemmTask* tasks, const GemmItem* items, int* err);
 cudaError_t prepare_gemm_umma();
+// TF32 on the tensor cores with FP32 operands (A, B of every task float): asynchronous element
+// copies into the core-matrix layout, four slabs in flight
+void launch_gemm_umma_tf32(int nitems, cudaStream_t st, const GemmTask* tasks, const GemmItem* items, int* err);
+void launch_to_f32(int64_t n, cudaStream_t st, const double* x, float* y);
+// interiors of the patches of r as compact FP32 row blocks (TF32 contractions with 16-byte copies)
+void launch_gather_interior_f32(int npatch, int64_t total, cudaStream_t st, const int64_t* e_ptr,
+                                const int64_t* ibase, const int* n0s, const int* N0s, const int64_t* d_off,
+                                const int* d_ld, const double* r, float* dst);
 // zpool: double, or float when zf32 (the interface pieces of the mixed-precision smoother)
 void launch_piece(int nitems, int max_n, cudaStream_t st, const PieceItem* items, const PieceMeta* pieces,
                   const void* zpool, bool zf32, const int64_t* piece_pos, const double* r, double* u, double tau,

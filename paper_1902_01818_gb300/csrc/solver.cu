@@ -105,6 +105,13 @@ struct DLevel {
   GemmItem* fd_items = nullptr;
   std::vector<std::pair<int, int>> fd_steps;  // item range per step
   std::vector<int> fd_step_ta;                 // element type of A per step (0 double, 1 float)
+  int fd_kind = 0;                             // contraction engine: 0 FP64 SIMT, 1 FP32 SIMT, 2 TF32, 3 BF16
+  float* r32 = nullptr;                        // FP32 copy of r for the TF32 contractions
+  float* rc = nullptr;                         // 2D TF32: compact FP32 interiors of r (16-byte rows)
+  int rc_n = 0;
+  int64_t rc_total = 0;
+  int64_t *rc_eptr = nullptr, *rc_ibase = nullptr, *rc_off = nullptr;
+  int *rc_n0 = nullptr, *rc_N0 = nullptr, *rc_ld = nullptr;
   FdSmall* fd_small = nullptr;                 // fused path (small 2D patches): one CTA per patch
   int fd_small_n = 0, fd_small_smem = 0;
   // pieces (interface pieces on levels >= 1, the coarse solve on level 0)
@@ -273,6 +280,14 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   std::vector<FDData> fd(L.K);
 #pragma omp parallel for schedule(dynamic)
   for (int k = 0; k < L.K; ++k) fd[k] = fd_setup(L, k, delta);
+  // contraction engine of this level: the tensor cores (TF32 / BF16 modes) only for large
+  // interiors; below ~160 per direction the 128 x 64 tiles leave too few CTAs and the 64 x 64 FP32
+  // SIMT tiles are faster (measured on the SIPG 3x3 layout)
+  int max_n = 0;
+  for (int k = 0; k < L.K; ++k)
+    for (int a = 0; a < d; ++a) max_n = std::max(max_n, fd[k].n[a]);
+  const int fdk = dl.arith <= 1 ? dl.arith : (max_n >= 160 ? dl.arith : 1);
+  dl.fd_kind = fdk;
   // U pool
   Vec Upool;
   std::vector<std::array<int64_t, 3>> uoff(L.K);
@@ -323,6 +338,12 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   char* T1 = reinterpret_cast<char*>(A.alloc<double>((size_t)std::max<int64_t>(tsize, 1)));
   char* T2 = reinterpret_cast<char*>(A.alloc<double>((size_t)std::max<int64_t>(tsize, 1)));
   const int tU = f32 ? 1 : 0;
+  // TF32 path: every operand FP32 in memory (the residual copied to FP32 before the first step)
+  float* r32 = nullptr;
+  if (fdk == 2 && d == 3) {
+    r32 = A.alloc<float>((size_t)L.nloc + 8);
+    dl.r32 = r32;
+  }
   std::vector<GemmTask> tasks;
   std::vector<GemmItem> items;
   dl.fd_steps.clear();
@@ -333,8 +354,8 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     for (const auto& g : st) {
       const int id = (int)tasks.size();
       tasks.push_back(g);
-      const int bm = dl.arith >= 2 ? 128 : gemm_tile(dl.arith);  // tensor-core tiles are 128 x 64
-      const int bn = dl.arith >= 2 ? 64 : bm;
+      const int bm = fdk >= 2 ? 128 : gemm_tile(fdk);  // tensor-core tiles are 128 x 64
+      const int bn = fdk >= 2 ? 64 : bm;
       const int tm = (g.M + bm - 1) / bm, tn = (g.N + bn - 1) / bn;
       for (int z = 0; z < g.batch; ++z)
         for (int a = 0; a < tm; ++a)
@@ -352,9 +373,63 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     g.dinv = nullptr;
     g.ldd = 0;
     g.tA = g.tB = g.tC = 0;
+    g.vec = g.ctrans = 0;
     return g;
   };
   const int nsteps = d == 2 ? 4 : 6;
+  // TF32 in 2D: every operand K-major with rows padded to a multiple of 4 floats (16-byte copies):
+  // transposed copies of U_0 and U_1, the outputs of steps 1 and 3 stored transposed, and the
+  // residual's interiors gathered into compact FP32 blocks before the first step
+  const bool vec2d = fdk == 2 && d == 2;
+  auto ld4 = [](int n) { return (n + 3) / 4 * 4; };
+  std::vector<std::array<int64_t, 4>> voff(L.K);  // U0, U0^T, U1, U1^T in the vec pool
+  std::vector<std::array<int64_t, 4>> toffv(L.K);  // Rc, C1^T, X, Y^T in the temporary pool
+  float* vU = nullptr;
+  float* vT = nullptr;
+  if (vec2d) {
+    std::vector<float> pool;
+    int64_t tsz = 0;
+    for (int k = 0; k < L.K; ++k) {
+      const int n0 = fd[k].n[0], n1 = fd[k].n[1];
+      auto put = [&](const Vec& U, int n, bool transpose) {
+        const int64_t off = (int64_t)pool.size();
+        pool.resize(pool.size() + (size_t)n * ld4(n), 0.0f);
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j)
+            pool[off + (size_t)i * ld4(n) + j] = (float)(transpose ? U[(size_t)j * n + i] : U[(size_t)i * n + j]);
+        return off;
+      };
+      voff[k] = {put(fd[k].U[0], n0, false), put(fd[k].U[0], n0, true), put(fd[k].U[1], n1, false),
+                 put(fd[k].U[1], n1, true)};
+      toffv[k][0] = tsz; tsz += (int64_t)n1 * ld4(n0);  // Rc: n1 x n0
+      toffv[k][1] = tsz; tsz += (int64_t)n0 * ld4(n1);  // C1^T: n0 x n1
+      toffv[k][2] = tsz; tsz += (int64_t)n1 * ld4(n0);  // X: n1 x n0
+      toffv[k][3] = tsz; tsz += (int64_t)n0 * ld4(n1);  // Y^T: n0 x n1
+    }
+    vU = A.upload(pool);
+    vT = A.alloc<float>((size_t)std::max<int64_t>(tsz, 4));
+    CK(cudaMemset(vT, 0, (size_t)std::max<int64_t>(tsz, 4) * sizeof(float)));  // padding columns stay 0
+    std::vector<int64_t> e_ptr(1, 0), ib, doff;
+    std::vector<int> n0s, N0s, dld;
+    for (int k = 0; k < L.K; ++k) {
+      const int n0 = fd[k].n[0], n1 = fd[k].n[1];
+      e_ptr.push_back(e_ptr.back() + (int64_t)n0 * n1);
+      ib.push_back(L.off[k] + 1 + L.N[k][0]);
+      n0s.push_back(std::max(n0, 1));
+      N0s.push_back(L.N[k][0]);
+      doff.push_back(toffv[k][0]);
+      dld.push_back(ld4(n0));
+    }
+    dl.rc = vT;
+    dl.rc_n = L.K;
+    dl.rc_total = e_ptr.back();
+    dl.rc_eptr = A.upload(e_ptr);
+    dl.rc_ibase = A.upload(ib);
+    dl.rc_n0 = A.upload(n0s);
+    dl.rc_N0 = A.upload(N0s);
+    dl.rc_off = A.upload(doff);
+    dl.rc_ld = A.upload(dld);
+  }
   std::vector<std::vector<GemmTask>> steps(nsteps);
   for (int k = 0; k < L.K; ++k) {
     const int n0 = fd[k].n[0], n1 = fd[k].n[1], n2 = d == 3 ? fd[k].n[2] : 1;
@@ -370,10 +445,35 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     GemmTask g{};
     // element types: U and temporaries tU; r (first input) and u (last output) double
     auto types = [&](GemmTask& t, int ta, int tb, int tc) { t.tA = ta; t.tB = tb; t.tC = tc; };
-    if (d == 2) {
-      // 1) T = R U0   (R: n1 x n0 rows of the interior, ld N0)
-      g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = dl.r + ibase; g.lda = N0; g.B = U0; g.ldb = n0;
-      g.C = Tk; g.ldc = n0; g.ndiv = n0; types(g, 0, tU, tU); steps[0].push_back(g);
+    if (vec2d) {
+      const float* U0v = vU + voff[k][0];
+      const float* U0t = vU + voff[k][1];
+      const float* U1v = vU + voff[k][2];
+      const float* U1t = vU + voff[k][3];
+      float* Rc = vT + toffv[k][0];
+      float* C1t = vT + toffv[k][1];
+      float* Xv = vT + toffv[k][2];
+      float* Yt = vT + toffv[k][3];
+      auto vtask = [&](GemmTask t) { t.vec = 1; t.transA = 0; t.transB = 1; t.tA = t.tB = 1; return t; };
+      // 1) C1 = R U0, stored transposed
+      g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = Rc; g.lda = ld4(n0); g.B = U0t; g.ldb = ld4(n0);
+      g.C = C1t; g.ldc = ld4(n1); g.ctrans = 1; g.ndiv = n0; g.tC = 1; steps[0].push_back(vtask(g));
+      // 2) X = (U1^T C1) * dinv
+      g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1t; g.lda = ld4(n1); g.B = C1t; g.ldb = ld4(n1);
+      g.C = Xv; g.ldc = ld4(n0); g.ndiv = n0; g.epi = 1; g.dinv = Dk; g.ldd = n0; g.tC = 1;
+      steps[1].push_back(vtask(g));
+      // 3) Y = X U0^T, stored transposed
+      g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = Xv; g.lda = ld4(n0); g.B = U0v; g.ldb = ld4(n0);
+      g.C = Yt; g.ldc = ld4(n1); g.ctrans = 1; g.ndiv = n0; g.tC = 1; steps[2].push_back(vtask(g));
+      // 4) u_interior += tau U1 Y
+      g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1v; g.lda = ld4(n1); g.B = Yt; g.ldb = ld4(n1);
+      g.C = dl.u + ibase; g.ldc = N0; g.ndiv = n0; g.epi = 2; g.alpha = tau; g.tC = 0;
+      steps[3].push_back(vtask(g));
+    } else if (d == 2) {
+      // 1) T = R U0   (R: n1 x n0 rows of the interior, ld N0; its FP32 copy on the TF32 path)
+      g = base(g); g.M = n1; g.N = n0; g.K = n0; g.lda = N0; g.B = U0; g.ldb = n0;
+      if (r32) { g.A = r32 + ibase; types(g, 1, tU, tU); } else { g.A = dl.r + ibase; types(g, 0, tU, tU); }
+      g.C = Tk; g.ldc = n0; g.ndiv = n0; steps[0].push_back(g);
       // 2) X = U1^T T, divided by lambda1[m] + lambda0[n] + sigma
       g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.transA = 1; g.lda = n1; g.B = Tk; g.ldb = n0;
       g.C = Xk; g.ldc = n0; g.ndiv = n0; g.epi = 1; g.dinv = Dk; g.ldd = n0; types(g, tU, tU, tU);
@@ -387,8 +487,9 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     } else {
       const int64_t plane = (int64_t)n1 * n0;
       // 1) T[i2] = R[i2] U0  (batched over planes i2)
-      g = base(g); g.M = n1; g.N = n0; g.K = n0; g.A = dl.r + ibase; g.lda = N0; g.sA = N01; g.B = U0; g.ldb = n0;
-      g.C = Tk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; types(g, 0, tU, tU); steps[0].push_back(g);
+      g = base(g); g.M = n1; g.N = n0; g.K = n0; g.lda = N0; g.sA = N01; g.B = U0; g.ldb = n0;
+      if (r32) { g.A = r32 + ibase; types(g, 1, tU, tU); } else { g.A = dl.r + ibase; types(g, 0, tU, tU); }
+      g.C = Tk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; steps[0].push_back(g);
       // 2) X[i2] = U1^T T[i2]
       g = base(g); g.M = n1; g.N = n0; g.K = n1; g.A = U1; g.transA = 1; g.lda = n1; g.B = Tk; g.ldb = n0;
       g.sB = plane; g.C = Xk; g.ldc = n0; g.sC = plane; g.ndiv = n0; g.batch = n2; types(g, tU, tU, tU); steps[1].push_back(g);
@@ -409,6 +510,7 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   }
   for (auto& s : steps) add_step(s);
   (void)lvl;
+  if (fdk <= 1) CK(prepare_gemm());
   // small 2D interiors: all four contractions of a patch in one CTA (shared memory), unless
   // MGIGA_FD_FUSE=0 (kept for testing the batched-GEMM path on small problems)
   const char* fuse_env = std::getenv("MGIGA_FD_FUSE");
@@ -944,10 +1046,12 @@ void matvec(mgiga_handle* h, int l, const double* u, double* out) {
 // one step of the fast diagonalisation: SIMT tiles (FP64 / FP32) or tensor-core tiles (TF32 / BF16)
 void run_fd_step(mgiga_handle* h, DLevel& d, size_t i) {
   const auto& s = d.fd_steps[i];
-  if (d.arith >= 2)
-    launch_gemm_umma(s.second - s.first, d.arith - 2, h->stream, d.fd_tasks, d.fd_items + s.first, h->gs_err);
+  if (d.fd_kind == 2)
+    launch_gemm_umma_tf32(s.second - s.first, h->stream, d.fd_tasks, d.fd_items + s.first, h->gs_err);
+  else if (d.fd_kind == 3)
+    launch_gemm_umma(s.second - s.first, 1, h->stream, d.fd_tasks, d.fd_items + s.first, h->gs_err);
   else
-    launch_gemm(s.second - s.first, d.arith, d.fd_step_ta[i], h->stream, d.fd_tasks, d.fd_items + s.first);
+    launch_gemm(s.second - s.first, d.fd_kind, d.fd_step_ta[i], h->stream, d.fd_tasks, d.fd_items + s.first);
 }
 
 // the interior part of the smoother: fused per patch on small 2D levels, else the batched GEMM steps
@@ -956,6 +1060,10 @@ void run_fd(mgiga_handle* h, DLevel& d) {
     launch_fd_small(d.fd_small_n, d.fd_small_smem, d.arith >= 1, h->stream, d.fd_small, d.r, d.u, h->opt.tau);
     return;
   }
+  if (d.r32) launch_to_f32(d.nloc, h->stream, d.r, d.r32);
+  if (d.rc)
+    launch_gather_interior_f32(d.rc_n, d.rc_total, h->stream, d.rc_eptr, d.rc_ibase, d.rc_n0, d.rc_N0, d.rc_off,
+                               d.rc_ld, d.r, d.rc);
   for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
 }
 

@@ -126,3 +126,24 @@ def test_cycle_residual_within_fp32_rounding(name):
         assert np.all(np.abs(got - ref) <= bound), (l, float(np.max(np.abs(got - ref) / bound)))
         # FP64 precision keeps the FP64 residual
     lib.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("name", ["conf2d_p2", "sipg2d_p3"])
+def test_mixed_smoother_batched_contractions(name, precision, monkeypatch):
+    """2D interiors this small take the fused one-CTA path; force the batched
+    contractions (on TF32: K-major 16-byte-copy tasks with transposed outputs)."""
+    monkeypatch.setenv("MGIGA_FD_FUSE", "0")
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    lib = binding().Solver(prob, levels=levels, smoother="hybrid", precision=precision, **opt)
+    orc = omg.Multigrid(prob, levels=levels, smoother="hybrid", **opt)
+    rng = np.random.default_rng(12)
+    for l in range(1, levels):
+        A = orc.h["A"][l]
+        n = A.shape[0]
+        u, f = rng.standard_normal(n), rng.standard_normal(n)
+        ref = u + orc.scms[l].apply(f - A @ u)
+        got = lib.apply("smooth", l, f, u)
+        assert np.linalg.norm(got - ref) <= smooth_tol(precision, prob["dim"]) * np.linalg.norm(ref - u), l
+    lib.close()

@@ -47,7 +47,28 @@ def hbm_peak_gbs():
 # finest level, per degree, from one ncu capture of this build on a GB300 (profiles/
 # traffic_sipg3x3_finest_level.md gives the command and the per-kernel figures).  Used only for the
 # default workload (scale 3, hybrid, FP32 smoothers); None elsewhere or when a stage's kernels change.
-DRAM_TRAFFIC = {}
+DRAM_TRAFFIC = {
+    ("band", 2): 1.094e+08,
+    ("residual", 2): 6.325e+07,
+    ("fd", 2): 2.507e+07,
+    ("gs", 2): 8.22e+07,
+    ("band", 3): 2.139e+08,
+    ("residual", 3): 1.153e+08,
+    ("fd", 3): 2.528e+07,
+    ("gs", 3): 1.362e+08,
+    ("band", 4): 3.533e+08,
+    ("residual", 4): 1.851e+08,
+    ("fd", 4): 2.551e+07,
+    ("gs", 4): 2.092e+08,
+    ("band", 5): 5.292e+08,
+    ("residual", 5): 2.732e+08,
+    ("fd", 5): 2.569e+07,
+    ("gs", 5): 3.075e+08,
+    ("band", 6): 7.441e+08,
+    ("residual", 6): 3.802e+08,
+    ("fd", 6): 2.59e+07,
+    ("gs", 6): 4.14e+08,
+}
 
 
 def dram_traffic(stage, degrees, args, f32):

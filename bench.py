@@ -5,8 +5,9 @@ interior vertices, 192 / 288 intervals per direction (alternating, so the
 interface knots do not match), degrees p = 2..6, penalty 5 (p+1)^2 / h, hybrid
 smoother (forward Gauss-Seidel + subspace-corrected mass smoother, tau .25,
 delta .1), PCG to ||f - A u|| / ||f|| <= 1e-8.  One step solves all five
-degrees once (0.52-0.54M unknowns each); value = unknowns solved / second over
-the whole job.  Inputs are resident in HBM before the timed region; every
+degrees once (0.52-0.54M unknowns each), the five independent solves concurrently
+(a CUDA stream and a host thread each; --sequential: one after another); value =
+unknowns solved / second over the whole job.  Inputs are resident in HBM before the timed region; every
 solve starts from u = 0.  The working set (five band matrices, 106 MB-730 MB
 each) exceeds L2, so no explicit flush is needed.
 
@@ -94,6 +95,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain-FP64 comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sequential", action="store_true",
+                    help="solve the degrees one after another (default: concurrently, a stream each)")
     return ap.parse_args()
 
 
@@ -259,8 +262,11 @@ def main():
     from paper_1902_01818_gb300 import mgiga
 
     degrees = [int(x) for x in args.degrees.split(",")]
-    stream = torch.cuda.Stream()  # all library work and the timing events live on this stream
+    stream = torch.cuda.Stream()  # the timing events live on this stream
     torch.cuda.set_stream(stream)
+    # one stream per degree (and precision): the independent solves of a step run concurrently,
+    # one host thread each, unless --sequential
+    streams = {}
     solvers, rhs_d, u_d, rhs_h, u_h, ndofs = [], [], [], [], [], []
     t_setup = time.perf_counter()
     precisions = [args.precision] + ([] if args.no_fp64_compare or args.precision == "fp64" else ["fp64"])
@@ -268,9 +274,10 @@ def main():
     for p in degrees:
         prob, opts = workload(p, args.scale, args.smoother)
         for pr in precisions:
+            streams[(p, pr)] = torch.cuda.Stream()
             handles[pr].append(mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"],
                                             tau=opts["tau"], delta=opts["delta"], precision=pr,
-                                            stream=stream.cuda_stream))
+                                            stream=streams[(p, pr)].cuda_stream))
         s = handles[args.precision][-1]
         f = s.load_sinprod()
         ndofs.append(len(f))
@@ -284,9 +291,17 @@ def main():
     print(f"set-up (assembly, hierarchy, smoother data, upload) of {len(degrees) * len(precisions)} handles: "
           f"{t_setup:.1f} s", file=sys.stderr, flush=True)
 
-    def step(host_path=False, which=None):
-        info = []
-        for i, s in enumerate(which if which is not None else solvers):
+    # concurrency is safe when no sweep needs the grid-wide (cooperative) kernel: the base colours
+    # cover every DoF on every level (true for this layout; checked, not assumed)
+    def coop_free(s, p):
+        base = 2 * (p + 1) ** 2
+        return all(int(s.colours(l).max()) < base for l in range(1, s.levels))
+
+    concurrent = not args.sequential and all(coop_free(s, p) for s, p in zip(solvers, degrees))
+
+    def solve_one(i, s, host_path, out):
+        st_ = streams[(degrees[i], s.precision)]
+        with torch.cuda.stream(st_):
             if host_path:
                 u_h[i].zero_()
                 u, it, rel, st = s.solve(rhs_h[i].numpy(), u0=u_h[i].numpy(), tol=1e-8)
@@ -294,8 +309,30 @@ def main():
             else:
                 u_d[i].zero_()
                 it, rel, st = s.solve_d(rhs_d[i], u_d[i], tol=1e-8)
-            info.append((it, rel))
-        return info
+        out[i] = (it, rel)
+
+    def step(host_path=False, which=None):
+        which = which if which is not None else solvers
+        out = [None] * len(which)
+        # worker streams start after everything enqueued on the timing stream so far
+        start = torch.cuda.Event()
+        start.record(stream)
+        for i, s in enumerate(which):
+            streams[(degrees[i], s.precision)].wait_event(start)
+        if concurrent and all(s.precision != "fp64" for s in which):
+            ths = [threading.Thread(target=solve_one, args=(i, s, host_path, out)) for i, s in enumerate(which)]
+            for t in ths:
+                t.start()
+            for t in ths:
+                t.join()
+        else:
+            for i, s in enumerate(which):
+                solve_one(i, s, host_path, out)
+        for i, s in enumerate(which):  # the timing stream continues after every solve
+            done = torch.cuda.Event()
+            done.record(streams[(degrees[i], s.precision)])
+            stream.wait_event(done)
+        return out
 
     for _ in range(args.warmup):
         step()
@@ -350,7 +387,22 @@ def main():
         torch.cuda.synchronize()
         ms64 = e_a.elapsed_time(e_b)
         plain = {"value": total_dof / (ms64 / 1e3), "unit": "DoF/s", "ms_per_step": ms64,
-                 "iterations": [x[0] for x in info64], "final_relres": [x[1] for x in info64]}
+                 "iterations": [x[0] for x in info64], "final_relres": [x[1] for x in info64],
+                 "solves": "sequential (the FP64 sweep is a grid-wide cooperative launch)"}
+    # the mixed path solved one degree after another, for comparison with the FP64 figure
+    mixed_seq = None
+    if concurrent:
+        concurrent = False
+        step()
+        torch.cuda.synchronize()
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record()
+        step()
+        e_b.record()
+        torch.cuda.synchronize()
+        concurrent = True
+        mixed_seq = {"value": total_dof / (e_a.elapsed_time(e_b) / 1e3), "unit": "DoF/s",
+                     "ms_per_step": e_a.elapsed_time(e_b), "solves": "sequential"}
 
     # roofline per stage on the finest level of every degree (times summed over the degrees); the
     # stage with the largest share of a PCG iteration (count x time) is reported.  Per PCG iteration
@@ -408,8 +460,11 @@ def main():
                        "step_ms_p50": float(np.percentile(step_ms, 50)),
                        "step_ms_p99": float(np.percentile(step_ms, 99)),
                        "l2": "inputs larger than L2 (0.9-3.7 GB operators per step)",
-                       "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1)},
+                       "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1),
+                       "solves": ("concurrent: one CUDA stream and host thread per degree" if concurrent
+                                  else "sequential")},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "plain_fp64": plain,
+            "mixed_sequential": mixed_seq,
             "clocks": clk.summary()}
     if cpu is not None:
         line["cpu_baseline"] = cpu

@@ -143,6 +143,7 @@ class Solver:
     def __init__(self, prob, levels=0, smoother="scms", tau=1.0, delta=0.12, nu=1, mu=1, outer="pcg",
                  precision="fp64", max_iter=1000, hbm_budget=0, stream=None, assemble=True):
         self.prob = prob
+        self.precision = precision
         cp, self._keep = marshal_problem(prob)
         opts = _Options()
         _lib.mgiga_default_options(C.byref(opts))

@@ -34,7 +34,7 @@ def _corner_index(bits):
 
 def grid_problem(cells, n, p, coupling, box=None, jitter=0.0, seed=0,
                  jitter_boundary_tangential=False, penalty_factor=5.0,
-                 flip_patches=(), transpose_patches=()):
+                 flip_patches=(), transpose_patches=(), active=None):
     """Grid of cells[0] x ... multilinear patches covering the box [0, box_a].
 
     n: intervals per direction, an int or a callable (patch grid multi-index,
@@ -45,7 +45,9 @@ def grid_problem(cells, n, p, coupling, box=None, jitter=0.0, seed=0,
     flip_patches: patch ids whose first parameter direction is reversed;
     transpose_patches: patch ids whose first two parameter directions are
        swapped.  Both exercise the interface orientation bits.
-    Patch ids are row-major over the cell grid (first direction fastest).
+    active: optional set of cell multi-indices to keep (a non-rectangular
+       arrangement); vertices on the boundary of the kept cells are not jittered.
+    Patch ids are row-major over the (kept) cell grid (first direction fastest).
     """
     d = len(cells)
     box = tuple(float(b) for b in (box if box is not None else cells))
@@ -56,8 +58,22 @@ def grid_problem(cells, n, p, coupling, box=None, jitter=0.0, seed=0,
         vidx = tuple(reversed(vidx))  # first index fastest
         x = np.array([box[a] * vidx[a] / cells[a] for a in range(d)])
         verts[vidx] = x
+    keep = None if active is None else set(tuple(c) for c in active)
+
+    def interior_vertex(vidx):
+        # a vertex inside the domain: every cell around it is kept
+        for off in itertools.product(*[(-1, 0)] * d):
+            c = tuple(vidx[a] + off[a] for a in range(d))
+            if any(c[a] < 0 or c[a] >= cells[a] for a in range(d)) or (keep is not None and c not in keep):
+                return False
+        return True
+
     for vidx in sorted(verts, key=lambda v: tuple(reversed(v))):
         on_bnd = [vidx[a] in (0, cells[a]) for a in range(d)]
+        if keep is not None:
+            if interior_vertex(vidx):
+                verts[vidx] = verts[vidx] + rng.uniform(-jitter, jitter, size=d)
+            continue
         if not any(on_bnd):
             verts[vidx] = verts[vidx] + rng.uniform(-jitter, jitter, size=d)
         elif jitter_boundary_tangential and not all(on_bnd):
@@ -69,6 +85,8 @@ def grid_problem(cells, n, p, coupling, box=None, jitter=0.0, seed=0,
 
     knots, geo_knots, geo_ctrl, corner_vertex = [], [], [], []
     cell_list = [tuple(reversed(c)) for c in itertools.product(*[range(c) for c in reversed(cells)])]
+    if keep is not None:
+        cell_list = [c for c in cell_list if c in keep]
     for pid, cidx in enumerate(cell_list):
         perm = list(range(d))
         if pid in transpose_patches:
@@ -211,3 +229,28 @@ def cube_2x2x2(p, coupling, n=48):
                         seed=301 + (p - 3), jitter_boundary_tangential=True)
     opts = dict(levels=0, smoother="hybrid", tau=0.25, delta=0.12, nu=1)
     return prob, opts
+
+
+def batched_problem(seed):
+    """One problem of the batched layout (seeded): K ~ U{1..16} unit-square
+    patches in ceil(sqrt(K)) columns filled row-major (the last row may be
+    partial), intervals per direction log-uniform in [16, 256] rounded to the
+    nearest c 2^j with c in {4..7} (so the hierarchy has >= 2 levels with >= 4
+    intervals on the coarsest), p ~ U{2..5}, conforming or SIPG with
+    probability 1/2, vertices inside the domain jittered U[-.1, .1]^2, hybrid
+    smoother (tau .25, delta .1), PCG; the right-hand side is i.i.d. N(0, 1)
+    load coefficients (seed + 1000).  Returns (problem, options, rhs seed)."""
+    rng = np.random.default_rng(seed)
+    K = int(rng.integers(1, 17))
+    cols = int(np.ceil(np.sqrt(K)))
+    rows = (K + cols - 1) // cols
+    active = [(i % cols, i // cols) for i in range(K)]
+    n_raw = float(np.exp(rng.uniform(np.log(16.0), np.log(256.0))))
+    cands = [c * 2 ** j for c in range(4, 8) for j in range(0, 7) if 16 <= c * 2 ** j <= 256]
+    n = int(min(cands, key=lambda v: (abs(v - n_raw), v)))
+    p = int(rng.integers(2, 6))
+    coupling = "conforming" if rng.uniform() < 0.5 else "sipg"
+    prob = grid_problem((cols, rows), n, p, coupling, box=(float(cols), float(rows)), jitter=0.1,
+                        seed=seed, active=active)
+    opts = dict(levels=0, smoother="hybrid", tau=0.25, delta=0.1, nu=1)
+    return prob, opts, seed + 1000

@@ -107,3 +107,18 @@ def test_conforming_numbering_order_and_sharing():
     # patch 1 shares its xi0 = 0 side with patch 0's xi0 = 1 side
     assert list(num["loc2glob"][1]) == [-1, -1, -1, 1, 2, -1, -1, -1, -1]
     assert num["ndof"] == 3
+
+
+def test_batched_layout_non_rectangular_problem_is_spd():
+    """A batched-layout problem with a partial last row of patches (seed 407:
+    3 SIPG patches): the oracle assembles a symmetric positive definite matrix,
+    every patch side shared by two patches is an interface, the others Dirichlet."""
+    from paper_1902_01818_gb300 import workloads as W
+    import scipy.sparse.linalg as spla
+    prob, opts, _ = W.batched_problem(407)
+    assert len(prob["knots"]) == 3 and len(prob["interfaces"]) == 2
+    num = discretize.numbering(prob, prob["knots"])
+    A = discretize.assemble_global(prob, prob["knots"], num)
+    assert abs(A - A.T).max() <= 1e-12 * abs(A).max()
+    lam = spla.eigsh(A, k=1, sigma=0, which="LM", return_eigenvectors=False)
+    assert lam[0] > 0

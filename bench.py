@@ -4,7 +4,8 @@ Workload (default): [0,3]^2 as 3x3 SIPG-coupled bilinear patches with jittered
 interior vertices, 192 / 288 intervals per direction (alternating, so the
 interface knots do not match), degrees p = 2..6, penalty 5 (p+1)^2 / h, hybrid
 smoother (forward Gauss-Seidel + subspace-corrected mass smoother, tau .25,
-delta .1), PCG to ||f - A u|| / ||f|| <= 1e-8.  One step solves all five
+delta .1), PCG to ||f - A u|| / ||f|| <= 1e-8; mixed precision by default (TF32 tensor-core
+contractions on the large levels, FP32 smoothers, FP64 CG and coarse solve).  One step solves all five
 degrees once (0.52-0.54M unknowns each), the five independent solves concurrently
 (a CUDA stream and a host thread each; --sequential: one after another); value =
 unknowns solved / second over the whole job.  Inputs are resident in HBM before the timed region; every
@@ -73,12 +74,20 @@ DRAM_TRAFFIC = {
 
 
 def dram_traffic(stage, degrees, args, f32):
-    if not (f32 and args.scale == 3 and args.smoother == "hybrid"):
+    if not (args.precision == "fp32" and args.scale == 3 and args.smoother == "hybrid"):
         return None
     vals = [DRAM_TRAFFIC.get((stage, p)) for p in degrees]
     if any(v is None for v in vals):
         return None
     return sum(vals) / len(vals)
+
+
+def bf16_peak_tflops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops_sustained"]), "of measured (sustained)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "of fallback (sustained)"
 
 
 def parse():
@@ -90,7 +99,7 @@ def parse():
     ap.add_argument("--degrees", default="2,3,4,5,6")
     ap.add_argument("--scale", type=int, default=3, help="interval multiplier of 64/96 (3: 192/288)")
     ap.add_argument("--smoother", default="hybrid", choices=["scms", "hybrid"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+    ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16", "fp64"],
                     help="smoother arithmetic of the timed path (CG is FP64 either way)")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain-FP64 comparison solves")
@@ -409,14 +418,16 @@ def main():
     # on the finest level: one FP64 band product (CG), three residuals inside the cycle (FP32 band on
     # the mixed path), two fast diagonalisations and, with the hybrid smoother, two Gauss-Seidel sweeps.
     hbm, hbm_src = hbm_peak_gbs()
-    f32 = args.precision == "fp32"
+    f32 = args.precision != "fp64"
     hybrid = args.smoother == "hybrid"
     counts = ({"band": 1, "residual": 3, "fd": 2, "gs": 2 if hybrid else 0} if f32 else
               {"band": 4, "fd": 2, "gs": 2 if hybrid else 0})
     names = {"band": "band_apply (FP64 band product)",
              "residual": "band_residual_f32 + cross_apply (residual inside the cycle, FP32 band)",
-             "fd": ("gemm_tiled (fast diagonalisation, FP32)" if f32 else
-                    "gemm_tiled (fast diagonalisation, FP64)"),
+             "fd": {"fp32": "gemm_tiled (fast diagonalisation, FP32)",
+                    "tf32": "gather_interior_f32 + gemm_umma_tf32 (fast diagonalisation, TF32 tensor cores)",
+                    "bf16": "gemm_umma (fast diagonalisation, BF16 tensor cores)"}.get(
+                        args.precision, "gemm_tiled (fast diagonalisation, FP64)"),
              "gs": ("gs_fill_phase + gs_patch_staged (one Gauss-Seidel sweep, FP32)" if f32 else
                     "gs_sweep_coop (one Gauss-Seidel sweep, FP64)")}
     stages = {}
@@ -432,6 +443,12 @@ def main():
         if st in ("band", "fd") and not (st == "fd" and f32):
             rec = {"bound": "alu", "achieved": fl / (t_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
+        elif st == "fd" and args.precision in ("tf32", "bf16"):
+            bf16, src = bf16_peak_tflops()
+            ratio = 0.5 if args.precision == "tf32" else 1.0  # nominal dense TF32 / BF16 = 1.1 / 2.25
+            rec = {"bound": "tensor", "achieved": fl / (t_ms / 1e3) / 1e12, "peak": bf16 * ratio,
+                   "unit": "TFLOP/s", "peak_source": src + (" (bf16 x nominal tf32/bf16 ratio 0.5)"
+                                                         if ratio != 1.0 else "")}
         elif st == "fd":
             rec = {"bound": "alu", "achieved": fl / (t_ms / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 x 2.07 GHz"}
@@ -452,10 +469,15 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if f32 else "f64", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": {"fp32": "f32+f64", "tf32": "tf32+f32+f64", "bf16": "bf16+f32+f64"}.get(args.precision, "f64"),
+            "data": "synthetic",
             "config": {"workload": f"sipg-3x3-[0,3]^2-jitter0.1-{64 * args.scale}/{96 * args.scale}-intervals",
                        "degrees": degrees, "unknowns": ndofs, "smoother": args.smoother, "outer": "pcg",
-                       "precision": ("fp32 smoothers, fp64 residual/CG/coarse" if f32 else "fp64"),
+                       "precision": {"fp32": "fp32 smoothers, fp64 CG/coarse",
+                                     "tf32": "tf32 contractions on large levels, fp32 smoothers, fp64 CG/coarse",
+                                     "bf16": "bf16 contractions on large levels, fp32 smoothers, fp64 CG/coarse"
+                                     }.get(args.precision, "fp64"),
                        "tol": 1e-8, "iterations": iters, "final_relres": rels,
                        "step_ms_p50": float(np.percentile(step_ms, 50)),
                        "step_ms_p99": float(np.percentile(step_ms, 99)),

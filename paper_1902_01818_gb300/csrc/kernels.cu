@@ -713,14 +713,27 @@ __global__ void __launch_bounds__(128) gemm_umma(const GemmTask* __restrict__ ta
 // lanes 32 (w mod 4).. and columns 32 (w / 4)...  Every wait is bounded.
 // ---------------------------------------------------------------------------
 constexpr int kUmmaStages = 4;
-constexpr int kUmmaTf32Smem = kUmmaStages * (UM + UN) * UKB;
+// core matrices of one 8-row group 144 B apart along K (not 128): the eight 16-byte copies that
+// fill one row's slab then land in distinct shared-memory banks; 8-row groups 8 x 144 B apart
+constexpr int kTfLbo = 144, kTfSbo = 8 * kTfLbo;
+constexpr int kTfA = (UM / 8) * kTfSbo, kTfB = (UN / 8) * kTfSbo;  // bytes of one slab of A / B
+constexpr int kUmmaTf32Smem = kUmmaStages * (kTfA + kTfB);
+
+__device__ __forceinline__ uint64_t umma_sdesc_tf(unsigned saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);             // start address
+  d |= (uint64_t)((kTfLbo >> 4) & 0x3FFFu) << 16;      // leading byte offset: next core matrix along K
+  d |= (uint64_t)((kTfSbo >> 4) & 0x3FFFu) << 32;      // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                              // descriptor version (tcgen05)
+  return d;                                            // base offset 0, no swizzle
+}
 
 __global__ void __launch_bounds__(256) gemm_umma_tf32(const GemmTask* __restrict__ tasks,
                                                       const GemmItem* __restrict__ items, int* err) {
   constexpr int KT = UKB / 4;  // K elements per slab
   extern __shared__ __align__(1024) unsigned char usm[];
-  auto sA = [&](int b) { return usm + b * (UM * UKB); };
-  auto sB = [&](int b) { return usm + kUmmaStages * UM * UKB + b * (UN * UKB); };
+  auto sA = [&](int b) { return usm + b * kTfA; };
+  auto sB = [&](int b) { return usm + kUmmaStages * kTfA + b * kTfB; };
   __shared__ __align__(8) unsigned long long mbar[kUmmaStages];
   __shared__ unsigned tmem_slot;
   const GemmItem it = items[blockIdx.x];
@@ -750,7 +763,9 @@ __global__ void __launch_bounds__(256) gemm_umma_tf32(const GemmTask* __restrict
   const int64_t sAm = g.transA ? 1 : g.lda, sAk = g.transA ? g.lda : 1;
   const int64_t sBn = g.transB ? g.ldb : 1, sBk = g.transB ? 1 : g.ldb;
   // element (row, kk) of a slab in the core-matrix layout: 8-row groups of 1024 B, 16-byte column groups
-  auto cm_off = [](int row, int kk) { return (row >> 3) * 1024 + (kk >> 2) * 128 + (row & 7) * 16 + (kk & 3) * 4; };
+  auto cm_off = [](int row, int kk) {
+    return (row >> 3) * kTfSbo + (kk >> 2) * kTfLbo + (row & 7) * 16 + (kk & 3) * 4;
+  };
   auto load = [&](int st) {
     const int b = st % kUmmaStages, k0 = st * KT;
     unsigned char* a = sA(b);
@@ -813,7 +828,7 @@ __global__ void __launch_bounds__(256) gemm_umma_tf32(const GemmTask* __restrict
       const unsigned a0 = smem_u32(sA(b)), b0 = smem_u32(sB(b));
 #pragma unroll
       for (int j = 0; j < UKB / 32; ++j) {
-        const uint64_t ad = umma_sdesc(a0 + 256 * j), bd = umma_sdesc(b0 + 256 * j);
+        const uint64_t ad = umma_sdesc_tf(a0 + 2 * kTfLbo * j), bd = umma_sdesc_tf(b0 + 2 * kTfLbo * j);
         const unsigned acc = (st > 0 || j > 0) ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"

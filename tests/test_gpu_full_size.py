@@ -72,10 +72,11 @@ def test_benchmark_layout_full_size(p):
     assert lib64.ndof() > 500_000
     assert _sample_error(prob, lib64, u64) <= 1e-4
     lib64.close()
-    lib32, u32, it32 = _solve(prob, opts, "fp32")
-    assert it32 <= it64 + 2, (it32, it64)
-    assert _sample_error(prob, lib32, u32) <= 1e-4
-    lib32.close()
+    for prec in ("fp32", "tf32"):
+        lib32, u32, it32 = _solve(prob, opts, prec)
+        assert it32 <= it64 + 2, (prec, it32, it64)
+        assert _sample_error(prob, lib32, u32) <= 1e-4
+        lib32.close()
 
 
 @pytest.mark.parametrize("coupling", ["conforming", "sipg"])

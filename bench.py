@@ -48,7 +48,8 @@ def hbm_peak_gbs():
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one application of a stage on the
 # finest level, per degree, from one ncu capture of this build on a GB300 (profiles/
 # traffic_sipg3x3_finest_level.md gives the command and the per-kernel figures).  Used only for the
-# default workload (scale 3, hybrid, FP32 smoothers); None elsewhere or when a stage's kernels change.
+# default workload (scale 3, hybrid; the band, residual and GS kernels are the same in the FP32 and
+# TF32 modes, the contractions only in FP32); None elsewhere or when a stage's kernels change.
 DRAM_TRAFFIC = {
     ("band", 2): 1.094e+08,
     ("residual", 2): 6.325e+07,
@@ -74,7 +75,9 @@ DRAM_TRAFFIC = {
 
 
 def dram_traffic(stage, degrees, args, f32):
-    if not (args.precision == "fp32" and args.scale == 3 and args.smoother == "hybrid"):
+    if not (args.scale == 3 and args.smoother == "hybrid" and args.precision in ("fp32", "tf32")):
+        return None
+    if stage == "fd" and args.precision != "fp32":  # the table's contractions are the FP32 SIMT ones
         return None
     vals = [DRAM_TRAFFIC.get((stage, p)) for p in degrees]
     if any(v is None for v in vals):

@@ -287,9 +287,11 @@ def main():
         prob, opts = workload(p, args.scale, args.smoother)
         for pr in precisions:
             streams[(p, pr)] = torch.cuda.Stream()
+            # concurrent solves: 8-CTA clusters on large levels pack better into the processing clusters
             handles[pr].append(mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"],
                                             tau=opts["tau"], delta=opts["delta"], precision=pr,
-                                            stream=streams[(p, pr)].cuda_stream))
+                                            stream=streams[(p, pr)].cuda_stream,
+                                            gs_cluster=0 if args.sequential else 8))
         s = handles[args.precision][-1]
         f = s.load_sinprod()
         ndofs.append(len(f))

@@ -130,16 +130,22 @@ typedef struct {
  * hbm_budget: 0 = no limit, else mgiga_assemble fails with MGIGA_ENOMEM when
  * its device footprint would exceed it.  stream: a cudaStream_t on which all
  * device work of the handle runs (NULL: the handle creates its own blocking
- * stream, which orders itself with the legacy default stream). */
+ * stream, which orders itself with the legacy default stream).
+ * gs_cluster: 0 = automatic; 2, 4, 8 or 16 = the thread-block cluster size
+ * (CTAs per patch) preferred by the patch-parallel Gauss-Seidel sweep of the
+ * mixed path on large levels.  Automatic takes 16 (fastest when the handle has
+ * the GPU to itself); when several handles solve concurrently on their own
+ * streams, 8 packs better into the GPU's processing clusters. */
 typedef struct {
   int levels, smoother, nu, mu, outer, precision, max_iter;
   double tau, delta;
   size_t hbm_budget;
   void* stream;
+  int gs_cluster;
 } mgiga_options;
 
 /* Fill `opts` with: levels 0, SCMS, nu 1, mu 1, PCG, FP64, max_iter 1000,
- * tau 1, delta 0.12, no budget, default stream. */
+ * tau 1, delta 0.12, no budget, default stream, automatic cluster size. */
 void mgiga_default_options(mgiga_options* opts);
 
 /* Validate the problem, build the DoF numbering, the piece decomposition and

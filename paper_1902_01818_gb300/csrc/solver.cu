@@ -286,7 +286,9 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   int max_n = 0;
   for (int k = 0; k < L.K; ++k)
     for (int a = 0; a < d; ++a) max_n = std::max(max_n, fd[k].n[a]);
-  const int fdk = dl.arith <= 1 ? dl.arith : (max_n >= 160 ? dl.arith : 1);
+  int tensor_min_n = 160;
+  if (const char* env = std::getenv("MGIGA_FD_TENSOR_MIN_N")) tensor_min_n = std::max(1, std::atoi(env));
+  const int fdk = dl.arith <= 1 ? dl.arith : (max_n >= tensor_min_n ? dl.arith : 1);
   dl.fd_kind = fdk;
   // U pool
   Vec Upool;
@@ -514,6 +516,8 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   // small 2D interiors: all four contractions of a patch in one CTA (shared memory), unless
   // MGIGA_FD_FUSE=0 (kept for testing the batched-GEMM path on small problems)
   const char* fuse_env = std::getenv("MGIGA_FD_FUSE");
+  int fuse_max_n = 48;
+  if (const char* env = std::getenv("MGIGA_FD_FUSE_MAX_N")) fuse_max_n = std::max(1, std::atoi(env));
   if (d == 2 && !(fuse_env && fuse_env[0] == '0')) {
     std::vector<FdSmall> fs;
     int smem = 0;
@@ -524,7 +528,7 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
       const int b = fd_small_smem(n0, n1, f32);
       // one CTA does 4 n^3 multiply-adds: beyond n = 48 the batched steps over all SMs win
       // (measured on the SIPG 3x3 layout: n ~ 30-45 fused 0.023 ms vs 0.039; n ~ 60-93 0.062 vs 0.048)
-      if (b > kFdSmallSmem || std::max(n0, n1) > 48) { fits = false; break; }
+      if (b > kFdSmallSmem || std::max(n0, n1) > fuse_max_n) { fits = false; break; }
       smem = std::max(smem, b);
       FdSmall q{};
       q.ibase = L.off[k] + 1 + L.N[k][0];
@@ -624,7 +628,7 @@ void build_pieces(const std::vector<Piece>& pcs, const Level& L, Arena& A, DLeve
 // fit one buffer are fetched as one chunk.
 void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl,
                      const std::vector<int>& order, const std::vector<int64_t>& gpos, const std::vector<int>& gpatch,
-                     const std::vector<int>& gx, int ncol, int B) {
+                     const std::vector<int>& gx, int ncol, int B, int gs_cluster) {
   auto gxr_of = [&](int e) { return gx[e] >= 0 && L.x_ptr[gx[e] + 1] > L.x_ptr[gx[e]]; };
   const int K = L.K, d = L.d, nb = L.nb, P = L.p;
   const int W = 2 * P + 1, nob = d == 2 ? W : W * W;
@@ -647,7 +651,11 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
       for (int q = 0; q < std::min(tpr, nob); ++q) worst = std::max(worst, ++cnt[((word(j, q) % 32) + 32) % 32]);
     return worst;
   };
-  const int64_t limit = 225 * 1024;
+  int64_t limit = 225 * 1024;
+  if (const char* env = std::getenv("MGIGA_GS_SMEM_KB")) {  // tuning: leave room for other streams' CTAs
+    const int v = std::atoi(env);
+    if (v >= 48 && v <= 225) limit = (int64_t)v * 1024;
+  }
   auto item_bytes = [&](int rp) { return ((int64_t)(nb + 3) * rp * 4 + 15) / 16 * 16; };
   struct Plan {
     int cs = 0, threads = 0, tpr = 0, nbuf = 0, max_items = 0;
@@ -779,7 +787,8 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
     for (int e = 0; e < nent; ++e) cnt[(size_t)colour[order[e]] * K + gpatch[e]]++;
     for (int v : cnt) maxrows_pk = std::max(maxrows_pk, v);
   }
-  std::vector<int> sizes = maxrows_pk >= 64 ? std::vector<int>{16, 8, 4, 2, 1} : std::vector<int>{1, 2, 4, 8, 16};
+  const int large = (gs_cluster == 2 || gs_cluster == 4 || gs_cluster == 8) ? gs_cluster : 16;
+  std::vector<int> sizes = maxrows_pk >= 64 ? std::vector<int>{large, 16, 8, 4, 2, 1} : std::vector<int>{1, 2, 4, 8, 16};
   if (const char* env = std::getenv("MGIGA_GS_CS")) {  // manual cluster size for tuning
     const int v = std::atoi(env);
     if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) sizes.insert(sizes.begin(), v);
@@ -938,7 +947,8 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
   a.off_meta = pl.off_meta;
 }
 
-void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl) {
+void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl,
+              int gs_cluster) {
   const int n = L.ndof;
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -990,7 +1000,7 @@ void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L,
   int B = 1;
   for (int a = 0; a < L.d; ++a) B *= L.p + 1;
   dl.gs_base = B;
-  if (f32) build_gs_staged(pr, colour, L, A, dl, order, gpos, gpatch, gx, ncol, B);
+  if (f32) build_gs_staged(pr, colour, L, A, dl, order, gpos, gpatch, gx, ncol, B, gs_cluster);
   int maxrows = 1;
   for (size_t c = 0; c + 1 < dl.gs_cptr.size(); ++c) maxrows = std::max(maxrows, dl.gs_cptr[c + 1] - dl.gs_cptr[c]);
   const int coop = gs_coop_max_blocks(L.d, L.p, f32);
@@ -1321,6 +1331,7 @@ void mgiga_default_options(mgiga_options* o) {
   o->delta = 0.12;
   o->hbm_budget = 0;
   o->stream = nullptr;
+  o->gs_cluster = 0;
 }
 
 double mgiga_source_sinprod(const double* x, void* ctx) {
@@ -1345,7 +1356,8 @@ mgiga_status mgiga_create(const mgiga_problem* problem, const mgiga_options* opt
     if (opts) h->opt = *opts; else mgiga_default_options(&h->opt);
     const mgiga_options& o = h->opt;
     if (o.smoother < 0 || o.smoother > 2 || o.nu < 1 || o.mu < 1 || o.mu > 2 || o.outer < 0 || o.outer > 1 ||
-        o.precision < MGIGA_PREC_FP64 || o.precision > MGIGA_PREC_BF16 || o.max_iter < 0 || !(o.tau > 0.0) || !(o.delta > 0.0) || o.levels < 0)
+        o.precision < MGIGA_PREC_FP64 || o.precision > MGIGA_PREC_BF16 || o.max_iter < 0 || !(o.tau > 0.0) || !(o.delta > 0.0) || o.levels < 0 ||
+        !(o.gs_cluster == 0 || o.gs_cluster == 2 || o.gs_cluster == 4 || o.gs_cluster == 8 || o.gs_cluster == 16))
       throw SetupError(MGIGA_EINVAL, "invalid options");
     h->stream = static_cast<cudaStream_t>(o.stream);
     const int lv = o.levels > 0 ? o.levels : auto_levels(h->pr);
@@ -1459,7 +1471,7 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
         build_fd(L, l, h->opt.delta, h->opt.tau, A, d);
         build_pieces(h->pieces[l], L, A, d, false);
       }
-      if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) build_gs(h->pr, h->colours[l], L, A, d);
+      if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) build_gs(h->pr, h->colours[l], L, A, d, h->opt.gs_cluster);
     }
     const Level& Lf = h->L[lv - 1];
     const int64_t g = guard_of(Lf);

@@ -102,6 +102,10 @@ def test_invalid_problems_return_status():
     with pytest.raises(mg.MgigaError) as e:
         mg.Solver(odd, levels=2, assemble=False)
     assert e.value.status == mg.EINVAL
+    with pytest.raises(mg.MgigaError) as e:
+        mg.Solver(prob, levels=2, gs_cluster=3, assemble=False)
+    assert e.value.status == mg.EINVAL
+    mg.Solver(prob, levels=2, gs_cluster=8, assemble=False).close()
     s = mg.Solver(prob, levels=2, assemble=False)
     with pytest.raises(mg.MgigaError) as e:
         s.vcycle(np.zeros(s.ndof()))

@@ -48,36 +48,37 @@ def hbm_peak_gbs():
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one application of a stage on the
 # finest level, per degree, from one ncu capture of this build on a GB300 (profiles/
 # traffic_sipg3x3_finest_level.md gives the command and the per-kernel figures).  Used only for the
-# default workload (scale 3, hybrid; the band, residual and GS kernels are the same in the FP32 and
-# TF32 modes, the contractions only in FP32); None elsewhere or when a stage's kernels change.
+# default configuration (scale 3, hybrid, TF32 contractions, 8-CTA GS clusters; the band, residual
+# and GS kernels are the same in the FP32 mode); None elsewhere or when a stage's kernels change.
 DRAM_TRAFFIC = {
-    ("band", 2): 1.094e+08,
+    ("band", 2): 1.096e+08,
     ("residual", 2): 6.325e+07,
-    ("fd", 2): 2.507e+07,
-    ("gs", 2): 8.22e+07,
-    ("band", 3): 2.139e+08,
+    ("fd", 2): 2.706e+07,
+    ("gs", 2): 8.198e+07,
+    ("band", 3): 2.14e+08,
     ("residual", 3): 1.153e+08,
-    ("fd", 3): 2.528e+07,
-    ("gs", 3): 1.362e+08,
+    ("fd", 3): 2.75e+07,
+    ("gs", 3): 1.352e+08,
     ("band", 4): 3.533e+08,
     ("residual", 4): 1.851e+08,
-    ("fd", 4): 2.551e+07,
-    ("gs", 4): 2.092e+08,
-    ("band", 5): 5.292e+08,
+    ("fd", 4): 2.764e+07,
+    ("gs", 4): 2.095e+08,
+    ("band", 5): 5.296e+08,
     ("residual", 5): 2.732e+08,
-    ("fd", 5): 2.569e+07,
-    ("gs", 5): 3.075e+08,
-    ("band", 6): 7.441e+08,
-    ("residual", 6): 3.802e+08,
-    ("fd", 6): 2.59e+07,
-    ("gs", 6): 4.14e+08,
+    ("fd", 5): 2.781e+07,
+    ("gs", 5): 3.012e+08,
+    ("band", 6): 7.435e+08,
+    ("residual", 6): 3.801e+08,
+    ("fd", 6): 2.796e+07,
+    ("gs", 6): 4.306e+08,
 }
 
 
 def dram_traffic(stage, degrees, args, f32):
-    if not (args.scale == 3 and args.smoother == "hybrid" and args.precision in ("fp32", "tf32")):
+    if not (args.scale == 3 and args.smoother == "hybrid" and args.precision in ("fp32", "tf32")
+            and not args.sequential):
         return None
-    if stage == "fd" and args.precision != "fp32":  # the table's contractions are the FP32 SIMT ones
+    if stage == "fd" and args.precision != "tf32":  # the table's contractions are the TF32 ones
         return None
     vals = [DRAM_TRAFFIC.get((stage, p)) for p in degrees]
     if any(v is None for v in vals):

@@ -26,13 +26,14 @@ def main(argv=None):
     ap.add_argument("--levels", default="all", help="comma-separated level indices (negative: from the finest)")
     ap.add_argument("--stages", default="band,residual,fd,pieces,gs,restrict,prolong,coarse,vcycle")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--gs-cluster", type=int, default=0, help="0 automatic, or 2/4/8/16 (see mgiga_options)")
     args = ap.parse_args(argv)
 
     from . import mgiga  # loads libmgiga.so (CUDA)
 
     prob, opts = W.sipg_3x3(args.degree, scale=args.scale, smoother=args.smoother)
     s = mgiga.Solver(prob, levels=0, smoother=args.smoother, tau=opts["tau"], delta=opts["delta"],
-                     precision=args.precision)
+                     precision=args.precision, gs_cluster=args.gs_cluster)
     nl = s.levels
     levels = list(range(nl - 1, -1, -1)) if args.levels == "all" else [int(x) % nl for x in args.levels.split(",")]
     print(f"p={args.degree} {args.precision} levels={nl} ndof={s.ndof()}", flush=True)

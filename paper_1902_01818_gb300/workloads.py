@@ -254,3 +254,38 @@ def batched_problem(seed):
                         seed=seed, active=active)
     opts = dict(levels=0, smoother="hybrid", tau=0.25, delta=0.1, nu=1)
     return prob, opts, seed + 1000
+
+
+def serving_stream(n_requests, seed=501, max_patch_dof=1e6):
+    """Requests of the serving layout (seeded): 2D with probability .7, else 3D;
+    1-27 unit patches in a near-square (near-cubic) arrangement filled row-major;
+    per-patch DoF log-uniform in [1e3, max_patch_dof] (intervals per direction
+    rounded to the nearest c 2^j, c in {4..7}, >= 2 levels); p ~ U{2..6};
+    conforming or SIPG with probability 1/2; vertices inside the domain jittered
+    (.1 in 2D, .05 in 3D); hybrid smoother; half of the requests reuse an earlier
+    operator.  Yields (key, problem, options, rhs seed); the right-hand side is
+    i.i.d. N(0, 1) load coefficients."""
+    rng = np.random.default_rng(seed)
+    ops = []
+    for i in range(n_requests):
+        if ops and rng.uniform() < 0.5:
+            key, prob, opts = ops[int(rng.integers(len(ops)))]
+        else:
+            d = 2 if rng.uniform() < 0.7 else 3
+            K = int(rng.integers(1, 28))
+            side = int(np.ceil(K ** (1.0 / d) - 1e-9))
+            cells = (side,) * d
+            active = [tuple((j // side ** a) % side for a in range(d)) for j in range(K)]
+            p = int(rng.integers(2, 7))
+            dof = float(np.exp(rng.uniform(np.log(1e3), np.log(max_patch_dof))))
+            n_raw = max(dof ** (1.0 / d) - p, 8.0)
+            min_n = 8 if d == 2 else 12  # two levels with >= 2 (2D) / 3 (3D) intervals per half
+            cands = [c * 2 ** j for c in range(4, 8) for j in range(0, 9) if c * 2 ** j >= min_n]
+            n = int(min(cands, key=lambda v: (abs(v - n_raw), v)))
+            coupling = "conforming" if rng.uniform() < 0.5 else "sipg"
+            prob = grid_problem(cells, n, p, coupling, box=tuple(float(c) for c in cells),
+                                jitter=0.1 if d == 2 else 0.05, seed=seed * 1000 + i, active=active)
+            opts = dict(levels=0, smoother="hybrid", tau=0.25, delta=0.1 if d == 2 else 0.12, nu=1)
+            key = f"op{i}"
+            ops.append((key, prob, opts))
+        yield key, prob, opts, seed * 1000 + 500 + i

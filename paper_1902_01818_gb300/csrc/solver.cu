@@ -1,6 +1,7 @@
 // libmgiga: handle, device data, V-cycle and PCG drivers, and the C ABI
 // declared in include/mgiga.h.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1395,16 +1396,28 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
   if (!h) return MGIGA_EINVAL;
   if (h->assembled) return fail(h, MGIGA_ESTATE, "already assembled");
   return guarded_call(h, [&]() -> mgiga_status {
+    // MGIGA_VERBOSE: time of each set-up phase on stderr
+    const bool verbose = std::getenv("MGIGA_VERBOSE") != nullptr;
+    auto t_last = std::chrono::steady_clock::now();
+    auto tick = [&](const char* what, int l) {
+      if (!verbose) return;
+      const auto now = std::chrono::steady_clock::now();
+      std::fprintf(stderr, "mgiga: set-up %-10s level %d: %.3f s\n", what, l,
+                   std::chrono::duration<double>(now - t_last).count());
+      t_last = now;
+    };
     const int lv = h->levels;
     Level& F = h->L[lv - 1];
     assemble_fine(h->pr, F, h->pr.knots);
     apply_dirichlet(F);
+    tick("assembly", lv - 1);
     h->T.assign(lv, Transfer{});
     for (int l = lv - 1; l > 0; --l) {
       h->T[l] = build_transfer(h->L[l - 1], h->L[l]);
       galerkin(h->L[l], h->T[l], h->L[l - 1]);
       apply_dirichlet(h->L[l - 1]);
     }
+    tick("galerkin", 0);
     // device: work runs on the caller's stream, or on a blocking stream of
     // the handle (the legacy default stream cannot be captured into graphs)
     if (!h->stream) {
@@ -1467,11 +1480,15 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
         build_pieces({all}, L, A, d, true);
         continue;
       }
+      tick("uploads", l);
       if (sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID) {
         build_fd(L, l, h->opt.delta, h->opt.tau, A, d);
+        tick("fd", l);
         build_pieces(h->pieces[l], L, A, d, false);
+        tick("pieces", l);
       }
       if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) build_gs(h->pr, h->colours[l], L, A, d, h->opt.gs_cluster);
+      tick("gs", l);
     }
     const Level& Lf = h->L[lv - 1];
     const int64_t g = guard_of(Lf);

@@ -129,8 +129,10 @@ typedef struct {
  * steps; mu: 1 = V-cycle.  max_iter bounds the outer iterations.
  * hbm_budget: 0 = no limit, else mgiga_assemble fails with MGIGA_ENOMEM when
  * its device footprint would exceed it.  stream: a cudaStream_t on which all
- * device work of the handle runs (NULL: the handle creates its own blocking
- * stream, which orders itself with the legacy default stream).
+ * device work of the handle runs (NULL: the handle creates its own
+ * non-blocking stream; set-up copies run on it, and the _d entry points order
+ * it after work already queued on the legacy default stream).  Handles used
+ * from different host threads may set up and solve concurrently.
  * gs_cluster: 0 = automatic; 2, 4, 8 or 16 = the thread-block cluster size
  * (CTAs per patch) preferred by the patch-parallel Gauss-Seidel sweep of the
  * mixed path on large levels.  Automatic takes 16 (fastest when the handle has

@@ -2,6 +2,7 @@
 // algebra for the set-up phase.
 #include <algorithm>
 #include <cmath>
+#include <limits>
 
 #include "host.hpp"
 
@@ -320,70 +321,161 @@ Vec spd_inverse(const Vec& A, int n, bool par) {
 
 // Cyclic Jacobi rotations on the symmetric C = L^{-1} K L^{-T} (M = L L^T):
 // C = V diag(lam) V^T, then U = L^{-T} V.
+// Symmetric eigen-decomposition C = V diag(lam) V^T (C n x n, row-major; returns Vt = V^T,
+// row j the eigenvector of lam[j]).  Householder reduction to tridiagonal form, then the
+// implicit QL iteration with Wilkinson-type shifts on the tridiagonal (Golub & Van Loan,
+// Matrix Computations, Sec. 8.3), its plane rotations applied to the reduction's orthogonal
+// factor.  O(n^3) with a small constant, rows contiguous in every update.
+static void sym_eig(Vec C, int n, Vec& Vt, Vec& lam) {
+  std::vector<Vec> hv(n);
+  std::vector<double> hbeta(n, 0.0);
+  Vec w(n), p(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    // x = C[k+1.., k] = C[k, k+1..] (symmetric)
+    double* rk = &C[(size_t)k * n];
+    double norm2 = 0.0;
+    for (int i = k + 1; i < n; ++i) norm2 += rk[i] * rk[i];
+    const double x0 = rk[k + 1];
+    const double tail = norm2 - x0 * x0;
+    if (tail <= 1e-300 * std::max(norm2, 1e-300)) continue;  // already tridiagonal in this column
+    const double alpha = x0 >= 0.0 ? -std::sqrt(norm2) : std::sqrt(norm2);
+    Vec& v = hv[k];
+    v.assign(n, 0.0);
+    for (int i = k + 1; i < n; ++i) v[i] = rk[i];
+    v[k + 1] -= alpha;
+    double vv = 0.0;
+    for (int i = k + 1; i < n; ++i) vv += v[i] * v[i];
+    const double beta = 2.0 / vv;
+    hbeta[k] = beta;
+    // trailing block A22 -= v w^T + w v^T with p = beta A22 v, w = p - (beta/2)(p.v) v
+    for (int i = k + 1; i < n; ++i) {
+      const double* ri = &C[(size_t)i * n];
+      double t = 0.0;
+      for (int j = k + 1; j < n; ++j) t += ri[j] * v[j];
+      p[i] = beta * t;
+    }
+    double pv = 0.0;
+    for (int i = k + 1; i < n; ++i) pv += p[i] * v[i];
+    for (int i = k + 1; i < n; ++i) w[i] = p[i] - 0.5 * beta * pv * v[i];
+    for (int i = k + 1; i < n; ++i) {
+      double* ri = &C[(size_t)i * n];
+      for (int j = k + 1; j < n; ++j) ri[j] -= v[i] * w[j] + w[i] * v[j];
+    }
+    for (int i = k + 2; i < n; ++i) C[(size_t)k * n + i] = C[(size_t)i * n + k] = 0.0;
+    C[(size_t)k * n + k + 1] = C[(size_t)(k + 1) * n + k] = alpha;
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = C[(size_t)i * n + i];
+  for (int i = 0; i + 1 < n; ++i) e[i] = C[(size_t)i * n + i + 1];
+  // Vt = Q^T = H_{n-3} ... H_0: apply the reflections from the left to the identity
+  Vt.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Vt[(size_t)i * n + i] = 1.0;
+  for (int k = 0; k + 2 < n; ++k) {
+    if (hbeta[k] == 0.0) continue;
+    const Vec& v = hv[k];
+    // Vt <- (I - beta v v^T) Vt: rows k+1..n-1 change
+    std::fill(w.begin(), w.end(), 0.0);
+    for (int i = k + 1; i < n; ++i) {
+      const double* ri = &Vt[(size_t)i * n];
+      const double vi = v[i];
+      for (int j = 0; j < n; ++j) w[j] += vi * ri[j];
+    }
+    for (int i = k + 1; i < n; ++i) {
+      double* ri = &Vt[(size_t)i * n];
+      const double f = hbeta[k] * v[i];
+      for (int j = 0; j < n; ++j) ri[j] -= f * w[j];
+    }
+  }
+  // implicit QL on (d, e); rotations of rows i, i+1 of Vt
+  const double eps = std::numeric_limits<double>::epsilon();
+  for (int l = 0; l < n; ++l) {
+    for (int iter = 0;; ++iter) {
+      int m = l;
+      for (; m + 1 < n; ++m) {
+        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= eps * dd) break;
+      }
+      if (m == l) break;
+      if (iter >= 100) throw SetupError(4, "symmetric eigenvalue iteration did not converge");
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+      double s = 1.0, c = 1.0, pp = 0.0;
+      int i = m - 1;
+      bool deflated = false;
+      for (; i >= l; --i) {
+        const double f = s * e[i], b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {  // split: the rotation would be undefined
+          d[i + 1] -= pp;
+          e[m] = 0.0;
+          deflated = true;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - pp;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        pp = s * r;
+        d[i + 1] = g + pp;
+        g = c * r - b;
+        double* ra = &Vt[(size_t)i * n];
+        double* rb = &Vt[(size_t)(i + 1) * n];
+        for (int k = 0; k < n; ++k) {
+          const double t = rb[k];
+          rb[k] = s * ra[k] + c * t;
+          ra[k] = c * ra[k] - s * t;
+        }
+      }
+      if (deflated) continue;
+      d[l] -= pp;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+  lam.assign(d.begin(), d.end());
+}
+
+// Generalized symmetric-definite eigenproblem K U = M U diag(lam), U^T M U = I (M = L L^T):
+// the symmetric C = L^{-1} K L^{-T} = V diag(lam) V^T, then U = L^{-T} V.
 void gen_eig(const Vec& K, const Vec& M, int n, Vec& U, Vec& lam) {
   Vec L = M;
   if (!cholesky(L, n)) throw SetupError(4, "mass matrix not SPD");
-  const Vec Wt = lower_inverse_t(L, n);
+  const Vec Wt = lower_inverse_t(L, n);  // row c: column c of W = L^{-1}
+  // C = W K W^T: T = W K (row i of W = column i of Wt... use W[i][k] = Wt[k][i])
   Vec W((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) W[(size_t)i * n + j] = Wt[(size_t)j * n + i];
-  // C = W K W^T
   Vec T((size_t)n * n, 0.0), C((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      double s = 0.0;
-      for (int k = 0; k <= i; ++k) s += W[(size_t)i * n + k] * K[(size_t)k * n + j];
-      T[(size_t)i * n + j] = s;
+  for (int i = 0; i < n; ++i) {  // T[i][:] = sum_{k <= i} W[i][k] K[k][:]
+    double* ti = &T[(size_t)i * n];
+    for (int k = 0; k <= i; ++k) {
+      const double wik = W[(size_t)i * n + k];
+      if (wik == 0.0) continue;
+      const double* kk = &K[(size_t)k * n];
+      for (int j = 0; j < n; ++j) ti[j] += wik * kk[j];
     }
-  for (int i = 0; i < n; ++i)
+  }
+  for (int i = 0; i < n; ++i)  // C[i][j] = sum_{k <= j} T[i][k] W[j][k]
     for (int j = 0; j <= i; ++j) {
+      const double* ti = &T[(size_t)i * n];
+      const double* wj = &W[(size_t)j * n];
       double s = 0.0;
-      for (int k = 0; k <= j; ++k) s += T[(size_t)i * n + k] * W[(size_t)j * n + k];
+      for (int k = 0; k <= j; ++k) s += ti[k] * wj[k];
       C[(size_t)i * n + j] = s;
       C[(size_t)j * n + i] = s;
     }
-  Vec V((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int i = 0; i < n; ++i) {
-      diag += C[(size_t)i * n + i] * C[(size_t)i * n + i];
-      for (int j = i + 1; j < n; ++j) off += C[(size_t)i * n + j] * C[(size_t)i * n + j];
-    }
-    if (off <= 1e-32 * diag) break;
-    for (int pp = 0; pp < n - 1; ++pp)
-      for (int qq = pp + 1; qq < n; ++qq) {
-        const double apq = C[(size_t)pp * n + qq];
-        if (std::fabs(apq) < 1e-300) continue;
-        const double app = C[(size_t)pp * n + pp], aqq = C[(size_t)qq * n + qq];
-        const double theta = (aqq - app) / (2.0 * apq);
-        const double tt = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(tt * tt + 1.0), s = tt * c;
-        for (int k = 0; k < n; ++k) {  // columns p, q
-          const double ckp = C[(size_t)k * n + pp], ckq = C[(size_t)k * n + qq];
-          C[(size_t)k * n + pp] = c * ckp - s * ckq;
-          C[(size_t)k * n + qq] = s * ckp + c * ckq;
-        }
-        for (int k = 0; k < n; ++k) {  // rows p, q
-          const double cpk = C[(size_t)pp * n + k], cqk = C[(size_t)qq * n + k];
-          C[(size_t)pp * n + k] = c * cpk - s * cqk;
-          C[(size_t)qq * n + k] = s * cpk + c * cqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[(size_t)k * n + pp], vkq = V[(size_t)k * n + qq];
-          V[(size_t)k * n + pp] = c * vkp - s * vkq;
-          V[(size_t)k * n + qq] = s * vkp + c * vkq;
-        }
-      }
-  }
-  lam.resize(n);
-  for (int i = 0; i < n; ++i) lam[i] = C[(size_t)i * n + i];
-  // U = W^T V
+  Vec Vt;
+  sym_eig(C, n, Vt, lam);
+  // U = W^T V: U[i][j] = sum_{k >= i} W[k][i] V[k][j] = sum_k Wt[i][k] Vt[j][k]
   U.assign((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
+      const double* wi = &Wt[(size_t)i * n];
+      const double* vj = &Vt[(size_t)j * n];
       double s = 0.0;
-      for (int k = i; k < n; ++k) s += W[(size_t)k * n + i] * V[(size_t)k * n + j];
+      for (int k = i; k < n; ++k) s += wi[k] * vj[k];
       U[(size_t)i * n + j] = s;
     }
 }

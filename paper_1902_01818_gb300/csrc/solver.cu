@@ -37,10 +37,13 @@ struct CudaError : std::runtime_error {
   } while (0)
 
 // Device allocations of one handle; every buffer is freed in the destructor.
+// Uploads and fills are ordered on the handle's stream: set-up in one thread
+// must not touch the legacy default stream while another thread captures.
 struct Arena {
   std::vector<void*> ptrs;
   size_t bytes = 0;
   size_t budget = 0;
+  cudaStream_t stream = nullptr;
   ~Arena() {
     for (void* p : ptrs) cudaFree(p);
   }
@@ -62,13 +65,13 @@ struct Arena {
   template <class T>
   T* upload(const std::vector<T>& v) {
     T* p = alloc<T>(v.size());
-    if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream));
     return p;
   }
   // vector with a zero guard of g elements on both sides; returns the data start
   double* guarded(int64_t n, int64_t g) {
     double* p = alloc<double>((size_t)(n + 2 * g));
-    CK(cudaMemset(p, 0, (size_t)(n + 2 * g) * sizeof(double)));
+    CK(cudaMemsetAsync(p, 0, (size_t)(n + 2 * g) * sizeof(double), stream));
     return p + g;
   }
 };
@@ -166,6 +169,7 @@ struct mgiga_handle {
   std::string err;
   cudaStream_t stream = nullptr;
   bool own_stream = false;  // created by the library when the options give none
+  cudaEvent_t legacy_done = nullptr;  // orders an owned stream after the legacy default stream
   std::unique_ptr<Arena> arena;
   std::vector<DLevel> D;
   // PCG state
@@ -188,6 +192,7 @@ struct mgiga_handle {
     if (host_scal) cudaFreeHost(host_scal);
     arena.reset();
     if (own_stream && stream) cudaStreamDestroy(stream);
+    if (legacy_done) cudaEventDestroy(legacy_done);
   }
 };
 
@@ -411,7 +416,7 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     }
     vU = A.upload(pool);
     vT = A.alloc<float>((size_t)std::max<int64_t>(tsz, 4));
-    CK(cudaMemset(vT, 0, (size_t)std::max<int64_t>(tsz, 4) * sizeof(float)));  // padding columns stay 0
+    CK(cudaMemsetAsync(vT, 0, (size_t)std::max<int64_t>(tsz, 4) * sizeof(float), A.stream));  // padding columns stay 0
     std::vector<int64_t> e_ptr(1, 0), ib, doff;
     std::vector<int> n0s, N0s, dld;
     for (int k = 0; k < L.K; ++k) {
@@ -1215,12 +1220,22 @@ void check_launch() {
 
 // a Gauss-Seidel sweep whose grid barrier gave up leaves gs_err set; read and
 // clear it after the stream has drained
+// An owned stream is non-blocking: order it after the legacy default stream,
+// on which a caller's device inputs may still be in flight.
+void after_legacy(mgiga_handle* h) {
+  if (!h->own_stream) return;
+  CK(cudaEventRecord(h->legacy_done, cudaStreamLegacy));
+  CK(cudaStreamWaitEvent(h->stream, h->legacy_done, 0));
+}
+
 void check_device_timeout(mgiga_handle* h) {
   if (!h->gs_err) return;
   int e = 0;
-  CK(cudaMemcpy(&e, h->gs_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&e, h->gs_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   if (e) {
-    CK(cudaMemset(h->gs_err, 0, sizeof(int)));
+    CK(cudaMemsetAsync(h->gs_err, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     throw SetupError(MGIGA_ETIMEOUT, "a Gauss-Seidel grid barrier wait expired");
   }
 }
@@ -1418,14 +1433,19 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       apply_dirichlet(h->L[l - 1]);
     }
     tick("galerkin", 0);
-    // device: work runs on the caller's stream, or on a blocking stream of
-    // the handle (the legacy default stream cannot be captured into graphs)
+    // device: work runs on the caller's stream, or on a non-blocking stream
+    // of the handle (the legacy default stream cannot be captured into
+    // graphs, and a blocking stream under capture in one thread would fail
+    // legacy-stream work of another); the _d entry points order an owned
+    // stream after the legacy default stream explicitly
     if (!h->stream) {
-      CK(cudaStreamCreate(&h->stream));
+      CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
       h->own_stream = true;
     }
+    if (!h->legacy_done) CK(cudaEventCreateWithFlags(&h->legacy_done, cudaEventDisableTiming));
     h->arena.reset(new Arena());
     Arena& A = *h->arena;
+    A.stream = h->stream;
     if (h->opt.precision == MGIGA_PREC_TF32 || h->opt.precision == MGIGA_PREC_BF16) CK(prepare_gemm_umma());
     A.budget = h->opt.hbm_budget;
     h->D.assign(lv, DLevel{});
@@ -1498,21 +1518,21 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
     h->b = A.guarded(Lf.nloc, g);
     h->t = A.guarded(Lf.nloc, g);
     h->scal = A.alloc<double>(S_COUNT);
-    CK(cudaMemset(h->scal, 0, S_COUNT * sizeof(double)));
+    CK(cudaMemsetAsync(h->scal, 0, S_COUNT * sizeof(double), h->stream));
     h->partials = A.alloc<double>(red_blocks());
     h->counter = A.alloc<unsigned int>(4);
-    CK(cudaMemset(h->counter, 0, 4 * sizeof(unsigned int)));
+    CK(cudaMemsetAsync(h->counter, 0, 4 * sizeof(unsigned int), h->stream));
     h->gs_bar = A.alloc<unsigned int>(2);
     h->gs_err = A.alloc<int>(1);
-    CK(cudaMemset(h->gs_bar, 0, 2 * sizeof(unsigned int)));
-    CK(cudaMemset(h->gs_err, 0, sizeof(int)));
+    CK(cudaMemsetAsync(h->gs_bar, 0, 2 * sizeof(unsigned int), h->stream));
+    CK(cudaMemsetAsync(h->gs_err, 0, sizeof(int), h->stream));
     int maxdof = 1;
     for (const auto& L : h->L) maxdof = std::max(maxdof, L.ndof);
     h->in1 = A.alloc<double>(maxdof);
     h->in2 = A.alloc<double>(maxdof);
     h->out = A.alloc<double>(maxdof);
     CK(cudaMallocHost(&h->host_scal, S_COUNT * sizeof(double)));
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(h->stream));
     h->assembled = true;
     return MGIGA_OK;
   });
@@ -1607,6 +1627,13 @@ static mgiga_status apply_impl(mgiga_handle* h, int op, int level, const double*
 }
 
 mgiga_status mgiga_apply_d(mgiga_handle* h, int op, int level, const double* a, const double* b, double* out) {
+  if (h && h->assembled) {
+    const mgiga_status s = guarded_call(h, [&]() -> mgiga_status {
+      after_legacy(h);
+      return MGIGA_OK;
+    });
+    if (s != MGIGA_OK) return s;
+  }
   return apply_impl(h, op, level, a, b, out);
 }
 
@@ -1639,6 +1666,7 @@ mgiga_status mgiga_residual_noalloc_d(mgiga_handle* h, int level, const double* 
   if (level < 0 || level >= h->levels) return fail(h, MGIGA_EINVAL, "bad level");
   if (!f || !u || !out) return fail(h, MGIGA_EINVAL, "NULL vector");
   return guarded_call(h, [&]() -> mgiga_status {
+    after_legacy(h);
     LaunchScope scope(h);
     const Level& L = h->L[level];
     DLevel& d = h->D[level];
@@ -1682,7 +1710,8 @@ mgiga_status mgiga_apply(mgiga_handle* h, int op, int level, const double* a, co
     if (b) CK(cudaMemcpyAsync(h->in2, b, (size_t)h->L[level].ndof * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     const mgiga_status s = apply_impl(h, op, level, a ? h->in1 : nullptr, b ? h->in2 : nullptr, h->out);
     if (s != MGIGA_OK) return s;
-    CK(cudaMemcpy(out, h->out, (size_t)nout * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(out, h->out, (size_t)nout * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return MGIGA_OK;
   });
 }
@@ -1693,6 +1722,7 @@ mgiga_status mgiga_vcycle_d(mgiga_handle* h, const double* r, double* z) {
   if (!h) return MGIGA_EINVAL;
   if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
   return guarded_call(h, [&]() -> mgiga_status {
+    after_legacy(h);
     LaunchScope scope(h);
     DLevel& d = h->D[h->levels - 1];
     launch_scatter(d.nloc, h->stream, d.loc2glob, r, d.f);
@@ -1713,7 +1743,8 @@ mgiga_status mgiga_vcycle(mgiga_handle* h, const double* r, double* z) {
     CK(cudaMemcpyAsync(h->in1, r, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     const mgiga_status s = mgiga_vcycle_d(h, h->in1, h->out);
     if (s != MGIGA_OK) return s;
-    CK(cudaMemcpy(z, h->out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(z, h->out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return MGIGA_OK;
   });
 }
@@ -1838,7 +1869,10 @@ mgiga_status mgiga_solve_d(mgiga_handle* h, const double* rhs, double* u, double
   if (!h) return MGIGA_EINVAL;
   if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
   if (!rhs || !u) return fail(h, MGIGA_EINVAL, "NULL vector");
-  return guarded_call(h, [&]() { return solve_impl(h, rhs, u, tol, iters, final_relres); });
+  return guarded_call(h, [&]() {
+    after_legacy(h);
+    return solve_impl(h, rhs, u, tol, iters, final_relres);
+  });
 }
 
 mgiga_status mgiga_solve(mgiga_handle* h, const double* rhs, double* u, double tol, int* iters,
@@ -1851,8 +1885,10 @@ mgiga_status mgiga_solve(mgiga_handle* h, const double* rhs, double* u, double t
     CK(cudaMemcpyAsync(h->in1, rhs, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->in2, u, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     const mgiga_status s = solve_impl(h, h->in1, h->in2, tol, iters, final_relres);
-    if (s == MGIGA_OK || s == MGIGA_ENOCONV)
-      CK(cudaMemcpy(u, h->in2, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+    if (s == MGIGA_OK || s == MGIGA_ENOCONV) {
+      CK(cudaMemcpyAsync(u, h->in2, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
     return s;
   });
 }

@@ -319,8 +319,6 @@ Vec spd_inverse(const Vec& A, int n, bool par) {
   return Z;
 }
 
-// Cyclic Jacobi rotations on the symmetric C = L^{-1} K L^{-T} (M = L L^T):
-// C = V diag(lam) V^T, then U = L^{-T} V.
 // Symmetric eigen-decomposition C = V diag(lam) V^T (C n x n, row-major; returns Vt = V^T,
 // row j the eigenvector of lam[j]).  Householder reduction to tridiagonal form, then the
 // implicit QL iteration with Wilkinson-type shifts on the tridiagonal (Golub & Van Loan,
@@ -443,7 +441,7 @@ void gen_eig(const Vec& K, const Vec& M, int n, Vec& U, Vec& lam) {
   Vec L = M;
   if (!cholesky(L, n)) throw SetupError(4, "mass matrix not SPD");
   const Vec Wt = lower_inverse_t(L, n);  // row c: column c of W = L^{-1}
-  // C = W K W^T: T = W K (row i of W = column i of Wt... use W[i][k] = Wt[k][i])
+  // C = W K W^T with W = L^{-1} lower triangular (W[i][k] = Wt[k][i]); first T = W K
   Vec W((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) W[(size_t)i * n + j] = Wt[(size_t)j * n + i];

@@ -110,6 +110,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sequential", action="store_true",
                     help="solve the degrees one after another (default: concurrently, a stream each)")
+    ap.add_argument("--priority", default="degree", choices=["degree", "none"],
+                    help="concurrent solves: higher stream priority for higher degrees (the longest solves)")
+    ap.add_argument("--gs-cluster", default="8",
+                    help="Gauss-Seidel cluster size per degree (one value, or one per degree); "
+                         "ignored with --sequential, which lets the library choose")
     return ap.parse_args()
 
 
@@ -284,15 +289,23 @@ def main():
     t_setup = time.perf_counter()
     precisions = [args.precision] + ([] if args.no_fp64_compare or args.precision == "fp64" else ["fp64"])
     handles = {pr: [] for pr in precisions}
-    for p in degrees:
+    cs = [int(x) for x in args.gs_cluster.split(",")]
+    cs = cs * len(degrees) if len(cs) == 1 else cs
+    if len(cs) != len(degrees):
+        raise SystemExit("--gs-cluster: one value, or one per degree")
+    # the solve of the highest degree takes the most V-cycles and the longest ones: its stream gets
+    # the highest priority, so its blocks are scheduled first and the others fill the gaps
+    by_work = sorted(degrees, reverse=True)
+    for p, c in zip(degrees, cs):
         prob, opts = workload(p, args.scale, args.smoother)
+        prio = -max(0, 3 - by_work.index(p)) if args.priority == "degree" and not args.sequential else 0
         for pr in precisions:
-            streams[(p, pr)] = torch.cuda.Stream()
+            streams[(p, pr)] = torch.cuda.Stream(priority=prio)
             # concurrent solves: 8-CTA clusters on large levels pack better into the processing clusters
             handles[pr].append(mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"],
                                             tau=opts["tau"], delta=opts["delta"], precision=pr,
                                             stream=streams[(p, pr)].cuda_stream,
-                                            gs_cluster=0 if args.sequential else 8))
+                                            gs_cluster=0 if args.sequential else c))
         s = handles[args.precision][-1]
         f = s.load_sinprod()
         ndofs.append(len(f))
@@ -489,8 +502,10 @@ def main():
                        "step_ms_p99": float(np.percentile(step_ms, 99)),
                        "l2": "inputs larger than L2 (0.9-3.7 GB operators per step)",
                        "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1),
-                       "solves": ("concurrent: one CUDA stream and host thread per degree" if concurrent
-                                  else "sequential")},
+                       "solves": ("concurrent: one CUDA stream and host thread per degree"
+                                  + (", stream priority by degree" if args.priority == "degree" else "")
+                                  if concurrent else "sequential"),
+                       "gs_cluster": None if args.sequential else cs},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "plain_fp64": plain,
             "mixed_sequential": mixed_seq,
             "clocks": clk.summary()}

@@ -1110,11 +1110,13 @@ __global__ void __launch_bounds__(256) gs_sweep_coop(GsSweepArgs a) {
 // ends, so that every band neighbour of a row is a plain shared-memory read
 // (off-patch columns have zero coefficients).  For every colour the CTA's
 // rows come as one or more contiguous blocks ("items") -- FP32 coefficients
-// [o][row], the packed slab position, f minus the couplings to the other
+// [line][row][o_0], the packed slab position, f minus the couplings to the other
 // parity (written by gs_fill_phase before the launch) and the inverse
 // diagonal; consecutive items are fetched together as one bulk asynchronous
 // copy ("chunk"), two chunk buffers in flight, mbarrier completion.  Colours are separated by the
-// CTA barrier (one CTA per patch) or the hardware cluster barrier.
+// CTA barrier; where the residue of the slow index changes from one colour to the next, by the
+// hardware cluster barrier, which publishes the halo stores (no row of a run of colours with one
+// slow residue reads a halo value that a neighbour updates during the run).
 // Every wait on an mbarrier is bounded: on expiry the CTA records the error,
 // stops computing and keeps taking part in the barriers.
 // ---------------------------------------------------------------------------
@@ -1143,7 +1145,7 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
   float* us = reinterpret_cast<float*>(smem);
   unsigned char* const buf0 = smem + a.off_buf;
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + a.off_mbar);
-  int4* cm = reinterpret_cast<int4*>(smem + a.off_meta);  // per item: rows, chunk, offset in chunk, Rp | end flag
+  int4* cm = reinterpret_cast<int4*>(smem + a.off_meta);  // per item: rows, chunk, offset in chunk, Rp | end flags
   int4* ch = cm + a.max_items;                             // per chunk: byte offset (lo, hi), bytes, -
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
@@ -1156,16 +1158,17 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
     cm[i] = a.cmeta[ibase + i];
     ch[i] = a.chunks[ibase + i];
   }
+  const int nbuf = a.nbuf;  // ring of chunk buffers: chunk j in buffer j % nbuf
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    for (int b = 0; b < nbuf; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   const int nchunk = nc > 0 ? cm[nc - 1].y + 1 : 0;
-  const int nbuf = a.nbuf;
+  int issued = 0;  // thread 0: chunks 0 .. issued - 1 have been requested
   auto copy = [&](int j) {  // thread 0: chunk j into its buffer
-    const int b = nbuf == 1 ? 0 : (j & 1);
+    const int b = j % nbuf;
     const unsigned bar = smem_u32(&mbar[b]);
     const int4 c = ch[j];
     const int64_t off = (int64_t)(unsigned)c.x | ((int64_t)c.y << 32);
@@ -1176,11 +1179,10 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
               smem_u32(buf0 + (size_t)b * a.cap)),
           "l"(a.pool + off), "r"(c.z), "r"(bar)
           : "memory");
+    issued = j + 1;
   };
-  if (tid == 0) {
-    if (nchunk > 0) copy(0);
-    if (nchunk > 1 && nbuf == 2) copy(1);
-  }
+  if (tid == 0)
+    for (int j = 0; j < min(nbuf, nchunk); ++j) copy(j);
   // u of the extended slab (zero outside the patch and in the guards), four independent loads per thread
   {
     const double* ug = a.u + pm.off;
@@ -1218,21 +1220,25 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
   const int rows_per_warp = 32 / TPR;
   const int rows_per_cta = nthr / TPR;
   bool ok = true;
+  bool synced = true;  // no item has been read since the last barrier
   int cur = -1;
   for (int ci = 0; ci < nc; ++ci) {
-    const int4 m = cm[ci];  // rows, chunk, offset in chunk, Rp | (last item of its colour) << 30
-    const int b = nbuf == 1 ? 0 : (m.y & 1);
-    if (m.y != cur) {  // first colour of chunk m.y
+    // rows, chunk, offset in chunk, Rp | (last item of its colour) << 30 | (last of its slow-residue run) << 29
+    const int4 m = cm[ci];
+    const int b = m.y % nbuf;
+    if (m.y != cur) {  // first item of chunk m.y
+      // chunk m.y + nbuf - 1 goes into the buffer of chunk m.y - 1: every thread must be done
+      // with it (a colour split across two chunks has no barrier between its items)
+      if (!synced) __syncthreads();
       cur = m.y;
-      const unsigned parity = nbuf == 1 ? 0u : (unsigned)((m.y >> 1) & 1);
+      const unsigned parity = (unsigned)((m.y / nbuf) & 1);
       if (ok && !mbar_wait(smem_u32(&mbar[b]), parity)) {
         ok = false;
         atomicExch(a.err, 2);
       }
-      // the other buffer held chunk m.y - 1, released by the barrier that ended its last colour
-      if (tid == 0 && ok && nbuf == 2 && m.y >= 1 && m.y + 1 < nchunk) copy(m.y + 1);
+      if (tid == 0 && ok && nbuf >= 2 && m.y >= 1 && m.y + nbuf - 1 < nchunk) copy(m.y + nbuf - 1);
     }
-    const int R = m.x, Rp = m.w & ((1 << 30) - 1);
+    const int R = m.x, Rp = m.w & ((1 << 29) - 1);
     const float* coef = reinterpret_cast<const float*>(buf0 + (size_t)b * a.cap + m.z);
     const int* lidx = reinterpret_cast<const int*>(coef + NB * Rp);
     const float* fv = reinterpret_cast<const float*>(lidx + Rp);
@@ -1251,11 +1257,11 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
           for (int ob = sub; ob < NOB; ob += TPR) {
             const int o1 = ob % W, o2 = ob / W;
             const float* ur = us + own + (D == 2 ? (o1 - P) * pitch : (o2 - P) * pitch + (o1 - P) * N0) - P;
-            const float* cr = coef + ob * W * Rp + row;
+            const float* cr = coef + (ob * Rp + row) * W;  // the row's line, 2P + 1 contiguous floats
 #pragma unroll
             for (int o0 = 0; o0 < W; ++o0) {
-              if (o0 & 1) acc1 = fmaf(cr[o0 * Rp], ur[o0], acc1);
-              else acc = fmaf(cr[o0 * Rp], ur[o0], acc);
+              if (o0 & 1) acc1 = fmaf(cr[o0], ur[o0], acc1);
+              else acc = fmaf(cr[o0], ur[o0], acc);
             }
           }
         }
@@ -1265,18 +1271,30 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
           const float v = us[own] + (fv[row] - acc) * dinv[row];
           us[own] = v;
           // refresh the copies of this value in the neighbours' halos
-          const int s = s_lo + srow;
-          for (int rr = max(0, r - H); rr <= min(cs - 1, r + H); ++rr) {
-            const int lo2 = rr * S - P;
-            if (rr == r || s < lo2 || s >= lo2 + S + 2 * P) continue;
-            float* rem = cluster.map_shared_rank(us, rr);
-            rem[G + (s - lo2) * pitch + rest] = v;
+          if (H == 1) {  // slabs at least P thick: only the first / last P slow indices are halo rows
+            if (srow < P && r > 0) cluster.map_shared_rank(us, r - 1)[G + (srow + S + P) * pitch + rest] = v;
+            if (srow >= S - P && r + 1 < cs) cluster.map_shared_rank(us, r + 1)[G + (srow - S + P) * pitch + rest] = v;
+          } else {
+            const int s = s_lo + srow;
+            for (int rr = max(0, r - H); rr <= min(cs - 1, r + H); ++rr) {
+              const int lo2 = rr * S - P;
+              if (rr == r || s < lo2 || s >= lo2 + S + 2 * P) continue;
+              float* rem = cluster.map_shared_rank(us, rr);
+              rem[G + (s - lo2) * pitch + rest] = v;
+            }
           }
         }
       }
     }
-    if (m.w >> 30) sync_all();  // rows of one colour never couple: a barrier after its last item only
+    // rows of one colour never couple: a barrier after its last item only; the
+    // halos change only between runs of colours with one residue of the slow index
+    if (m.w & (1 << 29)) sync_all();
+    else if (m.w & (1 << 30)) __syncthreads();
+    synced = (m.w & (1 << 30)) != 0;
   }
+  // after an expired wait: let the copies still in flight land (bounded) before the CTA exits
+  if (!ok && tid == 0)
+    for (int j = max(0, cur); j < issued; ++j) mbar_wait(smem_u32(&mbar[j % nbuf]), (unsigned)((j / nbuf) & 1));
   // the slab back to global memory
   double* ug = a.u + pm.off;
   const int n_own = (s_hi - s_lo) * plane;

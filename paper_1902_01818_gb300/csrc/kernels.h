@@ -40,7 +40,7 @@ cudaError_t launch_gs_sweep(int d, int p, bool f32, int blocks, cudaStream_t st,
 struct GsStagedArgs {
   int c_begin, c_end, forward;  // base colours of the phase, sweep direction
   int K, csize, base;           // patches, CTAs per patch cluster, base colours per parity
-  int nbuf, cap;                // chunk buffers (1: the CTA's whole phase at once, or 2) of cap bytes
+  int nbuf, cap;                // chunk buffers of cap bytes (1: the CTA's whole phase at once; else a ring)
   int threads, tpr;             // CTA size (256, 512 or 1024) and threads per row (4..32, power of two)
   const int* phase_patches;     // cluster q sweeps patch phase_patches[q]
   const int* slab;              // slab height (slow indices) per patch
@@ -85,6 +85,11 @@ void launch_prolong(int d, bool f32, int ntiles, cudaStream_t st, const Tile* ti
 int gemm_tile(int arith);
 // fused fast diagonalisation of small 2D patch interiors: one CTA per patch
 constexpr int kFdSmallSmem = 200 * 1024;
+// chunk buffers of the streamed Gauss-Seidel phase: two (one copy in flight
+// while one is read) measured fastest; more buffers mean smaller chunks, and
+// bulk copies of one SM complete one after another with a fixed cost each
+constexpr int kGsRing = 2;
+constexpr int kGsRingMax = 8;
 int fd_small_smem(int n0, int n1, bool f32);  // shared memory of one patch (must be <= kFdSmallSmem)
 cudaError_t prepare_fd_small();
 void launch_fd_small(int npatch, int smem, bool f32, cudaStream_t st, const FdSmall* patches, const double* r,

@@ -625,7 +625,9 @@ void build_pieces(const std::vector<Piece>& pcs, const Level& L, Arena& A, DLeve
 // Colour blocks of the staged patch-parallel sweep (mixed path).  A group is
 // (base colour c, patch k, slab r of the patch's cluster); its rows are split
 // into as few items as keep two item buffers in shared memory, each item a
-// block of float coef[o][Rp], int lidx[Rp] ((slow index - slab start) << 20 |
+// block of float coef[line][Rp][2p+1] (line: the band offsets along the slower
+// directions; a row's 2p+1 coefficients along xi_0 contiguous, so one thread
+// reads them at fixed offsets), int lidx[Rp] ((slow index - slab start) << 20 |
 // index in the plane), float f[Rp] (f minus the couplings to the other parity,
 // written before each phase) and float dinv[Rp] (1 / diagonal), padded to 16
 // bytes.  Rp >= rows and the shared-memory pitch of a slow index are chosen so
@@ -663,6 +665,12 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
     if (v >= 48 && v <= 225) limit = (int64_t)v * 1024;
   }
   auto item_bytes = [&](int rp) { return ((int64_t)(nb + 3) * rp * 4 + 15) / 16 * 16; };
+  // buffers of the streamed (non-resident) case
+  int ring = kGsRing;
+  if (const char* env = std::getenv("MGIGA_GS_NBUF")) {  // tuning
+    const int v = std::atoi(env);
+    if (v >= 2 && v <= kGsRingMax) ring = v;
+  }
   struct Plan {
     int cs = 0, threads = 0, tpr = 0, nbuf = 0, max_items = 0;
     int64_t cap = 0, total = 0;
@@ -693,13 +701,21 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
     for (int v : pl.rows) max_rows = std::max(max_rows, v);
     // CTA shape: a row is summed by tpr threads (its coefficient lines split
     // among them, then a shuffle tree), threads / tpr rows at a time; minimise
-    // the dependent steps of the longest colour
+    // the dependent steps of the longest colour plus the cycles its warp
+    // instructions take on the SM's four schedulers (per warp and line 3 W:
+    // two loads and an FMA per coefficient; per warp and pass ~50 for the
+    // row's set-up and update).  Measured on the finest level at p = 6
+    // (16-CTA clusters): 512 x 4 0.194 ms, 1024 x 4 0.201, 512 x 8 0.206,
+    // 1024 x 8 0.210, 256 x 4 0.213, 1024 x 16 0.237 -- the order this cost gives.
     double best = 1e30;
     for (int nt : {256, 512, 1024})
       for (int tpr : {4, 8, 16, 32}) {
         const int passes = std::max(1, (max_rows + nt / tpr - 1) / (nt / tpr));
         const int lines = (nob + tpr - 1) / tpr;
-        const double cost = passes * (lines * (W * 2.0 + 40.0) + 40.0 * std::log2((double)tpr)) + nt / 8.0;
+        const double latency = passes * (lines * (W * 2.0 + 40.0) + 40.0 * std::log2((double)tpr)) + nt / 8.0;
+        const double issue =
+            (double)max_rows * tpr / 32.0 * (lines * 3.0 * W + 6.0 * std::log2((double)tpr) + 50.0) / 4.0;
+        const double cost = latency + issue;
         if (cost < best) {
           best = cost;
           pl.threads = nt;
@@ -715,11 +731,11 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
       }
     }
     const int tpr = pl.tpr;
-    // padded rows: coefficient line q of row j is word q W Rp + j
+    // padded rows: coefficient line q of row j starts at word (q Rp + j) W
     pl.rp_deg.assign(32, 0);
     pl.rp_best = 1 << 30;
     for (int x = 0; x < 32; ++x) {
-      pl.rp_deg[x] = bank_degree(tpr, [&](int j, int q) { return q * W * x + j; });
+      pl.rp_deg[x] = bank_degree(tpr, [&](int j, int q) { return (q * x + j) * W; });
       pl.rp_best = std::min(pl.rp_best, pl.rp_deg[x]);
     }
     // slab pitch and guards; the extended slab
@@ -755,10 +771,12 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
       pl.cap = (max_region + 15) / 16 * 16;
       pl.max_items = B;
     } else {
-      // two buffers; groups larger than a buffer split into near-equal items
-      pl.nbuf = 2;
+      // a ring of nbuf buffers, nbuf - 1 chunks in flight while one is read;
+      // groups larger than a buffer split into near-equal items
+      pl.nbuf = ring;
+      const int64_t mbar_room = (8 * (int64_t)ring + 15) / 16 * 16;
       for (int extra = 1; extra <= 8; extra *= 2) {  // meta room for up to extra x B items
-        const int64_t cap = (limit - pl.off_buf - 16 - 32 * (int64_t)B * extra) / 2 / 16 * 16;
+        const int64_t cap = (limit - pl.off_buf - mbar_room - 32 * (int64_t)B * extra) / ring / 16 * 16;
         int rmax = 0;
         while (item_bytes(pl.rp_of(rmax + 1)) <= cap) ++rmax;
         if (rmax < 1) return false;
@@ -779,7 +797,7 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
       if (pl.cap == 0) return false;
     }
     pl.off_mbar = (int)((pl.off_buf + pl.nbuf * pl.cap + 15) / 16 * 16);
-    pl.off_meta = pl.off_mbar + 16;
+    pl.off_meta = pl.off_mbar + (8 * pl.nbuf + 15) / 16 * 16;
     pl.total = pl.off_meta + 32 * (int64_t)pl.max_items;
     return pl.total <= limit;
   };
@@ -854,7 +872,9 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
       for (int row = 0; row < R; ++row) {
         const int e = members[g][it_r0[i] + row];
         const int64_t pos = gpos[e];
-        for (int o = 0; o < nb; ++o) coef[(size_t)o * Rp + row] = (float)L.band[(size_t)o * L.nloc + pos];
+        for (int ob = 0; ob < nob; ++ob)
+          for (int o0 = 0; o0 < W; ++o0)
+            coef[((size_t)ob * Rp + row) * W + o0] = (float)L.band[(size_t)(ob * W + o0) * L.nloc + pos];
         const int64_t loc = pos - L.off[k];
         const int s = (int)(loc / plane), rest = (int)(loc % plane);
         lidx[row] = ((s - r * pl.slab[k]) << 20) | rest;
@@ -863,6 +883,15 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
       }
     }
   }
+  // A base colour fixes every index modulo p + 1 (the slow one outermost), so
+  // the rows of a run of colours with one residue rho of the slow index read
+  // only their own slow index among those = rho (mod p + 1) within reach P:
+  // during such a run no CTA reads a halo value a neighbour updates, nor
+  // updates one a neighbour reads.  The cluster barrier (halo exchange) is
+  // needed only where the residue changes; between the colours of a run the
+  // CTA barrier orders the CTA's own slab.
+  const int run_len = B % (P + 1) == 0 ? B / (P + 1) : 1;
+  auto slow_residue = [&](int c) { return (c % B) / run_len; };
   // per (direction, phase, k, r): items in sweep order grouped into chunks
   const size_t nreg = (size_t)2 * 2 * K * cs;
   std::vector<int64_t> item_ptr(nreg + 1, 0);
@@ -875,15 +904,18 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
         for (int r = 0; r < cs; ++r) {
           const size_t reg = (((size_t)dir * 2 + ph) * K + k) * cs + r;
           const int c0 = ph * B, nc = std::max(0, std::min((ph + 1) * B, nbase) - c0);
-          std::vector<int> seq;  // items in sweep order; last item of each colour flagged
+          // items in sweep order; the last item of each colour flagged (1), and
+          // of each run of colours with one residue of the slow index (2)
+          std::vector<int> seq;
           std::vector<char> last;
           for (int ci = 0; ci < nc; ++ci) {
             const int c = dir == 0 ? c0 + ci : c0 + nc - 1 - ci;
             const int g = (c * K + k) * cs + r;
             const int n_i = sub_ptr[g + 1] - sub_ptr[g];
+            const bool run_end = ci == nc - 1 || slow_residue(c) != slow_residue(dir == 0 ? c + 1 : c - 1);
             for (int j = 0; j < n_i; ++j) {
               seq.push_back(dir == 0 ? sub_ptr[g] + j : sub_ptr[g + 1] - 1 - j);
-              last.push_back(j == n_i - 1);
+              last.push_back(j == n_i - 1 ? (run_end ? 3 : 1) : 0);
             }
           }
           std::vector<int> chunk_of(seq.size());
@@ -902,7 +934,8 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
           item_ptr[reg] = (int64_t)cmeta.size();
           for (size_t q = 0; q < seq.size(); ++q) {
             const int i = seq[q], j = chunk_of[q];
-            cmeta.push_back(make_int4(it_rows[i], j, (int)(it_off[i] - lo[j]), it_rp[i] | (last[q] ? 1 << 30 : 0)));
+            cmeta.push_back(make_int4(it_rows[i], j, (int)(it_off[i] - lo[j]),
+                                      it_rp[i] | ((last[q] & 1) << 30) | ((last[q] >> 1) << 29)));
           }
           for (size_t q = 0; q < seq.size(); ++q)
             chunks.push_back(q < lo.size() ? make_int4((int)(uint32_t)(lo[q] & 0xffffffffLL), (int)(lo[q] >> 32),

@@ -147,3 +147,64 @@ def test_mixed_smoother_batched_contractions(name, precision, monkeypatch):
         got = lib.apply("smooth", l, f, u)
         assert np.linalg.norm(got - ref) <= smooth_tol(precision, prob["dim"]) * np.linalg.norm(ref - u), l
     lib.close()
+
+
+@pytest.mark.parametrize("cs", [2, 4, 8, 16])
+@pytest.mark.parametrize("name", ["sipg2d_p3", "sipg3d_p2", "conf2d_p2"])
+def test_gauss_seidel_cluster_sizes(name, cs, monkeypatch):
+    """The patch-parallel sweep with its patches cut into 2..16 slabs (one CTA
+    each, halos exchanged between runs of colours with one slow residue): both
+    directions match the FP64 sweep to FP32 rounding on every level, also where
+    a slab is thinner than the band's reach (halos from several neighbours)."""
+    monkeypatch.setenv("MGIGA_GS_CS", str(cs))
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    lib = binding().Solver(prob, levels=levels, smoother="hybrid", precision="fp32", **opt)
+    orc = omg.Multigrid(prob, levels=levels, smoother="hybrid", **opt)
+    rng = np.random.default_rng(13)
+    for l in range(1, levels):
+        A = orc.h["A"][l]
+        n = A.shape[0]
+        u, f = rng.standard_normal(n), rng.standard_normal(n)
+        for op, fn in (("gs_fwd", orc.gs[l].forward), ("gs_bwd", orc.gs[l].backward)):
+            ref = fn(f, u)
+            got = lib.apply(op, l, f, u)
+            assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref - u), (l, op)
+    lib.close()
+
+
+_STREAMED = {}
+
+
+def _streamed_case():
+    """The benchmark layout at 64/96 intervals, p = 4 (62,180 unknowns): the
+    patches' coefficient blocks exceed shared memory, so the sweep streams them
+    through its ring of chunk buffers.  Oracle sweeps on the finest level only."""
+    if not _STREAMED:
+        from oracle import hierarchy, smoothers
+        prob, opts = W.sipg_3x3(4, scale=1, smoother="hybrid")
+        h = hierarchy.build(prob, 1)
+        col = smoothers.colouring(prob, h["knots"][0], h["num"][0])
+        _STREAMED.update(prob=prob, opts=opts, A=h["A"][0],
+                         gs=smoothers.GaussSeidel(h["A"][0], smoothers.gs_order(col)))
+    return _STREAMED
+
+
+@pytest.mark.parametrize("cs,nbuf", [(1, 2), (1, 8), (16, 2), (16, 3)])
+def test_gauss_seidel_streamed_ring(cs, nbuf, monkeypatch):
+    """Streamed coefficient blocks through 2..8 chunk buffers, with colours split
+    over several chunks: both sweep directions match the FP64 sweep."""
+    monkeypatch.setenv("MGIGA_GS_CS", str(cs))
+    monkeypatch.setenv("MGIGA_GS_NBUF", str(nbuf))
+    c = _streamed_case()
+    o = c["opts"]
+    lib = binding().Solver(c["prob"], levels=0, smoother="hybrid", tau=o["tau"], delta=o["delta"],
+                           precision="fp32")
+    rng = np.random.default_rng(14)
+    n = c["A"].shape[0]
+    u, f = rng.standard_normal(n), rng.standard_normal(n)
+    for op, fn in (("gs_fwd", c["gs"].forward), ("gs_bwd", c["gs"].backward)):
+        ref = fn(f, u)
+        got = lib.apply(op, lib.levels - 1, f, u)
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref - u), op
+    lib.close()

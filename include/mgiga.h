@@ -267,6 +267,17 @@ enum {
                                coefficients and arithmetic unless the precision is FP64 */
 };
 mgiga_status mgiga_kernel_launches(const mgiga_handle* h, long long* n);
+
+/* Diagnostics of the bounded device waits.  Every spin-wait of the kernels
+ * (grid barrier, mbarrier of an asynchronous copy) gives up after a fixed
+ * number of polls (2^21), records the expiry in a device flag and lets the
+ * launch end; the host reads the flag after the stream drains and the call
+ * returns MGIGA_ETIMEOUT, the handle staying usable.  This call runs one such
+ * wait on a barrier phase that nothing completes, with `iterations` polls
+ * (1 .. 2^21), on the handle's stream (after mgiga_assemble): it returns
+ * MGIGA_ETIMEOUT with the message of a real expiry when the wait gave up,
+ * and *elapsed_ms (may be NULL) receives the wait's device duration. */
+mgiga_status mgiga_check_wait_expiry(mgiga_handle* h, long long iterations, double* elapsed_ms);
 mgiga_status mgiga_time_stage(mgiga_handle* h, int stage, int level, int reps, double* ms);
 mgiga_status mgiga_stage_work(const mgiga_handle* h, int stage, int level, double* flops, double* bytes);
 

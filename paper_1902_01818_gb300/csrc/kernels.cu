@@ -266,8 +266,10 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase) {
-  for (long long it = 0; it < (1ll << 21); ++it) {
+// Bounded wait for the completion of an mbarrier phase: false after `limit`
+// polls (the kernels use the default).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long long limit = 1ll << 21) {
+  for (long long it = 0; it < limit; ++it) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -1222,6 +1224,7 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
   bool ok = true;
   bool synced = true;  // no item has been read since the last barrier
   int cur = -1;
+  int failed_at = -1;  // the chunk whose wait expired
   for (int ci = 0; ci < nc; ++ci) {
     // rows, chunk, offset in chunk, Rp | (last item of its colour) << 30 | (last of its slow-residue run) << 29
     const int4 m = cm[ci];
@@ -1234,6 +1237,7 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
       const unsigned parity = (unsigned)((m.y / nbuf) & 1);
       if (ok && !mbar_wait(smem_u32(&mbar[b]), parity)) {
         ok = false;
+        failed_at = m.y;
         atomicExch(a.err, 2);
       }
       if (tid == 0 && ok && nbuf >= 2 && m.y >= 1 && m.y + nbuf - 1 < nchunk) copy(m.y + nbuf - 1);
@@ -1294,7 +1298,7 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
   }
   // after an expired wait: let the copies still in flight land (bounded) before the CTA exits
   if (!ok && tid == 0)
-    for (int j = max(0, cur); j < issued; ++j) mbar_wait(smem_u32(&mbar[j % nbuf]), (unsigned)((j / nbuf) & 1));
+    for (int j = failed_at; j < issued; ++j) mbar_wait(smem_u32(&mbar[j % nbuf]), (unsigned)((j / nbuf) & 1));
   // the slab back to global memory
   double* ug = a.u + pm.off;
   const int n_own = (s_hi - s_lo) * plane;
@@ -1710,6 +1714,27 @@ cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t
   GsStagedArgs arg = a;
   void* args[] = {&arg};
   return cudaLaunchKernelExC(&cfg, gs_staged_ptr(d, p), args);
+}
+
+// One thread waits, with the kernels' bounded-wait routine and `limit` polls,
+// on an mbarrier phase that nothing completes, and records the expiry in
+// *err the way the kernels do (no copy or peer is involved, so nothing is
+// left in flight); *elapsed_ns: the wait's duration by the global timer.
+__global__ void wait_expiry_probe(long long limit, int* err, long long* elapsed_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+  unsigned long long t0, t1;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  const bool done = mbar_wait(smem_u32(&bar), 0u, limit);
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+  *elapsed_ns = (long long)(t1 - t0);
+  if (!done) atomicExch(err, 2);
+}
+
+void launch_wait_expiry_probe(long long limit, cudaStream_t st, int* err, long long* elapsed_ns) {
+  ++g_launches;
+  wait_expiry_probe<<<1, 32, 0, st>>>(limit, err, elapsed_ns);
 }
 
 void launch_gs_fill_phase(int e0, int n, int nx, const int* xent, cudaStream_t st, const int64_t* f_off,

@@ -61,6 +61,7 @@ struct GsStagedArgs {
 bool gs_staged_fits(int d, int p, int csize, int smem, int threads);
 cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t st, const GsStagedArgs& a);
 // xent: the nx entries of [e0, e0 + n) with couplings to the other parity
+void launch_wait_expiry_probe(long long limit, cudaStream_t st, int* err, long long* elapsed_ns);
 void launch_gs_fill_phase(int e0, int n, int nx, const int* xent, cudaStream_t st, const int64_t* f_off,
                           const int64_t* gs_pos, const int2* xrange, const int64_t* x_col, const double* x_val,
                           const double* f, const double* u, unsigned char* pool);

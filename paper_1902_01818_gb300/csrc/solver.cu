@@ -178,7 +178,8 @@ struct mgiga_handle {
   double* partials = nullptr;
   unsigned int* counter = nullptr;
   unsigned int* gs_bar = nullptr;  // grid barrier state of the Gauss-Seidel sweep
-  int* gs_err = nullptr;           // set by a sweep whose barrier wait gave up
+  int* gs_err = nullptr;           // set by a kernel whose bounded wait gave up
+  long long* probe_ns = nullptr;   // duration of the wait-expiry check
   double *in1 = nullptr, *in2 = nullptr, *out = nullptr;  // staging (global order)
   double* host_scal = nullptr;                            // pinned
   cudaGraphExec_t g_iter_a = nullptr, g_iter_b = nullptr, g_vcycle = nullptr;
@@ -1269,7 +1270,7 @@ void check_device_timeout(mgiga_handle* h) {
   if (e) {
     CK(cudaMemsetAsync(h->gs_err, 0, sizeof(int), h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    throw SetupError(MGIGA_ETIMEOUT, "a Gauss-Seidel grid barrier wait expired");
+    throw SetupError(MGIGA_ETIMEOUT, "a bounded device wait expired (grid barrier or asynchronous copy)");
   }
 }
 
@@ -1923,6 +1924,26 @@ mgiga_status mgiga_solve(mgiga_handle* h, const double* rhs, double* u, double t
       CK(cudaStreamSynchronize(h->stream));
     }
     return s;
+  });
+}
+
+mgiga_status mgiga_check_wait_expiry(mgiga_handle* h, long long iterations, double* elapsed_ms) {
+  if (!h) return MGIGA_EINVAL;
+  if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  if (iterations < 1 || iterations > (1ll << 21)) return fail(h, MGIGA_EINVAL, "iterations outside [1, 2^21]");
+  return guarded_call(h, [&]() -> mgiga_status {
+    if (!h->probe_ns) h->probe_ns = h->arena->alloc<long long>(1);
+    {
+      LaunchScope scope(h);
+      launch_wait_expiry_probe(iterations, h->stream, h->gs_err, h->probe_ns);
+      check_launch();
+    }
+    long long ns = 0;
+    CK(cudaMemcpyAsync(&ns, h->probe_ns, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (elapsed_ms) *elapsed_ms = ns * 1e-6;
+    check_device_timeout(h);
+    return MGIGA_OK;
   });
 }
 

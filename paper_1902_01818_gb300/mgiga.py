@@ -77,6 +77,7 @@ _SIGS = {
     "mgiga_apply_d": (C.c_int, [_H, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mgiga_residual_noalloc_d": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mgiga_kernel_launches": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
+    "mgiga_check_wait_expiry": (C.c_int, [_H, C.c_longlong, _D]),
     "mgiga_time_stage": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, _D]),
     "mgiga_stage_work": (C.c_int, [_H, C.c_int, C.c_int, _D, _D]),
     "mgiga_num_levels": (C.c_int, [_H, _I]),
@@ -214,6 +215,12 @@ class Solver:
         n = C.c_int()
         self._check(_lib.mgiga_pieces(self._h, level, out.ctypes.data_as(_I), C.byref(n)))
         return out, n.value
+
+    def check_wait_expiry(self, iterations):
+        """One bounded device wait on a barrier nothing completes: (status, ms)."""
+        ms = C.c_double()
+        st = _lib.mgiga_check_wait_expiry(self._h, iterations, C.byref(ms))
+        return st, ms.value
 
     def kernel_launches(self):
         n = C.c_longlong()

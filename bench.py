@@ -125,6 +125,22 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """The largest value of x over all ranks (the timed region ends with the slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, unknowns_per_rank, steps, ms):
+    """Whole-job DoF/s: every rank solves its own replica of the workload (weak scaling)."""
+    return world * unknowns_per_rank * steps / (ms / 1e3)
+
+
 def workload(p, scale, smoother):
     from paper_1902_01818_gb300 import workloads as W
     return W.sipg_3x3(p, scale=scale, smoother=smoother)
@@ -382,25 +398,22 @@ def main():
         ev1.record()
         torch.cuda.synchronize()
         barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, device="cuda")
     launches = sum(s.kernel_launches() for s in solvers) - launches0
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     step_ms = [a.elapsed_time(b) for a, b, _ in per_step]
     iters = [x[0] for x in per_step[-1][2]]
     rels = [x[1] for x in per_step[-1][2]]
-    value = world * total_dof * args.steps / (ms / 1e3)
+    value = job_value(world, total_dof, args.steps, ms)
 
-    # end to end: host buffers, H2D and D2H inside the timed region
+    # end to end: host buffers, H2D and D2H inside the timed region (slowest rank)
     torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     for _ in range(max(1, args.steps // 2)):
         step(host_path=True)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
-    e2e = {"value": world * total_dof / e2e_s, "unit": "DoF/s",
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / max(1, args.steps // 2), world, device="cuda")
+    e2e = {"value": job_value(world, total_dof, 1, e2e_ms), "unit": "DoF/s",
            "h2d_bytes_per_step": int(2 * 8 * total_dof), "d2h_bytes_per_step": int(8 * total_dof)}
 
     # plain FP64 comparison: same workload, FP64 smoothers

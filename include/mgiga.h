@@ -186,7 +186,9 @@ mgiga_status mgiga_vcycle_d(mgiga_handle* h, const double* r, double* z);
  * Sec. 4) with PCG (outer = PCG) or the V-cycle as solver (outer = DIRECT).
  * u: initial guess on entry, solution on exit.  iters / final_relres may be
  * NULL.  Returns MGIGA_ENOCONV with the last iterate in u when max_iter
- * outer iterations do not suffice (max_iter = k yields the k-th iterate). */
+ * outer iterations do not suffice (max_iter = k yields the k-th iterate), and
+ * MGIGA_EBREAKDOWN when rhs or the initial guess holds NaN/Inf or CG breaks
+ * down (p^T A p <= 0, non-finite residual); a zero rhs gives u = 0. */
 mgiga_status mgiga_solve(mgiga_handle* h, const double* rhs, double* u, double tol,
                          int* iters, double* final_relres);
 mgiga_status mgiga_solve_d(mgiga_handle* h, const double* rhs, double* u, double tol,
@@ -270,11 +272,12 @@ mgiga_status mgiga_kernel_launches(const mgiga_handle* h, long long* n);
 
 /* Diagnostics of the bounded device waits.  Every spin-wait of the kernels
  * (grid barrier, mbarrier of an asynchronous copy) gives up after a fixed
- * number of polls (2^21), records the expiry in a device flag and lets the
- * launch end; the host reads the flag after the stream drains and the call
- * returns MGIGA_ETIMEOUT, the handle staying usable.  This call runs one such
+ * number of polls (2^18 for an mbarrier, ~1 s), records the expiry in a
+ * device flag and lets the launch end; the host reads the flag after the
+ * stream drains and the call returns MGIGA_ETIMEOUT, the handle staying
+ * usable.  This call runs one such
  * wait on a barrier phase that nothing completes, with `iterations` polls
- * (1 .. 2^21), on the handle's stream (after mgiga_assemble): it returns
+ * (1 .. 2^18), on the handle's stream (after mgiga_assemble): it returns
  * MGIGA_ETIMEOUT with the message of a real expiry when the wait gave up,
  * and *elapsed_ms (may be NULL) receives the wait's device duration. */
 mgiga_status mgiga_check_wait_expiry(mgiga_handle* h, long long iterations, double* elapsed_ms);

@@ -268,7 +268,7 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 
 // Bounded wait for the completion of an mbarrier phase: false after `limit`
 // polls (the kernels use the default).
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long long limit = 1ll << 21) {
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long long limit = kMbarPolls) {
   for (long long it = 0; it < limit; ++it) {
     unsigned ok;
     asm volatile(

@@ -91,6 +91,9 @@ constexpr int kFdSmallSmem = 200 * 1024;
 // bulk copies of one SM complete one after another with a fixed cost each
 constexpr int kGsRing = 2;
 constexpr int kGsRingMax = 8;
+// polls of a bounded mbarrier wait before it gives up: a failed poll suspends
+// ~3.8 us on a GB300 (measured with the wait-expiry check), so ~1 s
+constexpr long long kMbarPolls = 1ll << 18;
 int fd_small_smem(int n0, int n1, bool f32);  // shared memory of one patch (must be <= kFdSmallSmem)
 cudaError_t prepare_fd_small();
 void launch_fd_small(int npatch, int smem, bool f32, cudaStream_t st, const FdSmall* patches, const double* r,

@@ -1807,6 +1807,8 @@ static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, do
   read_scal();
   const double ff = h->host_scal[S_FF];
   if (iters) *iters = 0;
+  if (!std::isfinite(ff) || !std::isfinite(h->host_scal[S_RR]))
+    return fail(h, MGIGA_EBREAKDOWN, "non-finite right-hand side or initial guess");
   if (!(ff > 0.0)) {
     // zero right-hand side: the solution is zero
     CK(cudaMemsetAsync(h->x, 0, n * sizeof(double), st));
@@ -1930,7 +1932,7 @@ mgiga_status mgiga_solve(mgiga_handle* h, const double* rhs, double* u, double t
 mgiga_status mgiga_check_wait_expiry(mgiga_handle* h, long long iterations, double* elapsed_ms) {
   if (!h) return MGIGA_EINVAL;
   if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
-  if (iterations < 1 || iterations > (1ll << 21)) return fail(h, MGIGA_EINVAL, "iterations outside [1, 2^21]");
+  if (iterations < 1 || iterations > kMbarPolls) return fail(h, MGIGA_EINVAL, "iterations outside [1, 2^18]");
   return guarded_call(h, [&]() -> mgiga_status {
     if (!h->probe_ns) h->probe_ns = h->arena->alloc<long long>(1);
     {

@@ -46,7 +46,7 @@ def hbm_peak_gbs():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one application of a stage on the
-# finest level, per degree, from one ncu capture of this build on a GB300 (profiles/
+# finest level, per degree, from one ncu capture of the current kernels on a GB300 (profiles/
 # traffic_sipg3x3_finest_level.md gives the command and the per-kernel figures).  Used only for the
 # default configuration (scale 3, hybrid, TF32 contractions, 8-CTA GS clusters; the band, residual
 # and GS kernels are the same in the FP32 mode); None elsewhere or when a stage's kernels change.

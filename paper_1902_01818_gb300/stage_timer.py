@@ -7,7 +7,7 @@ For every level (finest first) prints the device milliseconds of one
 application of each stage (mgiga_time_stage: CUDA events on the handle's
 stream, after one warm-up application), plus the algorithmic flops and bytes
 of the band product, the fast diagonalisation and a Gauss-Seidel sweep.  Also
-the driver of the ncu captures of single stages: with --stages gs --levels L
+the program the ncu captures of single stages run: with --stages gs --levels L
 the only kernels launched after set-up are one warm-up and `reps` sweeps of
 level L.
 """

@@ -255,7 +255,8 @@ mgiga_status mgiga_residual_noalloc_d(mgiga_handle* h, int level, const double* 
  * (BAND: 2 nnz(A_l) flops, 8 nnz(A_l) + 24 N_l bytes; FD: 4 d n per interior
  * DoF flops, 24 bytes per interior DoF; GS: as BAND, with 4 bytes per nonzero
  * when the smoothers run in FP32 (precision other than FP64); RESIDUAL: as
- * BAND, 4 bytes per nonzero on the mixed path). */
+ * BAND, 4 bytes per nonzero on the mixed path); MGIGA_ESTATE before
+ * mgiga_assemble (the operators are not yet built). */
 enum {
   MGIGA_STAGE_BAND = 0,     /* band product A_l u (a1) */
   MGIGA_STAGE_FD = 1,       /* interior fast diagonalisation (a2) */

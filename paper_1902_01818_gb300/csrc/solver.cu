@@ -1737,6 +1737,7 @@ mgiga_status mgiga_apply(mgiga_handle* h, int op, int level, const double* a, co
   if (!h) return MGIGA_EINVAL;
   if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
   if (level < 0 || level >= h->levels) return fail(h, MGIGA_EINVAL, "bad level");
+  if (!a || !out) return fail(h, MGIGA_EINVAL, "NULL vector");
   return guarded_call(h, [&]() -> mgiga_status {
     const int nin = (op == MGIGA_OP_PROLONG) ? h->L[level - (level > 0 ? 1 : 0)].ndof : h->L[level].ndof;
     const int nout = (op == MGIGA_OP_RESTRICT) ? h->L[level - (level > 0 ? 1 : 0)].ndof : h->L[level].ndof;
@@ -1755,6 +1756,7 @@ static void run_vcycle_top(mgiga_handle* h) { vcycle(h, h->levels - 1); }
 mgiga_status mgiga_vcycle_d(mgiga_handle* h, const double* r, double* z) {
   if (!h) return MGIGA_EINVAL;
   if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  if (!r || !z) return fail(h, MGIGA_EINVAL, "NULL vector");
   return guarded_call(h, [&]() -> mgiga_status {
     after_legacy(h);
     LaunchScope scope(h);
@@ -1772,6 +1774,7 @@ mgiga_status mgiga_vcycle_d(mgiga_handle* h, const double* r, double* z) {
 mgiga_status mgiga_vcycle(mgiga_handle* h, const double* r, double* z) {
   if (!h) return MGIGA_EINVAL;
   if (!h->assembled) return fail(h, MGIGA_ESTATE, "mgiga_assemble has not run");
+  if (!r || !z) return fail(h, MGIGA_EINVAL, "NULL vector");
   return guarded_call(h, [&]() -> mgiga_status {
     const int n = h->L[h->levels - 1].ndof;
     CK(cudaMemcpyAsync(h->in1, r, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -2024,13 +2027,16 @@ mgiga_status mgiga_stage_work(const mgiga_handle* h, int stage, int level, doubl
   if (!h || level < 0 || level >= h->levels) return MGIGA_EINVAL;
   if (!stage_valid(h, stage, level)) return MGIGA_EINVAL;
   const Level& L = h->L[level];
+  if (L.band.empty()) return MGIGA_ESTATE;  // operators are assembled by mgiga_assemble
+  // the mixed path keeps FP32 band copies for the cycle's residuals (levels >= 1) and sweeps
+  const bool f32 = h->opt.precision != MGIGA_PREC_FP64;
   double fl = 0.0, by = 0.0;
   if (stage == MGIGA_STAGE_BAND || stage == MGIGA_STAGE_RESIDUAL) {
     // every nonzero once (FP32 coefficients for the residual of the mixed path), u and f read, out written
     double nnz = 0.0;
     for (double v : L.band) nnz += v != 0.0;
     fl = 2.0 * nnz;
-    by = (stage == MGIGA_STAGE_RESIDUAL && h->D[level].band32 ? 4.0 : 8.0) * nnz + 24.0 * (double)L.nloc;
+    by = (stage == MGIGA_STAGE_RESIDUAL && f32 && level > 0 ? 4.0 : 8.0) * nnz + 24.0 * (double)L.nloc;
   } else if (stage == MGIGA_STAGE_FD) {
     for (int k = 0; k < L.K; ++k) {
       double nint = 1.0, sum = 0.0;
@@ -2043,7 +2049,7 @@ mgiga_status mgiga_stage_work(const mgiga_handle* h, int stage, int level, doubl
     double nnz = 0.0;
     for (double v : L.band) nnz += v != 0.0;
     fl = 2.0 * nnz;
-    by = (h->D[level].arith >= 1 ? 4.0 : 8.0) * nnz + 24.0 * (double)L.nloc;
+    by = (f32 ? 4.0 : 8.0) * nnz + 24.0 * (double)L.nloc;
   } else {
     return MGIGA_EINVAL;
   }

@@ -111,3 +111,9 @@ def test_invalid_problems_return_status():
         s.vcycle(np.zeros(s.ndof()))
     assert e.value.status == mg.ESTATE
     s.close()
+    s = mg.Solver(prob, levels=2, smoother="hybrid", assemble=False)
+    for stage in ("band", "residual", "gs", "fd"):  # no operators before the set-up
+        with pytest.raises(mg.MgigaError) as e:
+            s.stage_work(stage, 1)
+        assert e.value.status == mg.ESTATE
+    s.close()

@@ -13,9 +13,15 @@ One handle is used by one thread at a time.
 
     srv = Server(workers=4, hbm_budget=120 << 30)
     srv.start()
-    fut = srv.submit(key, problem, options, rhs)
+    fut = srv.submit(key, problem, options, rhs)   # rhs: array, or an int seed
     u, iterations, relres, latency_s = fut.result()
-    srv.stop(); srv.stats()  # solves, rejected, p50/p99 latency, set-ups, evictions
+    srv.stop(); srv.stats()  # solves, solves/s, rejected, p50/p99 latency, set-ups,
+                             # evictions, resident bytes, queue length (now / largest)
+
+An int rhs is a seed: the worker draws i.i.d. N(0, 1) load coefficients of the
+operator's size once the handle exists.  `python -m paper_1902_01818_gb300.serve`
+serves the seeded serving stream with Poisson arrivals and prints the statistics
+as one JSON line.
 """
 import collections
 import concurrent.futures as cf
@@ -57,6 +63,7 @@ class Server:
         self.threads = []
         self.running = False
         self.latencies, self.rejected, self.setups, self.evictions = [], 0, 0, 0
+        self.t_first, self.t_last, self.max_queue = None, None, 0
 
     @staticmethod
     def _mgiga_factory(mgiga):
@@ -89,16 +96,25 @@ class Server:
 
     def submit(self, key, problem, options, rhs):
         fut = cf.Future()
+        rhs = rhs if isinstance(rhs, (int, np.integer)) else np.asarray(rhs, dtype=np.float64)
         with self.cv:
-            self.queue.append((key, problem, options, np.asarray(rhs, dtype=np.float64), time.perf_counter(), fut))
+            now = time.perf_counter()
+            if self.t_first is None:
+                self.t_first = now
+            self.queue.append((key, problem, options, rhs, now, fut))
+            self.max_queue = max(self.max_queue, len(self.queue))
             self.cv.notify()
         return fut
 
     def stats(self):
-        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
-        return {"solves": len(self.latencies), "rejected": self.rejected, "setups": self.setups,
-                "evictions": self.evictions, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "resident_bytes": self.used}
+        with self.cv:
+            lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+            span = (self.t_last - self.t_first) if self.t_last is not None else 0.0
+            return {"solves": len(self.latencies), "rejected": self.rejected, "setups": self.setups,
+                    "evictions": self.evictions, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                    "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                    "solves_per_s": len(self.latencies) / span if span > 0 else 0.0,
+                    "resident_bytes": self.used, "queue": len(self.queue), "max_queue": self.max_queue}
 
     # -- admission -----------------------------------------------------------
     def _evict_one_idle(self):
@@ -174,12 +190,63 @@ class Server:
                 continue
             try:
                 with e.lock:
+                    if isinstance(rhs, (int, np.integer)):
+                        from .workloads import random_vector
+                        rhs = random_vector(e.solver.ndof(), int(rhs), kind="normal")
                     u, it, rel, _st = e.solver.solve(rhs, tol=self.tol)
-                lat = time.perf_counter() - t0
+                done = time.perf_counter()
                 with self.cv:
-                    self.latencies.append(lat)
-                fut.set_result((u, it, rel, lat))
+                    self.latencies.append(done - t0)
+                    self.t_last = done if self.t_last is None else max(self.t_last, done)
+                fut.set_result((u, it, rel, done - t0))
             except Exception as exc:  # noqa: BLE001 -- reported to the caller
                 fut.set_exception(exc)
             finally:
                 self._release(e)
+
+
+def main(argv=None):
+    """Serve the seeded serving stream with Poisson arrivals; print the statistics."""
+    import argparse
+    import json
+
+    from . import workloads as W
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="HBM budget of the resident operators")
+    ap.add_argument("--rate", type=float, default=20.0, help="mean arrivals per second")
+    ap.add_argument("--max-patch-dof", type=float, default=1e5, help="upper end of the per-patch DoF range")
+    ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--seed", type=int, default=501)
+    args = ap.parse_args(argv)
+    srv = Server(workers=args.workers, hbm_budget=int(args.budget_gb * (1 << 30)), precision=args.precision)
+    arrivals = np.random.default_rng(args.seed + 7)
+    srv.start()
+    futs = []
+    t = time.perf_counter()
+    for key, prob, opts, rhs_seed in W.serving_stream(args.requests, seed=args.seed,
+                                                      max_patch_dof=args.max_patch_dof):
+        t += arrivals.exponential(1.0 / args.rate)
+        wait = t - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        futs.append(srv.submit(key, prob, opts, int(rhs_seed)))
+    failed, iters = 0, []
+    for f in futs:
+        try:
+            iters.append(f.result()[1])
+        except Rejected:
+            pass
+        except Exception:  # noqa: BLE001 -- counted and reported
+            failed += 1
+    st = srv.stats()
+    srv.stop()
+    st.update(requests=args.requests, failed=failed, workers=args.workers, budget_gb=args.budget_gb,
+              rate_per_s=args.rate, precision=args.precision,
+              mean_iterations=float(np.mean(iters)) if iters else None)
+    print(json.dumps(st), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -29,6 +29,9 @@ class _Fake:
     def device_bytes(self):
         return self.nbytes
 
+    def ndof(self):
+        return 5
+
     def close(self):
         self.closed = True
 
@@ -85,3 +88,21 @@ def test_many_concurrent_requests():
     st = srv.stats()
     srv.stop()
     assert st["solves"] == 40 and st["setups"] == 5 and st["evictions"] == 0
+
+
+def test_seed_right_hand_sides_and_throughput_statistics():
+    """An int right-hand side is a seed: the worker draws N(0, 1) load coefficients of
+    the operator's size; the statistics report solves/s and the admission queue."""
+    from paper_1902_01818_gb300 import workloads as W
+    srv, made = _server(10_000, workers=1, delay=0.02)
+    futs = [srv.submit("A", {"bytes": 10}, {}, 7) for _ in range(4)]  # queued before the workers start
+    assert srv.stats()["queue"] == 4 and srv.stats()["max_queue"] == 4
+    srv.start()
+    outs = [f.result(timeout=5) for f in futs]
+    expect = 2.0 * W.random_vector(5, 7, kind="normal")
+    for u, it, rel, lat in outs:
+        assert np.array_equal(u, expect)
+    st = srv.stats()
+    srv.stop()
+    assert st["queue"] == 0 and st["solves"] == 4
+    assert 0.0 < st["solves_per_s"] <= 4 / 0.08 * 1.01  # four 20 ms solves one after another

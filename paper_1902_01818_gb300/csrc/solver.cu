@@ -2004,19 +2004,23 @@ mgiga_status mgiga_time_stage(mgiga_handle* h, int stage, int level, int reps, d
   if (level < 0 || level >= h->levels || !stage_valid(h, stage, level)) return fail(h, MGIGA_EINVAL, "bad stage/level");
   return guarded_call(h, [&]() -> mgiga_status {
     LaunchScope scope(h);
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    struct Events {  // destroyed on every exit, also when a CUDA error throws
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      ~Events() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+      }
+    } ev;
+    CK(cudaEventCreate(&ev.e0));
+    CK(cudaEventCreate(&ev.e1));
     run_stage(h, stage, level);  // warm-up
-    CK(cudaEventRecord(e0, h->stream));
+    CK(cudaEventRecord(ev.e0, h->stream));
     for (int i = 0; i < reps; ++i) run_stage(h, stage, level);
-    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventRecord(ev.e1, h->stream));
     check_launch();
-    CK(cudaEventSynchronize(e1));
+    CK(cudaEventSynchronize(ev.e1));
     float t = 0.0f;
-    CK(cudaEventElapsedTime(&t, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    CK(cudaEventElapsedTime(&t, ev.e0, ev.e1));
     check_device_timeout(h);
     *ms = (double)t / reps;
     return MGIGA_OK;

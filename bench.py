@@ -32,6 +32,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "DoF/s to 1e-8 rel. residual (V-cycle-preconditioned CG, SIPG 3x3 patches, p=2..6)"
+METRIC_OF = {"sipg3x3": METRIC,
+             "cube-conforming": "DoF/s to 1e-8 rel. residual (V-cycle-preconditioned CG, conforming 2x2x2 cube patches)",
+             "cube-sipg": "DoF/s to 1e-8 rel. residual (V-cycle-preconditioned CG, SIPG 2x2x2 cube patches)"}
 # peaks: derived from unit counts and the maximum SM clock (2.07 GHz, 152 SMs)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA/clk/SM
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 128 FFMA/clk/SM
@@ -75,7 +78,8 @@ DRAM_TRAFFIC = {
 
 
 def dram_traffic(stage, degrees, args, f32):
-    if not (args.scale == 3 and args.smoother == "hybrid" and args.precision in ("fp32", "tf32")
+    if not (args.workload == "sipg3x3" and args.scale == 3 and args.smoother == "hybrid"
+            and args.precision in ("fp32", "tf32")
             and not args.sequential):
         return None
     if stage == "fd" and args.precision != "tf32":  # the table's contractions are the TF32 ones
@@ -100,7 +104,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--degrees", default="2,3,4,5,6")
+    ap.add_argument("--workload", default="sipg3x3", choices=list(WORKLOADS),
+                    help="sipg3x3: [0,3]^2 as 3x3 SIPG patches (the headline); cube-*: [0,1]^3 as "
+                         "2x2x2 patches, 48 intervals, conforming or SIPG")
+    ap.add_argument("--degrees", default=None, help="comma list (default: the workload's)")
     ap.add_argument("--scale", type=int, default=3, help="interval multiplier of 64/96 (3: 192/288)")
     ap.add_argument("--smoother", default="hybrid", choices=["scms", "hybrid"])
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16", "fp64"],
@@ -141,9 +148,25 @@ def job_value(world, unknowns_per_rank, steps, ms):
     return world * unknowns_per_rank * steps / (ms / 1e3)
 
 
-def workload(p, scale, smoother):
+# workload -> (default degrees, oracle sample expression for the CPU legs, description)
+WORKLOADS = {
+    "sipg3x3": ("2,3,4,5,6", "W.sipg_3x3(2, scale=1, smoother={smoother!r})",
+                "sipg-3x3-[0,3]^2-jitter0.1-{a}/{b}-intervals"),
+    "cube-conforming": ("3,4,5", "W.cube_2x2x2(3, 'conforming', n=12)",
+                        "conforming-2x2x2-[0,1]^3-jitter0.05-48-intervals"),
+    "cube-sipg": ("3,4,5", "W.cube_2x2x2(3, 'sipg', n=12)", "sipg-2x2x2-[0,1]^3-jitter0.05-48-intervals"),
+}
+
+
+def workload(p, args):
     from paper_1902_01818_gb300 import workloads as W
-    return W.sipg_3x3(p, scale=scale, smoother=smoother)
+    if args.workload == "sipg3x3":
+        return W.sipg_3x3(p, scale=args.scale, smoother=args.smoother)
+    return W.cube_2x2x2(p, args.workload.split("-")[1])
+
+
+def workload_name(args):
+    return WORKLOADS[args.workload][2].format(a=64 * args.scale, b=96 * args.scale)
 
 
 # ---------------------------------------------------------------------------
@@ -154,7 +177,7 @@ import json, sys, time
 sys.path.insert(0, {root!r})
 from oracle import discretize, mg
 from paper_1902_01818_gb300 import workloads as W
-prob, opts = W.sipg_3x3({p}, scale={scale}, smoother={smoother!r})
+prob, opts = {expr}
 M = mg.Multigrid(prob, smoother=opts["smoother"], tau=opts["tau"], delta=opts["delta"])
 f = discretize.assemble_load(prob, prob["knots"], M.h["num"][-1], W.source_sinprod)
 out = []
@@ -166,46 +189,52 @@ print(json.dumps(dict(ndof=M.ndof, runs=out)))
 """
 
 
-def run_oracle(p, scale, smoother, reps):
-    """Time the oracle's PCG solve in a fresh single-threaded process."""
+def run_oracle(expr, reps):
+    """Time the oracle's PCG solve of the problem `expr` builds in a fresh single-threaded process."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
-    code = ORACLE_SNIPPET.format(root=ROOT, p=p, scale=scale, smoother=smoother, reps=reps)
+    code = ORACLE_SNIPPET.format(root=ROOT, expr=expr, reps=reps)
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if res.returncode != 0:
         raise RuntimeError("oracle run failed: " + res.stderr[-2000:])
     return json.loads(res.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(smoother):
-    """Bounded sample: the oracle on the 64/96-interval version (60k unknowns), p = 2."""
-    r = run_oracle(2, 1, smoother, 1)
+def oracle_sample(args):
+    """The bounded sample of the workload the CPU legs time: the 2D layout at 64/96 intervals,
+    p = 2 (60k unknowns); the cube at 12 intervals, p = 3 (22k unknowns)."""
+    return WORKLOADS[args.workload][1].format(smoother=args.smoother)
+
+
+def cpu_baseline(args):
+    expr = oracle_sample(args)
+    r = run_oracle(expr, 1)
     t, it, rel = r["runs"][0]
     return {"value": r["ndof"] / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"one PCG solve of the same layout at 64/96 intervals, p=2 ({r['ndof']} unknowns, "
-                      f"{it} iterations, {t:.1f} s, setup excluded; numpy/scipy, 1 thread)"}
+            "sample": f"one PCG solve of {expr} ({r['ndof']} unknowns, {it} iterations, {t:.1f} s, "
+                      f"setup excluded; numpy/scipy, 1 thread)"}
 
 
 def reference_arm(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    # each step: one oracle PCG solve of the bounded sample (60k unknowns, p = 2)
-    r = run_oracle(2, 1, args.smoother, args.warmup + args.steps)
+    # each step: one oracle PCG solve of the bounded sample
+    expr = oracle_sample(args)
+    r = run_oracle(expr, args.warmup + args.steps)
     runs = r["runs"][args.warmup:]
     times = [x[0] for x in runs]
     total = sum(times)
     value = r["ndof"] * len(runs) / total
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRIC_OF[args.workload], "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(runs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"sipg-3x3-[0,3]^2-jitter0.1-64/96-intervals-p2 (bounded sample of the "
-                                   f"{192 if args.scale == 3 else 64 * args.scale}/{96 * args.scale} workload)",
+            "config": {"workload": f"{expr}: bounded sample of the {workload_name(args)} workload",
                        "smoother": args.smoother, "l2": "inputs larger than L2 n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(runs)} oracle PCG solves, {r['ndof']} unknowns, p=2, 1 thread"},
+                             "sample": f"{len(runs)} oracle PCG solves of {expr}, {r['ndof']} unknowns, 1 thread"},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -289,19 +318,19 @@ def main():
     # the CPU baseline runs first (spawned process, before this process uses the GPU)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.smoother)
+        cpu = cpu_baseline(args)
 
     import __graft_entry__
     __graft_entry__.build()
     from paper_1902_01818_gb300 import mgiga
 
-    degrees = [int(x) for x in args.degrees.split(",")]
+    degrees = [int(x) for x in (args.degrees or WORKLOADS[args.workload][0]).split(",")]
     stream = torch.cuda.Stream()  # the timing events live on this stream
     torch.cuda.set_stream(stream)
     # one stream per degree (and precision): the independent solves of a step run concurrently,
     # one host thread each, unless --sequential
     streams = {}
-    solvers, rhs_d, u_d, rhs_h, u_h, ndofs = [], [], [], [], [], []
+    solvers, rhs_d, u_d, rhs_h, u_h, ndofs, dims = [], [], [], [], [], [], []
     t_setup = time.perf_counter()
     precisions = [args.precision] + ([] if args.no_fp64_compare or args.precision == "fp64" else ["fp64"])
     handles = {pr: [] for pr in precisions}
@@ -313,7 +342,8 @@ def main():
     # the highest priority, so its blocks are scheduled first and the others fill the gaps
     by_work = sorted(degrees, reverse=True)
     for p, c in zip(degrees, cs):
-        prob, opts = workload(p, args.scale, args.smoother)
+        prob, opts = workload(p, args)
+        dims.append(prob["dim"])
         prio = -max(0, 3 - by_work.index(p)) if args.priority == "degree" and not args.sequential else 0
         for pr in precisions:
             streams[(p, pr)] = torch.cuda.Stream(priority=prio)
@@ -331,17 +361,18 @@ def main():
         u_h.append(torch.zeros(len(f), dtype=torch.float64).pin_memory())
     solvers = handles[args.precision]
     total_dof = sum(ndofs)
+    dev_bytes = sum(s.device_bytes() for s in solvers)
     t_setup = time.perf_counter() - t_setup
     print(f"set-up (assembly, hierarchy, smoother data, upload) of {len(degrees) * len(precisions)} handles: "
           f"{t_setup:.1f} s", file=sys.stderr, flush=True)
 
     # concurrency is safe when no sweep needs the grid-wide (cooperative) kernel: the base colours
     # cover every DoF on every level (true for this layout; checked, not assumed)
-    def coop_free(s, p):
-        base = 2 * (p + 1) ** 2
+    def coop_free(s, p, d):
+        base = 2 * (p + 1) ** d
         return all(int(s.colours(l).max()) < base for l in range(1, s.levels))
 
-    concurrent = not args.sequential and all(coop_free(s, p) for s, p in zip(solvers, degrees))
+    concurrent = not args.sequential and all(coop_free(s, p, d) for s, p, d in zip(solvers, degrees, dims))
 
     def solve_one(i, s, host_path, out):
         st_ = streams[(degrees[i], s.precision)]
@@ -457,7 +488,9 @@ def main():
     names = {"band": "band_apply (FP64 band product)",
              "residual": "band_residual_f32 + cross_apply (residual inside the cycle, FP32 band)",
              "fd": {"fp32": "gemm_tiled (fast diagonalisation, FP32)",
-                    "tf32": "gather_interior_f32 + gemm_umma_tf32 (fast diagonalisation, TF32 tensor cores)",
+                    "tf32": ("gather_interior_f32 + gemm_umma_tf32 (fast diagonalisation, TF32 tensor cores)"
+                             if args.workload == "sipg3x3" else
+                             "gemm_tiled (fast diagonalisation, FP32: interiors below the tensor-core size)"),
                     "bf16": "gemm_umma (fast diagonalisation, BF16 tensor cores)"}.get(
                         args.precision, "gemm_tiled (fast diagonalisation, FP64)"),
              "gs": ("gs_fill_phase + gs_patch_staged (one Gauss-Seidel sweep, FP32)" if f32 else
@@ -475,7 +508,7 @@ def main():
         if st in ("band", "fd") and not (st == "fd" and f32):
             rec = {"bound": "alu", "achieved": fl / (t_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
-        elif st == "fd" and args.precision in ("tf32", "bf16"):
+        elif st == "fd" and args.precision in ("tf32", "bf16") and args.workload == "sipg3x3":
             bf16, src = bf16_peak_tflops()
             ratio = 0.5 if args.precision == "tf32" else 1.0  # nominal dense TF32 / BF16 = 1.1 / 2.25
             rec = {"bound": "tensor", "achieved": fl / (t_ms / 1e3) / 1e12, "peak": bf16 * ratio,
@@ -499,12 +532,12 @@ def main():
     roof["stages"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                       for k, v in stages.items()}
 
-    line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC_OF[args.workload], "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": {"fp32": "f32+f64", "tf32": "tf32+f32+f64", "bf16": "bf16+f32+f64"}.get(args.precision, "f64"),
             "data": "synthetic",
-            "config": {"workload": f"sipg-3x3-[0,3]^2-jitter0.1-{64 * args.scale}/{96 * args.scale}-intervals",
+            "config": {"workload": workload_name(args),
                        "degrees": degrees, "unknowns": ndofs, "smoother": args.smoother, "outer": "pcg",
                        "precision": {"fp32": "fp32 smoothers, fp64 CG/coarse",
                                      "tf32": "tf32 contractions on large levels, fp32 smoothers, fp64 CG/coarse",
@@ -513,7 +546,7 @@ def main():
                        "tol": 1e-8, "iterations": iters, "final_relres": rels,
                        "step_ms_p50": float(np.percentile(step_ms, 50)),
                        "step_ms_p99": float(np.percentile(step_ms, 99)),
-                       "l2": "inputs larger than L2 (0.9-3.7 GB operators per step)",
+                       "l2": f"inputs larger than L2 ({dev_bytes / 1e9:.1f} GB of device data per step)",
                        "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1),
                        "solves": ("concurrent: one CUDA stream and host thread per degree"
                                   + (", stream priority by degree" if args.priority == "degree" else "")

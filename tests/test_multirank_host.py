@@ -59,16 +59,16 @@ def test_single_rank_needs_no_process_group():
     assert bench.job_value(1, 2_000_000, 5, 100.0) == pytest.approx(1e8)
 
 
-def _reference(monkeypatch, rank, world):
+def _reference(monkeypatch, rank, world, extra=()):
     calls = []
 
-    def fake_oracle(p, scale, smoother, reps):
-        calls.append((p, scale, reps))
+    def fake_oracle(expr, reps):
+        calls.append((expr, reps))
         return {"ndof": 59280, "runs": [[0.5 + 0.1 * i, 14, 5e-9] for i in range(reps)]}
 
     monkeypatch.setattr(bench, "run_oracle", fake_oracle)
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "3", "--warmup", "1",
-                                      "--gpus", str(world)])
+                                      "--gpus", str(world), *extra])
     monkeypatch.setenv("RANK", str(rank))
     monkeypatch.setenv("WORLD_SIZE", str(world))
     bench.reference_arm(bench.parse())
@@ -78,7 +78,8 @@ def _reference(monkeypatch, rank, world):
 def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     assert _reference(monkeypatch, 1, 2) == [] and capsys.readouterr().out == ""
     calls = _reference(monkeypatch, 0, 2)
-    assert calls == [(2, 1, 4)]  # warm-up + timed solves of the bounded sample
+    # warm-up + timed solves of the bounded sample: the 2D layout at 64/96 intervals, p = 2
+    assert calls == [("W.sipg_3x3(2, scale=1, smoother='hybrid')", 4)]
     line = json.loads(capsys.readouterr().out.strip())
     times = [0.6, 0.7, 0.8]  # the three timed runs after the warm-up one
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["steps"] == 3
@@ -98,3 +99,16 @@ def test_clock_record_reasons_and_median():
     assert s["sm_mhz"] == 2050.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
     assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
     assert bench.ClockSampler(0).summary()["reasons"] == ["unavailable"]
+
+
+def test_reference_arm_of_the_cube_times_a_cube_sample(monkeypatch, capsys):
+    calls = _reference(monkeypatch, 0, 1, ("--workload", "cube-sipg"))
+    assert calls == [("W.cube_2x2x2(3, 'sipg', n=12)", 4)]
+    line = json.loads(capsys.readouterr().out.strip())
+    assert "2x2x2" in line["metric"] and "cube_2x2x2" in line["config"]["workload"]
+
+
+def test_workload_defaults():
+    for name, (degrees, expr, desc) in bench.WORKLOADS.items():
+        assert name in bench.METRIC_OF and degrees and expr.startswith("W.")
+    assert bench.METRIC_OF["sipg3x3"] == bench.METRIC

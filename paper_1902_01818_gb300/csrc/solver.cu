@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/mgiga.h"
+#include "host_problem.hpp"
 #include "device.cuh"
 #include "host.hpp"
 #include "kernels.h"
@@ -1282,65 +1283,6 @@ struct LaunchScope {
   ~LaunchScope() { h->launches += launch_counter() - c0; }
 };
 
-// ---------------------------------------------------------------------------
-// problem import and validation
-// ---------------------------------------------------------------------------
-void import_problem(const mgiga_problem* P, Problem& pr) {
-  if (!P) throw SetupError(MGIGA_EINVAL, "problem is NULL");
-  if (P->dim != 2 && P->dim != 3) throw SetupError(MGIGA_EINVAL, "dim must be 2 or 3");
-  if (P->num_patches < 1) throw SetupError(MGIGA_EINVAL, "num_patches must be >= 1");
-  if (P->degree < 1 || P->degree > 8) throw SetupError(MGIGA_EINVAL, "degree must be in 1..8");
-  if (P->geo_degree < 1 || P->geo_degree > 8) throw SetupError(MGIGA_EINVAL, "geo_degree must be in 1..8");
-  if (!P->num_knots || !P->knots || !P->geo_num_knots || !P->geo_knots || !P->geo_ctrl)
-    throw SetupError(MGIGA_EINVAL, "NULL array in problem");
-  if (P->num_interfaces > 0 && !P->interfaces) throw SetupError(MGIGA_EINVAL, "interfaces is NULL");
-  if (P->coupling != MGIGA_CONFORMING && P->coupling != MGIGA_SIPG) throw SetupError(MGIGA_EINVAL, "bad coupling");
-  if (P->coupling == MGIGA_SIPG && !(P->sipg_penalty > 0.0)) throw SetupError(MGIGA_EINVAL, "sipg_penalty must be > 0");
-  pr.d = P->dim;
-  pr.K = P->num_patches;
-  pr.p = P->degree;
-  pr.coupling = P->coupling;
-  pr.penalty = P->sipg_penalty;
-  pr.knots.assign(pr.K, {});
-  pr.geo.assign(pr.K, Geometry{});
-  size_t kk = 0, gk = 0, gc = 0;
-  for (int k = 0; k < pr.K; ++k) {
-    int64_t ncp = 1;
-    for (int a = 0; a < pr.d; ++a) {
-      const int n = P->num_knots[k * pr.d + a];
-      if (n < 2 * pr.p + 2) throw SetupError(MGIGA_EINVAL, "knot vector too short");
-      Vec t(P->knots + kk, P->knots + kk + n);
-      kk += n;
-      for (int i = 0; i + 1 < n; ++i)
-        if (!(t[i] <= t[i + 1])) throw SetupError(MGIGA_EINVAL, "knot vector not nondecreasing");
-      for (int i = 0; i <= pr.p; ++i)
-        if (t[i] != 0.0 || t[n - 1 - i] != 1.0)
-          throw SetupError(MGIGA_EINVAL, "knot vectors must be open on [0, 1] (end multiplicity p+1)");
-      for (int i = pr.p + 1; i + 1 < n - pr.p - 1; ++i)
-        if (t[i] == t[i + 1]) throw SetupError(MGIGA_EINVAL, "interior knots must be simple (maximal smoothness)");
-      pr.knots[k][a] = t;
-      const int gn = P->geo_num_knots[k * pr.d + a];
-      if (gn < 2 * P->geo_degree + 2) throw SetupError(MGIGA_EINVAL, "geometry knot vector too short");
-      pr.geo[k].knots[a] = Vec(P->geo_knots + gk, P->geo_knots + gk + gn);
-      gk += gn;
-      pr.geo[k].ncp[a] = gn - P->geo_degree - 1;
-      ncp *= pr.geo[k].ncp[a];
-    }
-    pr.geo[k].q = P->geo_degree;
-    pr.geo[k].ctrl = Vec(P->geo_ctrl + gc, P->geo_ctrl + gc + ncp * pr.d);
-    gc += ncp * pr.d;
-  }
-  for (int i = 0; i < P->num_interfaces; ++i) {
-    const mgiga_interface& f = P->interfaces[i];
-    if (f.patch_a < 0 || f.patch_a >= pr.K || f.patch_b < 0 || f.patch_b >= pr.K || f.patch_a == f.patch_b)
-      throw SetupError(MGIGA_EINVAL, "bad interface patch");
-    if (f.side_a < 0 || f.side_a >= 2 * pr.d || f.side_b < 0 || f.side_b >= 2 * pr.d)
-      throw SetupError(MGIGA_EINVAL, "bad interface side");
-    if (f.orient > (pr.d == 3 ? 7u : 1u)) throw SetupError(MGIGA_EINVAL, "bad interface orientation");
-    pr.ifaces.push_back({f.patch_a, f.side_a, f.patch_b, f.side_b, f.orient});
-  }
-}
-
 mgiga_status fail(mgiga_handle* h, int st, const std::string& msg) {
   if (h) h->err = msg;
   return (mgiga_status)st;
@@ -1412,14 +1354,7 @@ mgiga_status mgiga_create(const mgiga_problem* problem, const mgiga_options* opt
     h->stream = static_cast<cudaStream_t>(o.stream);
     const int lv = o.levels > 0 ? o.levels : auto_levels(h->pr);
     h->levels = lv;
-    h->L.assign(lv, Level{});
-    h->L[lv - 1].knots = h->pr.knots;
-    for (int l = lv - 1; l > 0; --l) {
-      h->L[l - 1].knots.resize(h->pr.K);
-      for (int k = 0; k < h->pr.K; ++k)
-        for (int a = 0; a < h->pr.d; ++a) h->L[l - 1].knots[k][a] = coarsen_knots(h->L[l].knots[k][a], h->pr.p);
-    }
-    for (int l = 0; l < lv; ++l) build_topology(h->pr, h->L[l]);
+    init_levels(h->pr, lv, h->L);
     // integer set-up of the smoothers (host only): pieces and colours
     h->colours.assign(lv, {});
     h->pieces.assign(lv, {});
@@ -1456,16 +1391,9 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       t_last = now;
     };
     const int lv = h->levels;
-    Level& F = h->L[lv - 1];
-    assemble_fine(h->pr, F, h->pr.knots);
-    apply_dirichlet(F);
+    assemble_finest(h->pr, h->L);
     tick("assembly", lv - 1);
-    h->T.assign(lv, Transfer{});
-    for (int l = lv - 1; l > 0; --l) {
-      h->T[l] = build_transfer(h->L[l - 1], h->L[l]);
-      galerkin(h->L[l], h->T[l], h->L[l - 1]);
-      apply_dirichlet(h->L[l - 1]);
-    }
+    galerkin_hierarchy(h->L, h->T);
     tick("galerkin", 0);
     // device: work runs on the caller's stream, or on a non-blocking stream
     // of the handle (the legacy default stream cannot be captured into

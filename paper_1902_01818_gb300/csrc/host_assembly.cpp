@@ -558,14 +558,20 @@ void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec
 }
 
 void apply_dirichlet(Level& L) {
-  for (int k = 0; k < L.K; ++k)
-    for (int64_t r = L.off[k]; r < L.off[k + 1]; ++r)
-      for (int o = 0; o < L.nb; ++o) {
-        double& v = L.band[(size_t)o * L.nloc + r];
-        if (v == 0.0) continue;
-        const int64_t c = r + L.band_offset(k, o);
-        if (L.dirichlet[r] || c < L.off[k] || c >= L.off[k + 1] || L.dirichlet[c]) v = 0.0;
+  // offsets in parallel, the rows of one offset's column contiguous
+  for (int k = 0; k < L.K; ++k) {
+    const int64_t r0 = L.off[k], r1 = L.off[k + 1];
+#pragma omp parallel for schedule(static)
+    for (int o = 0; o < L.nb; ++o) {
+      const int64_t bo = L.band_offset(k, o);
+      double* col = &L.band[(size_t)o * L.nloc];
+      for (int64_t r = r0; r < r1; ++r) {
+        if (col[r] == 0.0) continue;
+        const int64_t c = r + bo;
+        if (L.dirichlet[r] || c < r0 || c >= r1 || L.dirichlet[c]) col[r] = 0.0;
       }
+    }
+  }
   // cross blocks: drop Dirichlet rows / columns
   std::vector<int64_t> rows, cols;
   std::vector<int> ptr(1, 0);

@@ -69,33 +69,37 @@ static void coarsen_band_dir(int d, int p, const std::array<int, 3>& Nin, const 
     for (int I = 0; I < nc; ++I)
       if (P[(size_t)i * nc + I] != 0.0) ch[I].push_back({i, P[(size_t)i * nc + I]});
   int wpow[3] = {1, W, W * W};
-#pragma omp parallel for schedule(static)
-  for (int64_t r = 0; r < rows_out; ++r) {
-    int idx[3];
-    int64_t rem = r;
-    for (int a = 0; a < 3; ++a) { idx[a] = (int)(rem % Nout[a]); rem /= Nout[a]; }
-    const int I = idx[dir];
-    for (int o = 0; o < nb; ++o) {
-      const int O = (o / wpow[dir]) % W - p;
-      const int J = I + O;
-      if (J < 0 || J >= nc) continue;
-      double s = 0.0;
-      for (const auto& c : ch[I]) {
-        const int i = c.first;
-        int fidx[3] = {idx[0], idx[1], idx[2]};
-        fidx[dir] = i;
-        const int64_t frow = fidx[0] + (int64_t)Nin[0] * (fidx[1] + (int64_t)Nin[1] * fidx[2]);
-        for (int od = -p; od <= p; ++od) {
-          const int j = i + od;
-          if (j < 0 || j >= nf) continue;
-          const double pj = P[(size_t)j * nc + J];
-          if (pj == 0.0) continue;
-          const int ofine = o + (od - O) * wpow[dir];
-          s += c.second * Bin[(size_t)ofine * rows_in + frow] * pj;
+  // offsets in parallel, rows innermost: the band is stored offset-major, so
+  // consecutive rows read and write consecutive words of one offset's column
+  const int64_t fstride[3] = {1, Nin[0], (int64_t)Nin[0] * Nin[1]};
+#pragma omp parallel for schedule(dynamic)
+  for (int o = 0; o < nb; ++o) {
+    const int O = (o / wpow[dir]) % W - p;
+    double* out = &Bout[(size_t)o * rows_out];
+    int64_t r = 0;
+    for (int i2 = 0; i2 < Nout[2]; ++i2)
+      for (int i1 = 0; i1 < Nout[1]; ++i1)
+        for (int i0 = 0; i0 < Nout[0]; ++i0, ++r) {
+          const int idx[3] = {i0, i1, i2};
+          const int I = idx[dir];
+          const int J = I + O;
+          if (J < 0 || J >= nc) continue;
+          // fine row of (i, rest) without the direction's own index
+          const int64_t fbase = idx[0] + fstride[1] * idx[1] + fstride[2] * idx[2] - fstride[dir] * I;
+          double s = 0.0;
+          for (const auto& c : ch[I]) {
+            const int i = c.first;
+            const int64_t frow = fbase + fstride[dir] * i;
+            // the nonzeros P[j, J] are the children j of J (ascending, as the band offsets od = j - i)
+            for (const auto& cj : ch[J]) {
+              const int od = cj.first - i;
+              if (od < -p || od > p) continue;
+              const int ofine = o + (od - O) * wpow[dir];
+              s += c.second * Bin[(size_t)ofine * rows_in + frow] * cj.second;
+            }
+          }
+          out[r] = s;
         }
-      }
-      Bout[(size_t)o * rows_out + r] = s;
-    }
   }
 }
 

@@ -268,6 +268,50 @@ static void patch_stiffness(const Problem& pr, Level& L, int k) {
               return deriv ? dq[dir].D[idx] : dq[dir].B[idx];
             };
             std::fill(Ke.begin(), Ke.end(), 0.0);
+            if (d == 2) {
+              // Ke(l0 + P1 l1, m0 + P1 m1) = sum_q0 sum_ab X0_a(l0) X0_b(m0) U_ab(q0, l1, m1),
+              // U_ab(q0, l1, m1) = sum_q1 C_ab(q0, q1) X1_a(l1) X1_b(m1), X_a the derivative along
+              // direction a, else the value; C is symmetric, so only blocks l1 <= m1 are summed and
+              // their transposes copied
+              const double* V0 = &dq[0].B[(size_t)e[0] * nq * P1];  // [q][l]
+              const double* D0 = &dq[0].D[(size_t)e[0] * nq * P1];
+              const double* V1 = &dq[1].B[(size_t)e[1] * nq * P1];
+              const double* D1 = &dq[1].D[(size_t)e[1] * nq * P1];
+              double blk[16 * 16], h0[16], h1[16];
+              for (int l1 = 0; l1 < P1; ++l1)
+                for (int m1 = l1; m1 < P1; ++m1) {
+                  for (int x = 0; x < P1 * P1; ++x) blk[x] = 0.0;
+                  for (int q0 = 0; q0 < nq; ++q0) {
+                    double u00 = 0.0, u01 = 0.0, u10 = 0.0, u11 = 0.0;
+                    for (int q1 = 0; q1 < nq; ++q1) {
+                      const double* c = &C[(size_t)(q0 + nq * q1) * 9];
+                      const double va = V1[q1 * P1 + l1], da = D1[q1 * P1 + l1];
+                      const double vb = V1[q1 * P1 + m1], db = D1[q1 * P1 + m1];
+                      u00 += c[0] * va * vb;
+                      u01 += c[1] * va * db;
+                      u10 += c[3] * da * vb;
+                      u11 += c[4] * da * db;
+                    }
+                    const double* g0 = &D0[q0 * P1];  // a = 0: derivative along xi_0
+                    const double* g1 = &V0[q0 * P1];
+                    for (int m0 = 0; m0 < P1; ++m0) {
+                      h0[m0] = u00 * g0[m0] + u01 * g1[m0];
+                      h1[m0] = u10 * g0[m0] + u11 * g1[m0];
+                    }
+                    for (int l0 = 0; l0 < P1; ++l0) {
+                      const double a0 = g0[l0], a1 = g1[l0];
+                      double* row = &blk[l0 * P1];
+                      for (int m0 = 0; m0 < P1; ++m0) row[m0] += a0 * h0[m0] + a1 * h1[m0];
+                    }
+                  }
+                  for (int l0 = 0; l0 < P1; ++l0)
+                    for (int m0 = (l1 == m1 ? l0 : 0); m0 < P1; ++m0) {  // a diagonal block: its upper half
+                      const double v = blk[l0 * P1 + m0];
+                      Ke[(size_t)(l0 + P1 * l1) * L2 + (m0 + P1 * m1)] = v;
+                      Ke[(size_t)(m0 + P1 * m1) * L2 + (l0 + P1 * l1)] = v;
+                    }
+                }
+            } else
             for (int a = 0; a < d; ++a)
               for (int b = 0; b < d; ++b) {
                 // contract q0

@@ -2,6 +2,7 @@
 // algebra for the set-up phase.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <limits>
 
 #include "host.hpp"
@@ -242,16 +243,65 @@ static inline double dot8(const double* a, const double* b, int n) {
   return r;
 }
 
+// Register tile of dot products: out[r][c] = sum_{k < n} a_r[k] b_c[k] for two
+// rows a_r and four rows b_c, each entry as two-lane partial sums combined in a
+// fixed order (GCC vector extension: 2 x f64 lanes on x86 and Arm alike).  Each
+// loaded pair of values serves four (a) or two (b) products.
+typedef double v2d __attribute__((vector_size(16)));
+
+static inline v2d ld2(const double* p) {
+  v2d v;
+  std::memcpy(&v, p, sizeof(v));
+  return v;
+}
+
+static inline void dot_2x4(const double* a0, const double* a1, const double* const b[4], int n, double out[2][4]) {
+  v2d s0[4] = {}, s1[4] = {};
+  int k = 0;
+  for (; k + 2 <= n; k += 2) {
+    const v2d x0 = ld2(a0 + k), x1 = ld2(a1 + k);
+    const v2d y0 = ld2(b[0] + k), y1 = ld2(b[1] + k), y2 = ld2(b[2] + k), y3 = ld2(b[3] + k);
+    s0[0] += x0 * y0; s0[1] += x0 * y1; s0[2] += x0 * y2; s0[3] += x0 * y3;
+    s1[0] += x1 * y0; s1[1] += x1 * y1; s1[2] += x1 * y2; s1[3] += x1 * y3;
+  }
+  for (int c = 0; c < 4; ++c) {
+    double t0 = s0[c][0] + s0[c][1], t1 = s1[c][0] + s1[c][1];
+    if (k < n) {
+      t0 += a0[k] * b[c][k];
+      t1 += a1[k] * b[c][k];
+    }
+    out[0][c] = t0;
+    out[1][c] = t1;
+  }
+}
+
 static bool cholesky(Vec& A, int n, bool par = false) {
   bool ok = true;
   for (int jb = 0; jb < n && ok; jb += kChol) {
     const int je = std::min(n, jb + kChol);
     if (jb > 0) {
+      // trailing update of the panel columns [jb, je): rows in pairs, columns in fours
+      const int npair = (n - jb + 1) / 2;
 #pragma omp parallel for schedule(static) if (par && n - jb > 128)
-      for (int i = jb; i < n; ++i) {
+      for (int ip = 0; ip < npair; ++ip) {
+        const int i = jb + 2 * ip;
         double* ri = &A[(size_t)i * n];
-        const int jmax = std::min(je, i + 1);
-        for (int j = jb; j < jmax; ++j) ri[j] -= dot8(ri, &A[(size_t)j * n], jb);
+        double* ri1 = i + 1 < n ? &A[(size_t)(i + 1) * n] : nullptr;
+        int j = jb;
+        if (ri1)
+          for (; j + 4 <= std::min(je, i + 1); j += 4) {  // every column of the tile <= i
+            const double* b[4] = {&A[(size_t)j * n], &A[(size_t)(j + 1) * n], &A[(size_t)(j + 2) * n],
+                                  &A[(size_t)(j + 3) * n]};
+            double d[2][4];
+            dot_2x4(ri, ri1, b, jb, d);
+            for (int c = 0; c < 4; ++c) {
+              ri[j + c] -= d[0][c];
+              ri1[j + c] -= d[1][c];
+            }
+          }
+        for (int jj = j; jj < std::min(je, i + 1); ++jj) ri[jj] -= dot8(ri, &A[(size_t)jj * n], jb);
+        if (ri1)
+          for (int jj = j; jj < std::min(je, i + 2); ++jj) ri1[jj] -= dot8(ri1, &A[(size_t)jj * n], jb);
       }
     }
     for (int j = jb; j < je; ++j) {
@@ -273,7 +323,10 @@ static bool cholesky(Vec& A, int n, bool par = false) {
 // Wt = (L^{-1})^T for the lower-triangular L (row-major): row c of Wt is
 // column c of L^{-1}, by forward substitution.  Columns are solved kInvCols at
 // a time so that each row of L is read once per group (in parallel over
-// groups when `par`).
+// groups when `par`); within a group four columns and two rows at a time (the
+// entries of Wt before a column's diagonal are zero, so the four columns share
+// the group's index range; the second row adds its term on the first after
+// that row is solved).
 constexpr int kInvCols = 64;
 
 static Vec lower_inverse_t(const Vec& L, int n, bool par = false) {
@@ -282,11 +335,39 @@ static Vec lower_inverse_t(const Vec& L, int n, bool par = false) {
 #pragma omp parallel for schedule(dynamic) if (par && n > 256)
   for (int g = 0; g < ngroups; ++g) {
     const int c0 = g * kInvCols, c1 = std::min(n, c0 + kInvCols);
-    for (int i = c0; i < n; ++i) {
+    int c = c0;
+    for (; c + 4 <= c1; c += 4) {
+      const double* b[4] = {&Wt[(size_t)c * n] + c, &Wt[(size_t)(c + 1) * n] + c, &Wt[(size_t)(c + 2) * n] + c,
+                            &Wt[(size_t)(c + 3) * n] + c};
+      double* w[4] = {&Wt[(size_t)c * n], &Wt[(size_t)(c + 1) * n], &Wt[(size_t)(c + 2) * n],
+                      &Wt[(size_t)(c + 3) * n]};
+      int i = c;
+      for (; i + 2 <= n; i += 2) {
+        const double* li = &L[(size_t)i * n];
+        const double* li1 = &L[(size_t)(i + 1) * n];
+        double d[2][4];
+        dot_2x4(li + c, li1 + c, b, i - c, d);
+        for (int q = 0; q < 4; ++q) {
+          const int cq = c + q;
+          const double wi = cq <= i ? ((i == cq ? 1.0 : 0.0) - d[0][q]) / li[i] : 0.0;
+          w[q][i] = wi;
+          if (cq <= i + 1) w[q][i + 1] = ((i + 1 == cq ? 1.0 : 0.0) - (d[1][q] + li1[i] * wi)) / li1[i + 1];
+        }
+      }
+      for (; i < n; ++i) {
+        const double* li = &L[(size_t)i * n];
+        for (int q = 0; q < 4; ++q) {
+          const int cq = c + q;
+          if (cq > i) continue;
+          w[q][i] = ((i == cq ? 1.0 : 0.0) - dot8(li + c, w[q] + c, i - c)) / li[i];
+        }
+      }
+    }
+    for (int i = c; i < n; ++i) {  // the group's last columns one at a time
       const double* li = &L[(size_t)i * n];
-      for (int c = c0; c < std::min(c1, i + 1); ++c) {
-        double* w = &Wt[(size_t)c * n];
-        w[i] = ((i == c ? 1.0 : 0.0) - dot8(li + c, w + c, i - c)) / li[i];
+      for (int cc = c; cc < std::min(c1, i + 1); ++cc) {
+        double* w = &Wt[(size_t)cc * n];
+        w[i] = ((i == cc ? 1.0 : 0.0) - dot8(li + cc, w + cc, i - cc)) / li[i];
       }
     }
   }
@@ -301,19 +382,37 @@ Vec spd_inverse(const Vec& A, int n, bool par) {
   if (!cholesky(L, n, par)) throw SetupError(4, "Cholesky factorisation broke down (matrix not SPD)");
   const Vec Wt = lower_inverse_t(L, n, par);
   // Z[i][j] = sum_{k >= max(i, j)} Wt[i][k] Wt[j][k], j <= i; a block of kInvCols rows i stays
-  // in cache while every row j is read once per block
+  // in cache while every row j is read once per block; rows in pairs and columns in fours where
+  // the tile lies below the diagonal (Wt[i][k] = 0 for k < i, so the pair shares the range k >= i)
   Vec Z((size_t)n * n, 0.0);
   const int nblk = (n + kInvCols - 1) / kInvCols;
 #pragma omp parallel for schedule(dynamic) if (par && n > 256)
-  for (int b = 0; b < nblk; ++b) {
-    const int i0 = b * kInvCols, i1 = std::min(n, i0 + kInvCols);
-    for (int j = 0; j < i1; ++j) {
-      const double* wj = &Wt[(size_t)j * n];
-      for (int i = std::max(i0, j); i < i1; ++i) {
-        const double s = dot8(&Wt[(size_t)i * n] + i, wj + i, n - i);
-        Z[(size_t)i * n + j] = s;
-        Z[(size_t)j * n + i] = s;
-      }
+  for (int bk = 0; bk < nblk; ++bk) {
+    const int i0 = bk * kInvCols, i1 = std::min(n, i0 + kInvCols);
+    for (int i = i0; i < i1; i += 2) {
+      const bool two = i + 1 < i1;
+      const double* wi = &Wt[(size_t)i * n];
+      const double* wi1 = two ? &Wt[(size_t)(i + 1) * n] : nullptr;
+      int j = 0;
+      if (two)
+        for (; j + 4 <= i + 1; j += 4) {  // columns j..j+3 <= i
+          const double* b[4] = {&Wt[(size_t)j * n] + i, &Wt[(size_t)(j + 1) * n] + i,
+                                &Wt[(size_t)(j + 2) * n] + i, &Wt[(size_t)(j + 3) * n] + i};
+          double d[2][4];
+          dot_2x4(wi + i, wi1 + i, b, n - i, d);
+          for (int q = 0; q < 4; ++q) {
+            Z[(size_t)i * n + j + q] = d[0][q];
+            Z[(size_t)(j + q) * n + i] = d[0][q];
+            Z[(size_t)(i + 1) * n + j + q] = d[1][q];
+            Z[(size_t)(j + q) * n + i + 1] = d[1][q];
+          }
+        }
+      for (int r = i; r < (two ? i + 2 : i + 1); ++r)
+        for (int jj = j; jj <= r; ++jj) {
+          const double v = dot8(&Wt[(size_t)r * n] + r, &Wt[(size_t)jj * n] + r, n - r);
+          Z[(size_t)r * n + jj] = v;
+          Z[(size_t)jj * n + r] = v;
+        }
     }
   }
   return Z;

@@ -222,20 +222,30 @@ static void patch_stiffness(const Problem& pr, Level& L, int k) {
   for (int a = 0; a < d; ++a) { dq[a] = dir_quad(L.knots[k][a], p); ne[a] = (int)dq[a].span.size(); }
   const int slow = d - 1;
   const int Q = d == 2 ? nq * nq : nq * nq * nq;
+  // the patch's band accumulated row-major (a row's offsets contiguous, so an
+  // element's entries of one row share cache lines), stored offset-major at the end
+  const int nb = L.nb;
+  const int64_t off = L.off[k], rows = L.off[k + 1] - L.off[k];
+  Vec Bt((size_t)rows * nb, 0.0);
   // element slabs along the slowest direction touch disjoint band rows when
   // they are p+1 apart: p+1 parallel phases
-  for (int phase = 0; phase < P1; ++phase) {
+  // (in 3D the rows of elements along xi_0 are coloured by both outer indices
+  // modulo p+1: (p+1)^2 phases of many independent rows, enough for every core)
+  const int nphase = d == 3 ? P1 * P1 : P1;
+  for (int phase = 0; phase < nphase; ++phase) {
+    const int r_slow = d == 3 ? phase / P1 : phase, r_mid = d == 3 ? phase % P1 : 0;
+    const int n_slow = (ne[slow] - r_slow + P1 - 1) / P1;
+    const int n_mid = d == 3 ? (ne[1] - r_mid + P1 - 1) / P1 : 1;
 #pragma omp parallel
     {
-      std::vector<double> C((size_t)Q * 9), T1, T2, Ke;
+      std::vector<double> C((size_t)Q * 9), T2, Ke;
       const int L2 = P1 * P1;
-      T1.resize((size_t)nq * nq * L2 * 9);
-      T2.resize((size_t)nq * L2 * L2 * 9);
+      T2.resize((size_t)9 * nq * nq * L2);  // 3D: the q2-contracted factors
       Ke.resize((size_t)(d == 2 ? L2 * L2 : L2 * L2 * L2));
 #pragma omp for schedule(dynamic)
-      for (int es = phase; es < ne[slow]; es += P1) {
-        const int n_mid = d == 3 ? ne[1] : 1;
-        for (int e1m = 0; e1m < n_mid; ++e1m)
+      for (int task = 0; task < n_slow * n_mid; ++task) {
+        const int es = r_slow + P1 * (task / n_mid);
+        const int e1m = r_mid + P1 * (task % n_mid);
           for (int e0 = 0; e0 < ne[0]; ++e0) {
             int e[3];
             e[0] = e0;
@@ -262,11 +272,6 @@ static void patch_stiffness(const Problem& pr, Level& L, int k) {
                       C[(size_t)qq * 9 + a * 3 + b] = s * v;
                     }
                 }
-            // per-direction factors F_a(l, m, q) = X_a(l, q) X_b(m, q)
-            auto X = [&](int dir, int deriv, int l, int q) {
-              const size_t idx = ((size_t)e[dir] * nq + q) * P1 + l;
-              return deriv ? dq[dir].D[idx] : dq[dir].B[idx];
-            };
             std::fill(Ke.begin(), Ke.end(), 0.0);
             if (d == 2) {
               // Ke(l0 + P1 l1, m0 + P1 m1) = sum_q0 sum_ab X0_a(l0) X0_b(m0) U_ab(q0, l1, m1),
@@ -311,60 +316,74 @@ static void patch_stiffness(const Problem& pr, Level& L, int k) {
                       Ke[(size_t)(m0 + P1 * m1) * L2 + (l0 + P1 * l1)] = v;
                     }
                 }
-            } else
-            for (int a = 0; a < d; ++a)
-              for (int b = 0; b < d; ++b) {
-                // contract q0
-                for (int q2 = 0; q2 < (d == 3 ? nq : 1); ++q2)
-                  for (int q1 = 0; q1 < nq; ++q1)
-                    for (int l0 = 0; l0 < P1; ++l0)
-                      for (int m0 = 0; m0 < P1; ++m0) {
-                        double s = 0.0;
-                        for (int q0 = 0; q0 < nq; ++q0)
-                          s += C[(size_t)(q0 + nq * (q1 + nq * q2)) * 9 + a * 3 + b] *
-                               X(0, a == 0, l0, q0) * X(0, b == 0, m0, q0);
-                        T1[((size_t)(q2 * nq + q1) * P1 + l0) * P1 + m0] = s;
-                      }
-                if (d == 2) {
-                  for (int l1 = 0; l1 < P1; ++l1)
-                    for (int m1 = 0; m1 < P1; ++m1)
-                      for (int q1 = 0; q1 < nq; ++q1) {
-                        const double f = X(1, a == 1, l1, q1) * X(1, b == 1, m1, q1);
-                        for (int l0 = 0; l0 < P1; ++l0)
-                          for (int m0 = 0; m0 < P1; ++m0)
-                            Ke[(size_t)(l0 + P1 * l1) * L2 + (m0 + P1 * m1)] +=
-                                f * T1[((size_t)q1 * P1 + l0) * P1 + m0];
-                      }
-                } else {
-                  // contract q1
-                  for (int q2 = 0; q2 < nq; ++q2)
-                    for (int l1 = 0; l1 < P1; ++l1)
-                      for (int m1 = 0; m1 < P1; ++m1) {
-                        double* dst = &T2[(((size_t)q2 * P1 + l1) * P1 + m1) * L2];
-                        for (int x = 0; x < L2; ++x) dst[x] = 0.0;
-                        for (int q1 = 0; q1 < nq; ++q1) {
-                          const double f = X(1, a == 1, l1, q1) * X(1, b == 1, m1, q1);
-                          const double* src = &T1[((size_t)(q2 * nq + q1) * P1) * P1];
-                          for (int x = 0; x < L2; ++x) dst[x] += f * src[x];
-                        }
-                      }
-                  // contract q2
-                  const int L3 = L2 * P1;
-                  for (int l2 = 0; l2 < P1; ++l2)
-                    for (int m2 = 0; m2 < P1; ++m2)
-                      for (int q2 = 0; q2 < nq; ++q2) {
-                        const double f = X(2, a == 2, l2, q2) * X(2, b == 2, m2, q2);
-                        for (int l1 = 0; l1 < P1; ++l1)
-                          for (int m1 = 0; m1 < P1; ++m1) {
-                            const double* src = &T2[(((size_t)q2 * P1 + l1) * P1 + m1) * L2];
-                            for (int l0 = 0; l0 < P1; ++l0)
-                              for (int m0 = 0; m0 < P1; ++m0)
-                                Ke[(size_t)(l0 + P1 * (l1 + P1 * l2)) * L3 + (m0 + P1 * (m1 + P1 * m2))] +=
-                                    f * src[l0 * P1 + m0];
-                          }
-                      }
-                }
+            } else {
+              // Ke(l, m) = sum_q sum_ab C_ab(q) prod_dir X_dir,a(l_dir) X_dir,b(m_dir), X_dir,a the
+              // derivative if a == dir, else the value.  Contract q2 (U), then per pair of row/column
+              // indices (l1, l2), (m1, m2) with l1 + P1 l2 <= m1 + P1 m2 contract q1 (V); along xi_0
+              // only "a == 0 or not" matters, so the nine pairs merge into a 2x2 form per q0 point
+              const int L3 = L2 * P1;
+              const double* Vd[3];
+              const double* Dd[3];
+              for (int dir = 0; dir < 3; ++dir) {
+                Vd[dir] = &dq[dir].B[(size_t)e[dir] * nq * P1];  // [q][l]
+                Dd[dir] = &dq[dir].D[(size_t)e[dir] * nq * P1];
               }
+              // U[((ab * nq + q0) * nq + q1) * L2 + l2 * P1 + m2] = sum_q2 C_ab X2_a(l2) X2_b(m2)
+              for (int ab = 0; ab < 9; ++ab) {
+                const int aa = ab / 3, bb = ab % 3;
+                const double* xa = aa == 2 ? Dd[2] : Vd[2];
+                const double* xb = bb == 2 ? Dd[2] : Vd[2];
+                for (int q0 = 0; q0 < nq; ++q0)
+                  for (int q1 = 0; q1 < nq; ++q1) {
+                    double* u = &T2[(((size_t)ab * nq + q0) * nq + q1) * L2];
+                    for (int x = 0; x < L2; ++x) u[x] = 0.0;
+                    for (int q2 = 0; q2 < nq; ++q2) {
+                      const double c = C[(size_t)(q0 + nq * (q1 + nq * q2)) * 9 + aa * 3 + bb];
+                      for (int l2 = 0; l2 < P1; ++l2) {
+                        const double cl = c * xa[q2 * P1 + l2];
+                        for (int m2 = 0; m2 < P1; ++m2) u[l2 * P1 + m2] += cl * xb[q2 * P1 + m2];
+                      }
+                    }
+                  }
+              }
+              double blk[16 * 16], h0[16], h1[16];
+              for (int L12 = 0; L12 < L2; ++L12)
+                for (int M12 = L12; M12 < L2; ++M12) {
+                  const int l1 = L12 % P1, l2 = L12 / P1, m1 = M12 % P1, m2 = M12 / P1;
+                  for (int x = 0; x < P1 * P1; ++x) blk[x] = 0.0;
+                  for (int q0 = 0; q0 < nq; ++q0) {
+                    double v[9];
+                    for (int ab = 0; ab < 9; ++ab) {
+                      const int aa = ab / 3, bb = ab % 3;
+                      const double* xa = aa == 1 ? Dd[1] : Vd[1];
+                      const double* xb = bb == 1 ? Dd[1] : Vd[1];
+                      const double* u = &T2[((size_t)ab * nq + q0) * nq * L2 + l2 * P1 + m2];
+                      double t = 0.0;
+                      for (int q1 = 0; q1 < nq; ++q1) t += u[(size_t)q1 * L2] * xa[q1 * P1 + l1] * xb[q1 * P1 + m1];
+                      v[ab] = t;
+                    }
+                    const double w00 = v[0], w01 = v[1] + v[2], w10 = v[3] + v[6];
+                    const double w11 = (v[4] + v[5]) + (v[7] + v[8]);
+                    const double* g0 = &Dd[0][q0 * P1];  // a == 0: derivative along xi_0
+                    const double* g1 = &Vd[0][q0 * P1];
+                    for (int m0 = 0; m0 < P1; ++m0) {
+                      h0[m0] = w00 * g0[m0] + w01 * g1[m0];
+                      h1[m0] = w10 * g0[m0] + w11 * g1[m0];
+                    }
+                    for (int l0 = 0; l0 < P1; ++l0) {
+                      const double a0 = g0[l0], a1 = g1[l0];
+                      double* row = &blk[l0 * P1];
+                      for (int m0 = 0; m0 < P1; ++m0) row[m0] += a0 * h0[m0] + a1 * h1[m0];
+                    }
+                  }
+                  for (int l0 = 0; l0 < P1; ++l0)
+                    for (int m0 = (L12 == M12 ? l0 : 0); m0 < P1; ++m0) {  // a diagonal block: its upper half
+                      const double val = blk[l0 * P1 + m0];
+                      Ke[(size_t)(l0 + P1 * L12) * L3 + (m0 + P1 * M12)] = val;
+                      Ke[(size_t)(m0 + P1 * M12) * L3 + (l0 + P1 * L12)] = val;
+                    }
+                }
+            }
             // scatter into the band: row of l, offset m - l
             const int LL = d == 2 ? L2 : L2 * P1;
             for (int l = 0; l < LL; ++l) {
@@ -372,16 +391,26 @@ static void patch_stiffness(const Problem& pr, Level& L, int k) {
               const int r0 = dq[0].span[e[0]] - p + l0;
               const int r1 = dq[1].span[e[1]] - p + l1;
               const int r2 = d == 3 ? dq[2].span[e[2]] - p + l2 : 0;
-              const int64_t row = L.pos(k, r0, r1, r2);
+              double* brow = &Bt[(size_t)(L.pos(k, r0, r1, r2) - off) * nb];
               for (int m = 0; m < LL; ++m) {
                 const int m0 = m % P1, m1 = (m / P1) % P1, m2 = m / (P1 * P1);
                 int o = (m0 - l0 + p) + W * (m1 - l1 + p);
                 if (d == 3) o += W * W * (m2 - l2 + p);
-                L.band[(size_t)o * L.nloc + row] += Ke[(size_t)l * LL + m];
+                brow[o] += Ke[(size_t)l * LL + m];
               }
             }
           }
       }
+    }
+  }
+  // blocked transpose: a block of rows (all offsets) stays in cache while its columns are written
+  constexpr int64_t kRowBlock = 256;
+#pragma omp parallel for schedule(static)
+  for (int64_t r0 = 0; r0 < rows; r0 += kRowBlock) {
+    const int64_t r1 = std::min(rows, r0 + kRowBlock);
+    for (int o = 0; o < nb; ++o) {
+      double* dst = &L.band[(size_t)o * L.nloc + off];
+      for (int64_t r = r0; r < r1; ++r) dst[r] = Bt[(size_t)r * nb + o];
     }
   }
 }
@@ -493,66 +522,92 @@ static void interface_terms(const Problem& pr, Level& L, const Interface& f,
   int nmax = 4;
   for (int c = 0; c < m; ++c) nmax *= p + 1;
   const size_t ld = (size_t)nmax;
-  std::vector<SideFun> fa, fb;
-  std::vector<int64_t> dofs;
-  Vec blk(ld * ld);
-  std::unordered_map<int64_t, int> slot;
-  std::vector<int> ids;
-  Vec J, Dn;
-  for (int c1 = 0; c1 < nc1; ++c1)
-    for (int c0 = 0; c0 < nc0; ++c0) {
-      dofs.clear();
-      slot.clear();
-      std::fill(blk.begin(), blk.end(), 0.0);
-      for (int g1 = 0; g1 < (m == 2 ? p + 1 : 1); ++g1)
-        for (int g0 = 0; g0 < p + 1; ++g0) {
-          double s[2] = {0.0, 0.0}, w = 1.0;
-          s[0] = cuts[0][c0] + (cuts[0][c0 + 1] - cuts[0][c0]) * xg[g0];
-          w *= (cuts[0][c0 + 1] - cuts[0][c0]) * wg[g0];
-          if (m == 2) {
-            s[1] = cuts[1][c1] + (cuts[1][c1 + 1] - cuts[1][c1]) * xg[g1];
-            w *= (cuts[1][c1 + 1] - cuts[1][c1]) * wg[g1];
+  // the cells' local blocks are computed in parallel (chunks of cells), then
+  // added to the band / cross couplings one cell after another in cell order
+  struct CellBlock {
+    std::vector<int64_t> dofs;
+    Vec blk;  // ld x ld
+  };
+  const int ncell = nc0 * nc1;
+  constexpr int kCellChunk = 256;
+  std::vector<CellBlock> out(std::min(ncell, kCellChunk));
+  for (int cbeg = 0; cbeg < ncell; cbeg += kCellChunk) {
+    const int cend = std::min(ncell, cbeg + kCellChunk);
+    int too_many = 0;  // an exception must not leave the parallel region: flag it, throw after
+#pragma omp parallel
+    {
+      std::vector<SideFun> fa, fb;
+      std::unordered_map<int64_t, int> slot;
+      std::vector<int> ids;
+      Vec J, Dn;
+#pragma omp for schedule(dynamic)
+      for (int cell = cbeg; cell < cend; ++cell) {
+       try {
+        const int c1 = cell / nc0, c0 = cell % nc0;
+        std::vector<int64_t>& dofs = out[cell - cbeg].dofs;
+        Vec& blk = out[cell - cbeg].blk;
+        dofs.clear();
+        slot.clear();
+        blk.assign(ld * ld, 0.0);
+        for (int g1 = 0; g1 < (m == 2 ? p + 1 : 1); ++g1)
+          for (int g0 = 0; g0 < p + 1; ++g0) {
+            double s[2] = {0.0, 0.0}, w = 1.0;
+            s[0] = cuts[0][c0] + (cuts[0][c0 + 1] - cuts[0][c0]) * xg[g0];
+            w *= (cuts[0][c0 + 1] - cuts[0][c0]) * wg[g0];
+            if (m == 2) {
+              s[1] = cuts[1][c1] + (cuts[1][c1 + 1] - cuts[1][c1]) * xg[g1];
+              w *= (cuts[1][c1 + 1] - cuts[1][c1]) * wg[g1];
+            }
+            double sb[2] = {s[0], s[1]};
+            if (swap) std::swap(sb[0], sb[1]);
+            for (int c = 0; c < m; ++c)
+              if (f.orient & (1u << c)) sb[c] = 1.0 - sb[c];
+            double xa[3] = {0, 0, 0}, xb[3] = {0, 0, 0};
+            xa[f.sa / 2] = f.sa % 2 ? 1.0 : 0.0;
+            xb[f.sb / 2] = f.sb % 2 ? 1.0 : 0.0;
+            for (int c = 0; c < m; ++c) { xa[ta[c]] = s[c]; xb[tb[c]] = sb[c]; }
+            double na[3], nb[3], dSa, dSb;
+            side_functions(pr, L, f.pa, f.sa, xa, fa, na, &dSa);
+            side_functions(pr, L, f.pb, f.sb, xb, fb, nb, &dSb);
+            const double wq = w * dSa;
+            auto reg = [&](int64_t pos) {
+              auto it = slot.find(pos);
+              if (it != slot.end()) return it->second;
+              const int id = (int)dofs.size();
+              if (id >= nmax) throw SetupError(1, "interface cell has too many active functions");
+              slot.emplace(pos, id);
+              dofs.push_back(pos);
+              return id;
+            };
+            ids.clear(); J.clear(); Dn.clear();
+            for (const auto& x : fa) {
+              ids.push_back(reg(x.pos));
+              J.push_back(x.val);
+              double g = 0.0;
+              for (int c = 0; c < d; ++c) g += x.grad[c] * na[c];
+              Dn.push_back(0.5 * g);
+            }
+            for (const auto& x : fb) {
+              ids.push_back(reg(x.pos));
+              J.push_back(-x.val);
+              double g = 0.0;
+              for (int c = 0; c < d; ++c) g += x.grad[c] * na[c];
+              Dn.push_back(0.5 * g);
+            }
+            for (size_t i = 0; i < ids.size(); ++i)
+              for (size_t j = 0; j < ids.size(); ++j)
+                blk[(size_t)ids[i] * ld + ids[j]] += wq * (-Dn[i] * J[j] - J[i] * Dn[j] + eta * J[i] * J[j]);
           }
-          double sb[2] = {s[0], s[1]};
-          if (swap) std::swap(sb[0], sb[1]);
-          for (int c = 0; c < m; ++c)
-            if (f.orient & (1u << c)) sb[c] = 1.0 - sb[c];
-          double xa[3] = {0, 0, 0}, xb[3] = {0, 0, 0};
-          xa[f.sa / 2] = f.sa % 2 ? 1.0 : 0.0;
-          xb[f.sb / 2] = f.sb % 2 ? 1.0 : 0.0;
-          for (int c = 0; c < m; ++c) { xa[ta[c]] = s[c]; xb[tb[c]] = sb[c]; }
-          double na[3], nb[3], dSa, dSb;
-          side_functions(pr, L, f.pa, f.sa, xa, fa, na, &dSa);
-          side_functions(pr, L, f.pb, f.sb, xb, fb, nb, &dSb);
-          const double wq = w * dSa;
-          auto reg = [&](int64_t pos) {
-            auto it = slot.find(pos);
-            if (it != slot.end()) return it->second;
-            const int id = (int)dofs.size();
-            if (id >= nmax) throw SetupError(1, "interface cell has too many active functions");
-            slot.emplace(pos, id);
-            dofs.push_back(pos);
-            return id;
-          };
-          ids.clear(); J.clear(); Dn.clear();
-          for (const auto& x : fa) {
-            ids.push_back(reg(x.pos));
-            J.push_back(x.val);
-            double g = 0.0;
-            for (int c = 0; c < d; ++c) g += x.grad[c] * na[c];
-            Dn.push_back(0.5 * g);
-          }
-          for (const auto& x : fb) {
-            ids.push_back(reg(x.pos));
-            J.push_back(-x.val);
-            double g = 0.0;
-            for (int c = 0; c < d; ++c) g += x.grad[c] * na[c];
-            Dn.push_back(0.5 * g);
-          }
-          for (size_t i = 0; i < ids.size(); ++i)
-            for (size_t j = 0; j < ids.size(); ++j)
-              blk[(size_t)ids[i] * ld + ids[j]] += wq * (-Dn[i] * J[j] - J[i] * Dn[j] + eta * J[i] * J[j]);
-        }
+       } catch (...) {
+#pragma omp atomic write
+        too_many = 1;
+       }
+      }
+    }
+    if (too_many) throw SetupError(1, "interface cell has too many active functions");
+    for (int cell = cbeg; cell < cend; ++cell) {
+      const std::vector<int64_t>& dofs = out[cell - cbeg].dofs;
+      const Vec& blk = out[cell - cbeg].blk;
       for (size_t i = 0; i < dofs.size(); ++i)
         for (size_t j = 0; j < dofs.size(); ++j) {
           const double v = blk[i * ld + j];
@@ -575,6 +630,7 @@ static void interface_terms(const Problem& pr, Level& L, const Interface& f,
           }
         }
     }
+  }
 }
 
 void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec, 3>>& fine_knots) {

@@ -126,7 +126,6 @@ void galerkin(const Level& F, const Transfer& T, Level& C) {
       for (int64_t r = 0; r < crow; ++r) C.band[(size_t)o * C.nloc + C.off[k] + r] = B[(size_t)o * crow + r];
   }
   // cross blocks: C_c = P_a^T C P_b, tensor-product parents per direction
-  std::unordered_map<uint64_t, double> acc;
   auto parents = [&](int64_t pos, std::vector<std::pair<int64_t, double>>& out) {
     out.clear();
     const int k = F.patch_of[pos];
@@ -147,29 +146,75 @@ void galerkin(const Level& F, const Transfer& T, Level& C) {
         for (const auto& x0 : par[0])
           out.push_back({C.pos(k, x0.first, x1.first, x2.first), x0.second * x1.second * x2.second});
   };
-  std::vector<std::pair<int64_t, double>> pr_, pc_;
+  // parents of every fine position in the couplings, once
+  std::unordered_map<int64_t, int> pid;
+  std::vector<int64_t> plist;
+  auto want = [&](int64_t pos) {
+    if (pid.emplace(pos, (int)plist.size()).second) plist.push_back(pos);
+  };
   for (size_t i = 0; i < F.x_row.size(); ++i) {
-    parents(F.x_row[i], pr_);
-    for (int j = F.x_ptr[i]; j < F.x_ptr[i + 1]; ++j) {
-      parents(F.x_col[j], pc_);
-      for (const auto& a : pr_)
-        for (const auto& b : pc_)
-          acc[((uint64_t)a.first << 32) | (uint64_t)b.first] += a.second * F.x_val[j] * b.second;
+    want(F.x_row[i]);
+    for (int j = F.x_ptr[i]; j < F.x_ptr[i + 1]; ++j) want(F.x_col[j]);
+  }
+  std::vector<std::vector<std::pair<int64_t, double>>> par_of(plist.size());
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t t = 0; t < (int64_t)plist.size(); ++t) parents(plist[t], par_of[t]);
+  std::vector<int> colp(F.x_col.size());
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < (int64_t)F.x_col.size(); ++j) colp[j] = pid.at(F.x_col[j]);
+  // coarse rows, each with its fine coupling rows (ascending) and the row parent's weight
+  std::map<int64_t, std::vector<std::pair<int, double>>> rows_of;
+  for (size_t i = 0; i < F.x_row.size(); ++i)
+    for (const auto& a : par_of[pid.at(F.x_row[i])]) rows_of[a.first].push_back({(int)i, a.second});
+  std::vector<int64_t> crow;
+  std::vector<const std::vector<std::pair<int, double>>*> cfine;
+  for (const auto& e : rows_of) {
+    crow.push_back(e.first);
+    cfine.push_back(&e.second);
+  }
+  // row by row (in parallel): a coarse entry gets its contributions in the order of
+  // (fine row, coupling, column parent), each as row weight * value * column weight
+  std::vector<std::vector<std::pair<int64_t, double>>> res(crow.size());
+#pragma omp parallel
+  {
+    std::vector<double> acc((size_t)C.nloc, 0.0);
+    std::vector<char> mark((size_t)C.nloc, 0);
+    std::vector<int64_t> touched;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t r = 0; r < (int64_t)crow.size(); ++r) {
+      touched.clear();
+      for (const auto& fi : *cfine[r]) {
+        const int i = fi.first;
+        const double wa = fi.second;
+        for (int j = F.x_ptr[i]; j < F.x_ptr[i + 1]; ++j)
+          for (const auto& b : par_of[colp[j]]) {
+            if (!mark[b.first]) {
+              mark[b.first] = 1;
+              touched.push_back(b.first);
+            }
+            acc[b.first] += wa * F.x_val[j] * b.second;
+          }
+      }
+      std::sort(touched.begin(), touched.end());
+      auto& out = res[r];
+      out.reserve(touched.size());
+      for (int64_t c : touched) {
+        out.push_back({c, acc[c]});
+        acc[c] = 0.0;
+        mark[c] = 0;
+      }
     }
   }
-  std::vector<std::pair<uint64_t, double>> ent(acc.begin(), acc.end());
-  std::sort(ent.begin(), ent.end());
   C.x_row.clear(); C.x_ptr.assign(1, 0); C.x_col.clear(); C.x_val.clear();
-  for (const auto& e : ent) {
-    const int64_t r = (int64_t)(e.first >> 32), c = (int64_t)(e.first & 0xffffffffu);
-    if (C.x_row.empty() || C.x_row.back() != r) {
-      if (!C.x_row.empty()) C.x_ptr.push_back((int)C.x_col.size());
-      C.x_row.push_back(r);
+  for (size_t r = 0; r < crow.size(); ++r) {
+    if (res[r].empty()) continue;
+    C.x_row.push_back(crow[r]);
+    for (const auto& e : res[r]) {
+      C.x_col.push_back(e.first);
+      C.x_val.push_back(e.second);
     }
-    C.x_col.push_back(c);
-    C.x_val.push_back(e.second);
+    C.x_ptr.push_back((int)C.x_col.size());
   }
-  if (!C.x_row.empty()) C.x_ptr.push_back((int)C.x_col.size());
 }
 
 // ---------------------------------------------------------------------------

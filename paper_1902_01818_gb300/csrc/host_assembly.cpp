@@ -227,6 +227,12 @@ static void patch_stiffness(const Problem& pr, Level& L, int k) {
   const int nb = L.nb;
   const int64_t off = L.off[k], rows = L.off[k + 1] - L.off[k];
   Vec Bt((size_t)rows * nb, 0.0);
+  // band offset of entry (l, m) of an element matrix: ocode[m] - ocode[l] + ocode0, with
+  // ocode[x] = x0 + W x1 + W^2 x2 for the local index x = x0 + P1 (x1 + P1 x2)
+  std::vector<int> ocode(d == 2 ? P1 * P1 : P1 * P1 * P1);
+  for (int x = 0; x < (int)ocode.size(); ++x)
+    ocode[x] = x % P1 + W * ((x / P1) % P1) + (d == 3 ? W * W * (x / (P1 * P1)) : 0);
+  const int ocode0 = p + W * p + (d == 3 ? W * W * p : 0);
   // element slabs along the slowest direction touch disjoint band rows when
   // they are p+1 apart: p+1 parallel phases
   // (in 3D the rows of elements along xi_0 are coloured by both outer indices
@@ -391,13 +397,9 @@ static void patch_stiffness(const Problem& pr, Level& L, int k) {
               const int r0 = dq[0].span[e[0]] - p + l0;
               const int r1 = dq[1].span[e[1]] - p + l1;
               const int r2 = d == 3 ? dq[2].span[e[2]] - p + l2 : 0;
-              double* brow = &Bt[(size_t)(L.pos(k, r0, r1, r2) - off) * nb];
-              for (int m = 0; m < LL; ++m) {
-                const int m0 = m % P1, m1 = (m / P1) % P1, m2 = m / (P1 * P1);
-                int o = (m0 - l0 + p) + W * (m1 - l1 + p);
-                if (d == 3) o += W * W * (m2 - l2 + p);
-                brow[o] += Ke[(size_t)l * LL + m];
-              }
+              double* brow = &Bt[(size_t)(L.pos(k, r0, r1, r2) - off) * nb] + (ocode0 - ocode[l]);
+              const double* kr = &Ke[(size_t)l * LL];
+              for (int m = 0; m < LL; ++m) brow[ocode[m]] += kr[m];
             }
           }
       }

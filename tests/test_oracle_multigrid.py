@@ -246,3 +246,36 @@ def test_coarse_solve_inverts_a0():
     A0 = M.h["A"][0].toarray()
     f = np.random.default_rng(0).standard_normal(A0.shape[0])
     assert np.max(np.abs(A0 @ M.coarse_solve(f) - f)) <= 1e-12 * np.max(np.abs(f))
+
+
+@pytest.mark.parametrize("d,p", [(2, 2), (2, 4), (3, 2)])
+def test_couplings_within_a_slow_residue_run_stay_on_one_slow_index(d, p):
+    """A base colour fixes every index modulo p + 1, the slow one outermost, so the
+    colours with one residue of the slowest index form a consecutive run.  Two
+    coupled DoFs of one patch whose colours lie in the same run have the same slow
+    index: during such a run a row never reads a value that another slow index
+    (another slab, hence another CTA of the patch-parallel sweep) updates in it."""
+    cells = (3, 3) if d == 2 else (2, 2, 2)
+    n = (lambda c, a: 6 if sum(c) % 2 == 0 else 8) if d == 2 else 4
+    prob = W.grid_problem(cells, n, p, "sipg", jitter=0.05, seed=7)
+    num = discretize.numbering(prob, prob["knots"])
+    col = smoothers.colouring(prob, prob["knots"], num)
+    B = (p + 1) ** d
+    run_len = B // (p + 1)
+    S = smoothers.structural_pattern(prob, prob["knots"], num).tocoo()
+    owner = num["owner"]
+    shapes = num["shapes"]
+    checked = 0
+    for r, c in zip(S.row.tolist(), S.col.tolist()):
+        if r == c or col[r] >= 2 * B or col[c] >= 2 * B:
+            continue
+        (kr, fr), (kc, fc) = owner[r], owner[c]
+        if kr != kc or col[r] // B != col[c] // B:
+            continue
+        if (col[r] % B) // run_len != (col[c] % B) // run_len:
+            continue
+        slow_r = discretize.unflatten(fr, shapes[kr])[d - 1]
+        slow_c = discretize.unflatten(fc, shapes[kc])[d - 1]
+        assert slow_r == slow_c, (r, c)
+        checked += 1
+    assert checked > 0

@@ -643,20 +643,31 @@ void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec
   std::unordered_map<uint64_t, double> cross;
   if (pr.coupling == 1)
     for (const auto& f : pr.ifaces) interface_terms(pr, L, f, fine_knots, cross);
-  // cross-patch entries to CSR by row position
-  std::vector<std::pair<uint64_t, double>> ent(cross.begin(), cross.end());
-  std::sort(ent.begin(), ent.end());
-  L.x_row.clear(); L.x_ptr.assign(1, 0); L.x_col.clear(); L.x_val.clear();
-  for (const auto& e : ent) {
-    const int64_t r = (int64_t)(e.first >> 32), c = (int64_t)(e.first & 0xffffffffu);
-    if (L.x_row.empty() || L.x_row.back() != r) {
-      if (!L.x_row.empty()) L.x_ptr.push_back((int)L.x_col.size());
-      L.x_row.push_back(r);
-    }
-    L.x_col.push_back(c);
-    L.x_val.push_back(e.second);
+  // cross-patch entries to CSR by row position: counted by row, then each row's
+  // columns sorted (rows in parallel)
+  std::vector<int64_t> cnt((size_t)L.nloc + 1, 0);
+  for (const auto& e : cross) ++cnt[(size_t)(e.first >> 32) + 1];
+  for (int64_t r = 0; r < L.nloc; ++r) cnt[(size_t)r + 1] += cnt[(size_t)r];
+  std::vector<std::pair<int64_t, double>> ent(cross.size());
+  {
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (const auto& e : cross) ent[(size_t)fill[(size_t)(e.first >> 32)]++] = {(int64_t)(e.first & 0xffffffffu), e.second};
   }
-  if (!L.x_row.empty()) L.x_ptr.push_back((int)L.x_col.size());
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t r = 0; r < L.nloc; ++r)
+    if (cnt[(size_t)r + 1] > cnt[(size_t)r]) std::sort(ent.begin() + cnt[(size_t)r], ent.begin() + cnt[(size_t)r + 1]);
+  L.x_row.clear(); L.x_ptr.assign(1, 0); L.x_col.clear(); L.x_val.clear();
+  L.x_col.reserve(ent.size());
+  L.x_val.reserve(ent.size());
+  for (int64_t r = 0; r < L.nloc; ++r) {
+    if (cnt[(size_t)r + 1] == cnt[(size_t)r]) continue;
+    L.x_row.push_back(r);
+    for (int64_t q = cnt[(size_t)r]; q < cnt[(size_t)r + 1]; ++q) {
+      L.x_col.push_back(ent[(size_t)q].first);
+      L.x_val.push_back(ent[(size_t)q].second);
+    }
+    L.x_ptr.push_back((int)L.x_col.size());
+  }
 }
 
 void apply_dirichlet(Level& L) {

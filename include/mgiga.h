@@ -128,7 +128,8 @@ typedef struct {
  * interior operator's mass term is 1/(delta h_l^2) (Sec. 5).  nu: smoothing
  * steps; mu: 1 = V-cycle.  max_iter bounds the outer iterations.
  * hbm_budget: 0 = no limit, else mgiga_assemble fails with MGIGA_ENOMEM when
- * its device footprint would exceed it.  stream: a cudaStream_t on which all
+ * its device footprint would exceed it (before any host assembly when the
+ * FP64 operators of all levels alone exceed it).  stream: a cudaStream_t on which all
  * device work of the handle runs (NULL: the handle creates its own
  * non-blocking stream; set-up copies run on it, and the _d entry points order
  * it after work already queued on the legacy default stream).  Handles used

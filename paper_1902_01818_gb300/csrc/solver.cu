@@ -1380,6 +1380,17 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
   if (!h) return MGIGA_EINVAL;
   if (h->assembled) return fail(h, MGIGA_ESTATE, "already assembled");
   return guarded_call(h, [&]() -> mgiga_status {
+    // every level's FP64 band goes to the device: a lower bound of the footprint,
+    // known before the (long) host assembly -- refuse at once what cannot fit
+    if (h->opt.hbm_budget) {
+      const int W = 2 * h->pr.p + 1;
+      const double nb = h->pr.d == 2 ? (double)W * W : (double)W * W * W;
+      double lower = 0.0;
+      for (const Level& L : h->L) lower += (double)L.nloc * nb * sizeof(double);
+      if (lower > (double)h->opt.hbm_budget)
+        throw SetupError(MGIGA_ENOMEM, "device footprint exceeds hbm_budget (the FP64 operators alone need " +
+                                           std::to_string((long long)lower) + " bytes)");
+    }
     // MGIGA_VERBOSE: time of each set-up phase on stderr
     const bool verbose = std::getenv("MGIGA_VERBOSE") != nullptr;
     auto t_last = std::chrono::steady_clock::now();

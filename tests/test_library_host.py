@@ -117,3 +117,19 @@ def test_invalid_problems_return_status():
             s.stage_work(stage, 1)
         assert e.value.status == mg.ESTATE
     s.close()
+
+
+def test_budget_refusal_before_any_host_or_device_work():
+    """An HBM budget below the FP64 operators of all levels is refused by
+    mgiga_assemble at once (MGIGA_ENOMEM), before the host assembly and without
+    touching a GPU; the handle stays destroyable."""
+    import time
+    mg = binding()
+    prob = W.grid_problem((2, 2), 16, 3, "sipg", jitter=0.1, seed=3)
+    s = mg.Solver(prob, levels=2, precision="fp32", hbm_budget=1 << 16, assemble=False)
+    t0 = time.perf_counter()
+    with pytest.raises(mg.MgigaError) as e:
+        s.assemble()
+    assert e.value.status == mg.ENOMEM and "FP64 operators alone" in s.last_error()
+    assert time.perf_counter() - t0 < 1.0
+    s.close()

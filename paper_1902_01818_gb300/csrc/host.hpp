@@ -87,6 +87,7 @@ struct Level {
   // operator: band[o * nloc + pos], o = sum_a (o_a + p) (2p+1)^a
   int nb = 0;
   Vec band;
+  double nnz = 0.0;  // nonzero band coefficients (kept when the host band is released)
   // SIPG cross-patch couplings, CSR over rows x_row[i]
   std::vector<int64_t> x_row;
   std::vector<int> x_ptr;

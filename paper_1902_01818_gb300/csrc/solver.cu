@@ -1506,6 +1506,14 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
     h->out = A.alloc<double>(maxdof);
     CK(cudaMallocHost(&h->host_scal, S_COUNT * sizeof(double)));
     CK(cudaStreamSynchronize(h->stream));
+    // the device holds the operators now: keep the nonzero counts, release the host bands
+    // (a resident handle otherwise keeps twice its operators' size in host memory)
+    for (Level& L : h->L) {
+      double nnz = 0.0;
+      for (double v : L.band) nnz += v != 0.0;
+      L.nnz = nnz;
+      Vec().swap(L.band);
+    }
     h->assembled = true;
     return MGIGA_OK;
   });
@@ -1970,14 +1978,13 @@ mgiga_status mgiga_stage_work(const mgiga_handle* h, int stage, int level, doubl
   if (!h || level < 0 || level >= h->levels) return MGIGA_EINVAL;
   if (!stage_valid(h, stage, level)) return MGIGA_EINVAL;
   const Level& L = h->L[level];
-  if (L.band.empty()) return MGIGA_ESTATE;  // operators are assembled by mgiga_assemble
+  if (!h->assembled) return MGIGA_ESTATE;  // operators are assembled by mgiga_assemble
   // the mixed path keeps FP32 band copies for the cycle's residuals (levels >= 1) and sweeps
   const bool f32 = h->opt.precision != MGIGA_PREC_FP64;
   double fl = 0.0, by = 0.0;
   if (stage == MGIGA_STAGE_BAND || stage == MGIGA_STAGE_RESIDUAL) {
     // every nonzero once (FP32 coefficients for the residual of the mixed path), u and f read, out written
-    double nnz = 0.0;
-    for (double v : L.band) nnz += v != 0.0;
+    const double nnz = L.nnz;
     fl = 2.0 * nnz;
     by = (stage == MGIGA_STAGE_RESIDUAL && f32 && level > 0 ? 4.0 : 8.0) * nnz + 24.0 * (double)L.nloc;
   } else if (stage == MGIGA_STAGE_FD) {
@@ -1989,8 +1996,7 @@ mgiga_status mgiga_stage_work(const mgiga_handle* h, int stage, int level, doubl
     }
   } else if (stage == MGIGA_STAGE_GS) {
     // every nonzero once (FP32 coefficients on the mixed path), u read and written, f read
-    double nnz = 0.0;
-    for (double v : L.band) nnz += v != 0.0;
+    const double nnz = L.nnz;
     fl = 2.0 * nnz;
     by = (f32 ? 4.0 : 8.0) * nnz + 24.0 * (double)L.nloc;
   } else {

@@ -35,6 +35,12 @@ CASES = {
                                          jitter_boundary_tangential=True, flip_patches=(5,)), 2),
     "sipg3d_p2": (lambda: W.grid_problem((2, 1, 2), _nm, 2, "sipg", jitter=0.05, seed=4, flip_patches=(1,),
                                          transpose_patches=(2,)), 2),
+    "sipg2d_p6": (lambda: W.grid_problem((2, 2), lambda c, a: 8 if sum(c) % 2 == 0 else 10, 6, "sipg",
+                                         jitter=0.1, seed=8, flip_patches=(2,)), 2),
+    "sipg3d_p4": (lambda: W.grid_problem((2, 2, 2), 2, 4, "sipg", jitter=0.05, seed=9, transpose_patches=(1,),
+                                         jitter_boundary_tangential=True), 2),
+    "conf3d_p4": (lambda: W.grid_problem((2, 2, 2), 2, 4, "conforming", jitter=0.05, seed=10, flip_patches=(3,),
+                                         jitter_boundary_tangential=True), 2),
     "lshape_conf_p3": (lambda: W.grid_problem((2, 2), 4, 3, "conforming", jitter=0.1, seed=5,
                                               active=[(0, 0), (1, 0), (0, 1)]), 2),
     "lshape_sipg_p2": (lambda: W.grid_problem((2, 2), _nm, 2, "sipg", jitter=0.1, seed=6,

@@ -272,6 +272,14 @@ enum {
 };
 mgiga_status mgiga_kernel_launches(const mgiga_handle* h, long long* n);
 
+/* Relative residuals ||f - A u|| / ||f|| of the last mgiga_solve[_d] on this
+ * handle: the initial one, then one per outer iteration (PCG: the recursive
+ * residual, the last entry the confirming true residual; direct: the true
+ * residual); a zero right-hand side gives {0}; empty before the first solve.
+ * *n receives the number of entries; min(cap, *n) are written to out (out may
+ * be NULL when cap is 0). */
+mgiga_status mgiga_residual_history(const mgiga_handle* h, double* out, int cap, int* n);
+
 /* Diagnostics of the bounded device waits.  Every spin-wait of the kernels
  * (grid barrier, mbarrier of an asynchronous copy) gives up after a fixed
  * number of polls (2^18 for an mbarrier, ~1 s), records the expiry in a

@@ -186,6 +186,7 @@ struct mgiga_handle {
   cudaGraphExec_t g_iter_a = nullptr, g_iter_b = nullptr, g_vcycle = nullptr;
   long long g_iter_a_kernels = 0, g_iter_b_kernels = 0;
   long long launches = 0;  // kernels enqueued on the device by this handle
+  std::vector<double> history;  // relative residuals of the last solve: initial, then per iteration
 
   ~mgiga_handle() {
     if (g_iter_a) cudaGraphExecDestroy(g_iter_a);
@@ -1757,6 +1758,7 @@ static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, do
   read_scal();
   const double ff = h->host_scal[S_FF];
   if (iters) *iters = 0;
+  h->history.clear();
   if (!std::isfinite(ff) || !std::isfinite(h->host_scal[S_RR]))
     return fail(h, MGIGA_EBREAKDOWN, "non-finite right-hand side or initial guess");
   if (!(ff > 0.0)) {
@@ -1765,10 +1767,12 @@ static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, do
     launch_gather(d.ndof, st, d.owner, h->x, u);
     CK(cudaStreamSynchronize(st));
     if (final_relres) *final_relres = 0.0;
+    h->history.push_back(0.0);
     return MGIGA_OK;
   }
   const double nf = std::sqrt(ff);
   double rel = std::sqrt(h->host_scal[S_RR]) / nf;
+  h->history.push_back(rel);
   const int maxit = h->opt.max_iter;
   int it = 0;
   bool converged = rel <= tol;
@@ -1783,6 +1787,7 @@ static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, do
       read_scal();
       ++it;
       rel = std::sqrt(h->host_scal[S_RR]) / nf;
+      h->history.push_back(rel);
       if (!std::isfinite(rel)) return fail(h, MGIGA_EBREAKDOWN, "non-finite residual");
       converged = rel <= tol;
     }
@@ -1826,6 +1831,7 @@ static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, do
       ++it;
       const double pq = h->host_scal[S_PQ];
       rel = std::sqrt(h->host_scal[S_RR]) / nf;
+      h->history.push_back(rel);
       if (!(pq > 0.0) || !std::isfinite(rel)) return fail(h, MGIGA_EBREAKDOWN, "CG breakdown (p^T A p <= 0 or NaN)");
       if (rel <= tol) {
         // confirm with the true residual
@@ -1834,7 +1840,12 @@ static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, do
         check_launch();
         read_scal();
         const double trel = std::sqrt(h->host_scal[S_TMP]) / nf;
-        if (trel <= tol) { rel = trel; converged = true; break; }
+        if (trel <= tol) {  // the history ends with the confirmed (true) residual
+          rel = trel;
+          h->history.back() = trel;
+          converged = true;
+          break;
+        }
       }
       if (it >= maxit) break;
       CK(cudaGraphLaunch(h->g_iter_b, st));
@@ -1897,6 +1908,13 @@ mgiga_status mgiga_check_wait_expiry(mgiga_handle* h, long long iterations, doub
     check_device_timeout(h);
     return MGIGA_OK;
   });
+}
+
+mgiga_status mgiga_residual_history(const mgiga_handle* h, double* out, int cap, int* n) {
+  if (!h || !n || cap < 0 || (cap > 0 && !out)) return MGIGA_EINVAL;
+  *n = (int)h->history.size();
+  for (int i = 0; i < std::min(cap, *n); ++i) out[i] = h->history[(size_t)i];
+  return MGIGA_OK;
 }
 
 mgiga_status mgiga_kernel_launches(const mgiga_handle* h, long long* n) {

@@ -78,6 +78,7 @@ _SIGS = {
     "mgiga_residual_noalloc_d": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mgiga_kernel_launches": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
     "mgiga_check_wait_expiry": (C.c_int, [_H, C.c_longlong, _D]),
+    "mgiga_residual_history": (C.c_int, [_H, _D, C.c_int, _I]),
     "mgiga_time_stage": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, _D]),
     "mgiga_stage_work": (C.c_int, [_H, C.c_int, C.c_int, _D, _D]),
     "mgiga_num_levels": (C.c_int, [_H, _I]),
@@ -221,6 +222,15 @@ class Solver:
         ms = C.c_double()
         st = _lib.mgiga_check_wait_expiry(self._h, iterations, C.byref(ms))
         return st, ms.value
+
+    def residual_history(self):
+        """Relative residuals of the last solve: initial, then per outer iteration."""
+        n = C.c_int()
+        self._check(_lib.mgiga_residual_history(self._h, None, 0, C.byref(n)))
+        out = np.zeros(n.value)
+        if n.value:
+            self._check(_lib.mgiga_residual_history(self._h, _dptr(out), n.value, C.byref(n)))
+        return out
 
     def kernel_launches(self):
         n = C.c_longlong()

@@ -178,6 +178,11 @@ def test_pcg_iterates_and_iteration_count(name, smoother):
     assert abs(it_l - it_o) <= 1
     assert rel_l <= 1e-8
     assert np.linalg.norm(orc.A @ u_l - f) <= 1e-8 * np.linalg.norm(f) * 1.0001
+    # the residual history: initial (u = 0: exactly 1), per iteration, the confirmed one last
+    h = lib.residual_history()
+    assert len(h) == it_l + 1 and h[-1] == rel_l and abs(h[0] - 1.0) <= 1e-14
+    m = min(len(h), len(hist))
+    assert np.allclose(h[:m], hist[:m], rtol=1e-6), (h[:m], hist[:m])
 
 
 @pytest.mark.parametrize("name", ["conf2d_p2", "sipg2d_p3"])

@@ -133,3 +133,11 @@ def test_budget_refusal_before_any_host_or_device_work():
     assert e.value.status == mg.ENOMEM and "FP64 operators alone" in s.last_error()
     assert time.perf_counter() - t0 < 1.0
     s.close()
+
+
+def test_residual_history_is_empty_before_a_solve():
+    mg = binding()
+    prob = W.grid_problem((2, 1), 4, 2, "sipg")
+    s = mg.Solver(prob, levels=2, assemble=False)
+    assert s.residual_history().size == 0
+    s.close()

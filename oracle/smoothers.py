@@ -54,6 +54,65 @@ def interior_operator(knots_k, p, delta):
     return L.tocsc(), sigma
 
 
+def interior_eigen(knots_k, p, delta):
+    """The interior operator L_T of a patch in its eigenbasis (Sec. 5, Eq. Ldef).
+
+    L_T (interior_operator above) is a Kronecker sum of the 1D parameter-domain
+    pencils (K^_a, M^_a) restricted to the interior indices, plus sigma times
+    the Kronecker product of the M^_a.  With the generalised eigenpairs
+    K^_a U_a = M^_a U_a diag(lam_a), U_a^T M^_a U_a = I (LAPACK through
+    scipy.linalg.eigh, a library routine), it is
+        L_T = (M^ U)_{d-1} x .. x (M^ U)_0 diag(sigma + sum_a lam_a) (..)^T,
+    so L_T^{-1} = (U_{d-1} x .. x U_0) diag(1 / (sigma + sum_a lam_a)) (..)^T.
+    Returns (U_a list, lam_a list, sigma).  Used where a sparse LU of the
+    Kronecker matrix is too slow (large patches); pinned against that LU on
+    small patches.
+    """
+    Us, lams = [], []
+    for t in knots_k:
+        K, M = discretize.param_matrices_1d(t, p)
+        lam, U = sla.eigh(K[1:-1, 1:-1], M[1:-1, 1:-1])
+        Us.append(U)
+        lams.append(lam)
+    h = discretize.grid_size(knots_k)
+    return Us, lams, 1.0 / (delta * h * h)
+
+
+def interior_solve_eigen(knots_k, p, delta):
+    """x -> L_T^{-1} x on one patch interior (interior flat order, direction 0
+    fastest) by the eigenbasis of interior_eigen: the transforms are applied
+    one direction at a time to the array of shape (n_{d-1}, .., n_0)."""
+    Us, lams, sigma = interior_eigen(knots_k, p, delta)
+    d = len(Us)
+    shape = tuple(len(lams[a]) for a in range(d - 1, -1, -1))
+    den = np.full(shape, sigma)
+    for a in range(d):
+        ax = d - 1 - a  # array axis of direction a
+        den = den + lams[a].reshape([-1 if i == ax else 1 for i in range(d)])
+
+    def apply(x):
+        X = x.reshape(shape)
+        for a in range(d):  # X <- U_a^T along direction a
+            X = np.moveaxis(np.tensordot(Us[a].T, X, axes=([1], [d - 1 - a])), 0, d - 1 - a)
+        X = X / den
+        for a in range(d):  # X <- U_a along direction a
+            X = np.moveaxis(np.tensordot(Us[a], X, axes=([1], [d - 1 - a])), 0, d - 1 - a)
+        return X.reshape(-1)
+
+    return apply
+
+
+def interior_dofs(num, k):
+    """Global DoFs of the interior of patch k (indices 1..N-2 in every
+    direction) in interior flat order (direction 0 fastest)."""
+    shape = num["shapes"][k]
+    multi = discretize.unflatten(np.arange(int(np.prod(shape))), shape)
+    inner = np.ones(len(multi[0]), dtype=bool)
+    for a, n in enumerate(shape):
+        inner &= (multi[a] >= 1) & (multi[a] <= n - 2)
+    return num["loc2glob"][k][inner]
+
+
 class SCMS:
     """Subspace-corrected mass smoother of one level (Sec. 5, Eq. Ldef)."""
 

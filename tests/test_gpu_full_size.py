@@ -80,7 +80,10 @@ def test_benchmark_layout_full_size(p):
 
 
 @pytest.mark.parametrize("coupling", ["conforming", "sipg"])
-def test_cube_full_size(coupling):
+def test_cube_full_size(coupling, monkeypatch):
+    """Interiors of 49 per direction: MGIGA_FD_TENSOR_MIN_N=1 sends the TF32 and
+    BF16 contractions to the tensor cores (by default these sizes take FP32 SIMT)."""
+    monkeypatch.setenv("MGIGA_FD_TENSOR_MIN_N", "1")
     prob, opts = W.cube_2x2x2(3, coupling)
     lib64, u64, it64 = _solve(prob, opts, "fp64")
     _numbering_matches(prob, lib64)
@@ -92,3 +95,62 @@ def test_cube_full_size(coupling):
         assert it <= it64 + extra, (prec, it, it64)
         assert _sample_error(prob, lib, u, npts=4) <= 1e-4
         lib.close()
+
+
+def _interior_smoother_check(prob, opts, precision, seed):
+    """One application of the smoother on the finest level with u = 0 and f
+    supported on the patch interiors: the interface pieces receive zero, so the
+    result is tau sum_k P_k L_k^{-1} P_k^T f over the interiors (Sec. 5,
+    Eq. Ldef), which the oracle evaluates patch by patch in the eigenbasis of the
+    1D pencils (LAPACK; pinned against the sparse LU of L_k on small patches).
+    Returns the relative 2-norm error."""
+    from oracle import smoothers
+    lib = binding().Solver(prob, levels=opts.get("levels", 0), smoother=opts["smoother"], tau=opts["tau"],
+                           delta=opts["delta"], precision=precision)
+    num = discretize.numbering(prob, prob["knots"])
+    assert lib.ndof() == num["ndof"]
+    rng = np.random.default_rng(seed)
+    f = np.zeros(num["ndof"])
+    ref = np.zeros(num["ndof"])
+    for k in range(len(prob["knots"])):
+        idx = smoothers.interior_dofs(num, k)
+        f[idx] = rng.standard_normal(len(idx))
+        solve = smoothers.interior_solve_eigen(prob["knots"][k], prob["degree"], opts["delta"])
+        ref[idx] = opts["tau"] * solve(f[idx])
+    got = lib.apply("smooth", lib.levels - 1, f, np.zeros_like(f))
+    lib.close()
+    return np.linalg.norm(got - ref) / np.linalg.norm(ref)
+
+
+def _smooth_tol(precision, d):
+    # one application's rounding bound (as in test_gpu_mixed.smooth_tol): FP64 at the
+    # accuracy of the two eigen-solvers, FP32 summation, 2d truncated / rounded TF32 / BF16 steps
+    if precision == "fp64":
+        return 1e-10
+    if precision == "fp32":
+        return 1e-5
+    return 4 * d * (2.0 ** -10 if precision == "tf32" else 2.0 ** -8)
+
+
+@pytest.mark.parametrize("precision,chained", [("fp64", "1"), ("fp32", "1"), ("tf32", "1"), ("tf32", "0"),
+                                              ("bf16", "1")])
+@pytest.mark.parametrize("p", [2, 6])
+def test_benchmark_layout_finest_smoother(p, precision, chained, monkeypatch):
+    """The finest level of the benchmark layout (192/288 intervals, interiors of
+    190-292 per direction): by default the TF32 / BF16 modes run the tcgen05
+    contractions here (TF32: the chained passes, or the four separate steps with
+    MGIGA_FD_CHAINED=0), FP32 the SIMT tiles, FP64 the FP64 tiles."""
+    monkeypatch.setenv("MGIGA_FD_CHAINED", chained)
+    prob, opts = W.sipg_3x3(p, scale=3, smoother="hybrid")
+    err = _interior_smoother_check(prob, opts, precision, seed=20 + p)
+    assert err <= _smooth_tol(precision, 2), err
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_cube_finest_smoother_tensor_cores(precision, monkeypatch):
+    """The 3D contractions (six steps, batched planes) on the tensor cores at the
+    cube's full size (48 intervals, p = 3: interiors of 49)."""
+    monkeypatch.setenv("MGIGA_FD_TENSOR_MIN_N", "1")
+    prob, opts = W.cube_2x2x2(3, "sipg")
+    err = _interior_smoother_check(prob, opts, precision, seed=31)
+    assert err <= _smooth_tol(precision, 3), err

@@ -208,3 +208,34 @@ def test_gauss_seidel_streamed_ring(cs, nbuf, monkeypatch):
         got = lib.apply(op, lib.levels - 1, f, u)
         assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref - u), op
     lib.close()
+
+
+@pytest.mark.parametrize("precision,chained", [("tf32", "1"), ("tf32", "0"), ("bf16", "1")])
+@pytest.mark.parametrize("name", list(CASES))
+def test_tensor_core_smoother_every_level(name, precision, chained, monkeypatch):
+    """The tcgen05 contractions on these small interiors: MGIGA_FD_TENSOR_MIN_N=1
+    sends every level's fast diagonalisation to the tensor cores (2D TF32: the two
+    chained-contraction passes of fd_fused_tf32, or with MGIGA_FD_CHAINED=0 the
+    four gemm_umma_tf32 steps; 3D TF32: gemm_umma_tf32; BF16: gemm_umma<BF16>;
+    with MGIGA_FD_FUSE=0 the 2D levels leave the one-CTA SIMT path), one smoother
+    application against the oracle's explicit interior solves at the rounding
+    bound of the arithmetic."""
+    monkeypatch.setenv("MGIGA_FD_TENSOR_MIN_N", "1")
+    monkeypatch.setenv("MGIGA_FD_FUSE", "0")
+    monkeypatch.setenv("MGIGA_FD_CHAINED", chained)
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    lib = binding().Solver(prob, levels=levels, smoother="hybrid", precision=precision, **opt)
+    orc = omg.Multigrid(prob, levels=levels, smoother="hybrid", **opt)
+    rng = np.random.default_rng(15)
+    for l in range(1, levels):
+        A = orc.h["A"][l]
+        n = A.shape[0]
+        u, f = rng.standard_normal(n), rng.standard_normal(n)
+        ref = u + orc.scms[l].apply(f - A @ u)
+        got = lib.apply("smooth", l, f, u)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref - u)
+        assert err <= smooth_tol(precision, prob["dim"]), (l, err)
+        # and not exact: the tensor-core arithmetic is really in use
+        assert err > 1e-9, (l, err)
+    lib.close()

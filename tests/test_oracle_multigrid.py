@@ -279,3 +279,93 @@ def test_couplings_within_a_slow_residue_run_stay_on_one_slow_index(d, p):
         assert slow_r == slow_c, (r, c)
         checked += 1
     assert checked > 0
+
+
+def _smoother_error_ops(M, l):
+    """Dense error propagation of the pre- and post-smoothing steps on level l,
+    built from the oracle's single smoother applications (each pinned above):
+    S_pre = (I - W A)^nu (I - G_f A), S_post = (I - G_b A)(I - W A)^nu for the
+    hybrid smoother (Algorithm 2), without the Gauss-Seidel factors for SCMS."""
+    A = M.h["A"][l].toarray()
+    n = A.shape[0]
+    I = np.eye(n)
+    W = np.column_stack([M.scms[l].apply(I[:, j]) for j in range(n)])
+    S = np.linalg.matrix_power(I - W @ A, M.nu)
+    if M.smoother == "hybrid":
+        z = np.zeros(n)
+        Gf = np.column_stack([M.gs[l].forward(I[:, j], z) for j in range(n)])
+        Gb = np.column_stack([M.gs[l].backward(I[:, j], z) for j in range(n)])
+        return S @ (I - Gf @ A), (I - Gb @ A) @ S
+    return S, S
+
+
+@pytest.mark.parametrize("smoother,nu", [("hybrid", 1), ("hybrid", 2), ("scms", 2)])
+def test_w_cycle_matches_the_textbook_recursion(smoother, nu):
+    """mu = 2 (W-cycle, Sec. 4): the error propagation of the cycle satisfies the
+    two-grid recursion E_l = S_post (I - P_l (I - E_{l-1}^mu) A_{l-1}^{-1} P_l^T A_l)
+    S_pre with E_0 = 0 (exact coarse solve); evaluated here with dense matrices
+    on three levels, so that level 1 is visited twice per cycle on level 2.
+    A second visit that reuses a stale residual, or a single visit, fails it."""
+    prob = W.grid_problem((2, 2), _nm, 2, "sipg", jitter=0.1, seed=8)
+    M = mg.Multigrid(prob, levels=3, smoother=smoother, tau=0.5, delta=0.2, nu=nu, mu=2)
+    E = None
+    for l in range(1, 3):
+        A = M.h["A"][l].toarray()
+        P = M.h["P"][l].toarray()
+        Ac = M.h["A"][l - 1].toarray()
+        n = A.shape[0]
+        Ec = np.zeros_like(Ac) if E is None else E
+        mu = 2 if l > 1 else 1  # with an exact coarse solve a second visit changes nothing
+        coarse = (np.eye(Ac.shape[0]) - np.linalg.matrix_power(Ec, mu)) @ np.linalg.inv(Ac)
+        S_pre, S_post = _smoother_error_ops(M, l)
+        E = S_post @ (np.eye(n) - P @ coarse @ P.T @ A) @ S_pre
+    Eo = M.error_propagation()
+    assert np.max(np.abs(Eo - E)) <= 1e-10 * max(1.0, np.max(np.abs(E)))
+    # and with mu = 1 the recursion differs: the pin separates V- and W-cycles
+    Mv = mg.Multigrid(prob, levels=3, smoother=smoother, tau=0.5, delta=0.2, nu=nu, mu=1)
+    assert np.max(np.abs(Mv.error_propagation() - E)) > 1e-6
+
+
+@pytest.mark.parametrize("coupling", ["conforming", "sipg"])
+def test_w_cycle_converges_and_preconditioner_is_symmetric(coupling):
+    n = 4 if coupling == "conforming" else _nm
+    prob = W.grid_problem((2, 2), n, 2, coupling, jitter=0.1, seed=8)
+    tau = 1.0 if coupling == "conforming" else 0.5
+    M = mg.Multigrid(prob, levels=3, smoother="hybrid", tau=tau, delta=0.2, mu=2, nu=2)
+    rho = max(abs(np.linalg.eigvals(M.error_propagation())))
+    Mv = mg.Multigrid(prob, levels=3, smoother="hybrid", tau=tau, delta=0.2, mu=1, nu=2)
+    rho_v = max(abs(np.linalg.eigvals(Mv.error_propagation())))
+    assert rho < 1.0 and rho <= rho_v + 1e-12, (rho, rho_v)  # more coarse work contracts no worse
+    rng = np.random.default_rng(3)
+    x, y = rng.standard_normal(M.ndof), rng.standard_normal(M.ndof)
+    bx, by = M.precondition(x), M.precondition(y)
+    assert abs(y @ bx - x @ by) <= 1e-12 * np.linalg.norm(bx) * np.linalg.norm(y)
+
+
+def test_two_level_w_cycle_equals_v_cycle():
+    """On two levels the coarse solve is exact, so after the first coarse
+    correction P^T (f - A u) = 0 (Galerkin A_0 = P^T A P) and a second one adds
+    nothing: the W- and V-cycles coincide."""
+    prob = W.grid_problem((2, 2), _nm, 3, "sipg", jitter=0.1, seed=5)
+    Mw = mg.Multigrid(prob, levels=2, smoother="hybrid", tau=0.5, delta=0.2, mu=2)
+    Mv = mg.Multigrid(prob, levels=2, smoother="hybrid", tau=0.5, delta=0.2, mu=1)
+    r = np.random.default_rng(4).standard_normal(Mw.ndof)
+    bw, bv = Mw.precondition(r), Mv.precondition(r)
+    assert np.max(np.abs(bw - bv)) <= 1e-12 * np.max(np.abs(bv))
+
+
+@pytest.mark.parametrize("d,p", [(1, 3), (2, 1), (2, 2), (2, 4), (2, 6), (3, 2), (3, 3)])
+def test_interior_eigen_solve_equals_sparse_lu(d, p):
+    """The eigenbasis form of L_T^{-1} (used at sizes where the sparse LU is too
+    slow) against the sparse LU of the assembled Kronecker operator, on patches
+    with a different interval count in every direction (a transposed direction
+    or a wrong eigenvalue sum fails)."""
+    nint = [5, 7, 6][:d] if d > 1 else [9]
+    cells = (1,) * max(d, 2) if d > 1 else (1, 1)
+    prob = W.grid_problem(cells, lambda c, a: nint[a] if a < len(nint) else 4, p, "sipg", jitter=0.0)
+    kn = prob["knots"][0][:d]
+    L, _ = smoothers.interior_operator(kn, p, 0.12)
+    ap = smoothers.interior_solve_eigen(kn, p, 0.12)
+    x = np.random.default_rng(d * 10 + p).standard_normal(L.shape[0])
+    ref = spla.spsolve(L, x)
+    assert np.max(np.abs(ap(x) - ref)) <= 1e-11 * np.max(np.abs(ref))

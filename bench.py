@@ -207,6 +207,98 @@ def oracle_sample(args):
     return WORKLOADS[args.workload][1].format(smoother=args.smoother)
 
 
+def _oracle_worker_init():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
+def oracle_job(kind, p, scale, smoother):
+    """One oracle job in a spawned single-threaded worker (the oracle is test infrastructure; this
+    CPU leg is the one place the benchmark runs it).  kind 'time': a timed PCG solve (set-up
+    excluded); kind 'solution': the oracle's load vector and its PCG solution to 1e-8."""
+    from oracle import discretize, mg
+    from paper_1902_01818_gb300 import workloads as W
+    prob, opts = W.sipg_3x3(p, scale=scale, smoother=smoother)
+    t0 = time.perf_counter()
+    M = mg.Multigrid(prob, smoother=opts["smoother"], tau=opts["tau"], delta=opts["delta"])
+    f = discretize.assemble_load(prob, prob["knots"], M.h["num"][-1], W.source_sinprod)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    u, it, hist = M.solve_pcg(f, tol=1e-8)
+    t = time.perf_counter() - t0
+    out = {"ndof": int(M.ndof), "seconds": t, "setup_s": t_setup, "iterations": int(it), "relres": float(hist[-1])}
+    if kind == "solution":
+        out.update(f=f, u=u)
+    return out
+
+
+class OracleLegs:
+    """CPU legs of the benchmark, started before the process touches the GPU (spawned workers):
+      * cpu_baseline: one timed oracle PCG solve of the benchmark's own layout (192/288 intervals)
+        at p = 2, one core;
+      * the oracle's FP64 solutions of the 64/96-interval sample, p = 2..6, against which both GPU
+        arms report their error;
+      * afterwards, all host cores: one oracle solve of the 64/96, p = 2 sample per core at once."""
+
+    def __init__(self, args, degrees):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        # one BLAS / OpenMP thread in every worker: a spawned child imports this module (and numpy)
+        # before any initializer runs, so the limit must be in the environment it inherits
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"
+        self.args = args
+        self.ncpu = os.cpu_count() or 1
+        self.pool = cf.ProcessPoolExecutor(max_workers=max(2, min(self.ncpu, len(degrees) + 1)),
+                                           mp_context=mp.get_context("spawn"), initializer=_oracle_worker_init)
+        self.base = self.pool.submit(oracle_job, "time", 2, args.scale, args.smoother)
+        self.sol = {p: self.pool.submit(oracle_job, "solution", p, 1, args.smoother) for p in degrees}
+
+    def baseline(self):
+        r = self.base.result()
+        return {"value": r["ndof"] / r["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                "sample": f"one oracle PCG solve of the benchmark layout at {64 * self.args.scale}/"
+                          f"{96 * self.args.scale} intervals, p = 2 ({r['ndof']} unknowns, {r['iterations']} "
+                          f"iterations to 1e-8, {r['seconds']:.1f} s; set-up {r['setup_s']:.0f} s excluded; "
+                          f"numpy/scipy, 1 thread)", "cpu_model": cpu_model(), "nproc": self.ncpu}
+
+    def solutions(self):
+        return {p: fu.result() for p, fu in self.sol.items()}
+
+    def all_cores(self):
+        """One 64/96, p = 2 oracle solve per host core, all at once (after the GPU timing)."""
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.pool.shutdown(wait=True)
+        n = self.ncpu
+        with cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn"),
+                                    initializer=_oracle_worker_init) as ex:
+            t0 = time.perf_counter()
+            rs = list(ex.map(oracle_job, ["time"] * n, [2] * n, [1] * n, [self.args.smoother] * n))
+            wall = time.perf_counter() - t0
+        slowest = max(r["seconds"] for r in rs)
+        return {"value": sum(r["ndof"] for r in rs) / slowest, "unit": "DoF/s", "cores": n, "kind": "oracle",
+                "cpu_model": cpu_model(), "nproc": n,
+                "sample": f"{n} independent oracle PCG solves of the 64/96-interval layout, p = 2 ({rs[0]['ndof']} "
+                          f"unknowns each), one per core at once, 1 thread each; value = unknowns / the slowest "
+                          f"solve ({slowest:.1f} s; set-ups excluded, wall {wall:.0f} s)"}
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(args):
     expr = oracle_sample(args)
     r = run_oracle(expr, 1)
@@ -315,16 +407,19 @@ def main():
         if world > 1:
             dist.barrier()
 
-    # the CPU baseline runs first (spawned process, before this process uses the GPU)
-    cpu = None
+    degrees = [int(x) for x in (args.degrees or WORKLOADS[args.workload][0]).split(",")]
+    # the CPU legs start first (spawned processes, before this process uses the GPU)
+    legs, cpu = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args)
+        if args.workload == "sipg3x3":
+            legs = OracleLegs(args, degrees)
+        else:
+            cpu = cpu_baseline(args)
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_1902_01818_gb300 import mgiga
+    from paper_1902_01818_gb300 import mgiga, workloads as W
 
-    degrees = [int(x) for x in (args.degrees or WORKLOADS[args.workload][0]).split(",")]
     stream = torch.cuda.Stream()  # the timing events live on this stream
     torch.cuda.set_stream(stream)
     # one stream per degree (and precision): the independent solves of a step run concurrently,
@@ -374,9 +469,11 @@ def main():
 
     concurrent = not args.sequential and all(coop_free(s, p, d) for s, p, d in zip(solvers, degrees, dims))
 
-    def solve_one(i, s, host_path, out):
+    def solve_one(i, s, host_path, out, ev=None):
         st_ = streams[(degrees[i], s.precision)]
         with torch.cuda.stream(st_):
+            if ev is not None:
+                ev[i][0].record(st_)
             if host_path:
                 u_h[i].zero_()
                 u, it, rel, st = s.solve(rhs_h[i].numpy(), u0=u_h[i].numpy(), tol=1e-8)
@@ -384,9 +481,11 @@ def main():
             else:
                 u_d[i].zero_()
                 it, rel, st = s.solve_d(rhs_d[i], u_d[i], tol=1e-8)
+            if ev is not None:
+                ev[i][1].record(st_)
         out[i] = (it, rel)
 
-    def step(host_path=False, which=None):
+    def step(host_path=False, which=None, ev=None):
         which = which if which is not None else solvers
         out = [None] * len(which)
         # worker streams start after everything enqueued on the timing stream so far
@@ -395,14 +494,14 @@ def main():
         for i, s in enumerate(which):
             streams[(degrees[i], s.precision)].wait_event(start)
         if concurrent and all(s.precision != "fp64" for s in which):
-            ths = [threading.Thread(target=solve_one, args=(i, s, host_path, out)) for i, s in enumerate(which)]
+            ths = [threading.Thread(target=solve_one, args=(i, s, host_path, out, ev)) for i, s in enumerate(which)]
             for t in ths:
                 t.start()
             for t in ths:
                 t.join()
         else:
             for i, s in enumerate(which):
-                solve_one(i, s, host_path, out)
+                solve_one(i, s, host_path, out, ev)
         for i, s in enumerate(which):  # the timing stream continues after every solve
             done = torch.cuda.Event()
             done.record(streams[(degrees[i], s.precision)])
@@ -423,15 +522,18 @@ def main():
         for _ in range(args.steps):
             e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e_a.record()
-            info = step()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in solvers]
+            info = step(ev=ev)
             e_b.record()
-            per_step.append((e_a, e_b, info))
+            per_step.append((e_a, e_b, info, ev))
         ev1.record()
         torch.cuda.synchronize()
         barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, device="cuda")
     launches = sum(s.kernel_launches() for s in solvers) - launches0
-    step_ms = [a.elapsed_time(b) for a, b, _ in per_step]
+    step_ms = [a.elapsed_time(b) for a, b, _, _ in per_step]
+    # per solve (call to result ready on its stream), per degree, over the timed steps
+    solve_ms = {p: [ev[i][0].elapsed_time(ev[i][1]) for _, _, _, ev in per_step] for i, p in enumerate(degrees)}
     iters = [x[0] for x in per_step[-1][2]]
     rels = [x[1] for x in per_step[-1][2]]
     value = job_value(world, total_dof, args.steps, ms)
@@ -453,13 +555,15 @@ def main():
         step(which=handles["fp64"])
         torch.cuda.synchronize()
         e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in degrees]
         e_a.record()
-        info64 = step(which=handles["fp64"])
+        info64 = step(which=handles["fp64"], ev=ev64)
         e_b.record()
         torch.cuda.synchronize()
         ms64 = e_a.elapsed_time(e_b)
         plain = {"value": total_dof / (ms64 / 1e3), "unit": "DoF/s", "ms_per_step": ms64,
                  "iterations": [x[0] for x in info64], "final_relres": [x[1] for x in info64],
+                 "solve_ms": {str(p): round(ev64[i][0].elapsed_time(ev64[i][1]), 3) for i, p in enumerate(degrees)},
                  "solves": "sequential (the FP64 sweep is a grid-wide cooperative launch)"}
     # the mixed path solved one degree after another, for comparison with the FP64 figure
     mixed_seq = None
@@ -532,6 +636,29 @@ def main():
     roof["stages"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                       for k, v in stages.items()}
 
+    # error of both arms against the FP64 oracle, on the oracle-sized sample of the layout
+    oracle_err = None
+    if legs is not None:
+        sols = legs.solutions()
+        per = {}
+        for p in degrees:
+            ref = sols[p]
+            prob, opts = W.sipg_3x3(p, scale=1, smoother=args.smoother)
+            rec = {"unknowns": ref["ndof"], "oracle_iterations": ref["iterations"]}
+            for pr in precisions:
+                s = mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"], tau=opts["tau"],
+                                 delta=opts["delta"], precision=pr)
+                u, it, rel, _ = s.solve(ref["f"], tol=1e-8)
+                r_true = ref["f"] - s.apply("matvec", -1, u)
+                s.close()
+                rec[pr] = {"rel_error_vs_oracle": float(np.linalg.norm(u - ref["u"]) / np.linalg.norm(ref["u"])),
+                           "iterations": it, "true_relres": float(np.linalg.norm(r_true) / np.linalg.norm(ref["f"]))}
+            per[str(p)] = rec
+        oracle_err = {"sample": f"the same layout at 64/96 intervals (the oracle's size), p = {degrees}, the "
+                                f"oracle's load vector; ||u - u_oracle|| / ||u_oracle||, both stopped at 1e-8",
+                      "per_degree": per}
+        cpu = legs.baseline()
+
     line = {"metric": METRIC_OF[args.workload], "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
@@ -546,6 +673,9 @@ def main():
                        "tol": 1e-8, "iterations": iters, "final_relres": rels,
                        "step_ms_p50": float(np.percentile(step_ms, 50)),
                        "step_ms_p99": float(np.percentile(step_ms, 99)),
+                       "solve_ms": {str(p): {"p50": round(float(np.percentile(v, 50)), 3),
+                                             "p99": round(float(np.percentile(v, 99)), 3)}
+                                    for p, v in solve_ms.items()},
                        "l2": f"inputs larger than L2 ({dev_bytes / 1e9:.1f} GB of device data per step)",
                        "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1),
                        "solves": ("concurrent: one CUDA stream and host thread per degree"
@@ -553,10 +683,12 @@ def main():
                                   if concurrent else "sequential"),
                        "gs_cluster": None if args.sequential else cs},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "plain_fp64": plain,
-            "mixed_sequential": mixed_seq,
+            "mixed_sequential": mixed_seq, "oracle_error": oracle_err,
             "clocks": clk.summary()}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if legs is not None:
+        line["cpu_all_cores"] = legs.all_cores()
     if rank == 0:
         print(json.dumps(line), flush=True)
     for hs in handles.values():

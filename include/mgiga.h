@@ -63,16 +63,19 @@ enum { MGIGA_CONFORMING = 0, MGIGA_SIPG = 1 };
 enum { MGIGA_SMOOTHER_SCMS = 0, MGIGA_SMOOTHER_GS = 1, MGIGA_SMOOTHER_HYBRID = 2 };
 /* outer iteration: CG preconditioned by one V-cycle, or the V-cycle as solver */
 enum { MGIGA_OUTER_PCG = 0, MGIGA_OUTER_DIRECT = 1 };
-/* arithmetic of the smoothers inside the cycle (the outer CG is always FP64):
+/* arithmetic of the preconditioner (the outer CG is always FP64):
  * MGIGA_PREC_FP64: everything FP64 (the path checked against the oracle).
- * MGIGA_PREC_FP32: the fast-diagonalisation contractions and the Gauss-Seidel
- *   sweeps compute in FP32 (eigenvector matrices and a colour-ordered band copy
- *   stored in FP32); residuals, transfers, interface pieces, the coarse
- *   Cholesky solve and all CG vectors and inner products stay FP64, and CG
+ * MGIGA_PREC_FP32: inside the cycle, on every level but the coarsest, the
+ *   fast-diagonalisation contractions, the Gauss-Seidel sweeps (a colour-ordered
+ *   FP32 copy of the band), the interface-piece solves (FP32 inverses), the
+ *   residuals (FP32 band coefficients and FP32 sums; the SIPG cross-patch
+ *   terms stay FP64) and the transfers compute in FP32, while the vectors
+ *   between the stages are stored in FP64.  The coarse Cholesky solve, the
+ *   CG band product, all CG vectors and inner products stay FP64, and CG
  *   uses the flexible (Polak-Ribiere) beta.
  * MGIGA_PREC_TF32 / MGIGA_PREC_BF16: as FP32, with the fast-diagonalisation
- *   contractions on the tensor cores (tcgen05, TF32 or BF16 operands, FP32
- *   accumulation). */
+ *   contractions of large patch interiors on the tensor cores (tcgen05, TF32
+ *   or BF16 operands, FP32 accumulation). */
 enum { MGIGA_PREC_FP64 = 0, MGIGA_PREC_FP32 = 1, MGIGA_PREC_TF32 = 2, MGIGA_PREC_BF16 = 3 };
 
 /* One interface between side_a of patch_a and side_b of patch_b.
@@ -236,8 +239,10 @@ mgiga_status mgiga_apply_d(mgiga_handle* h, int op, int level, const double* a, 
  * cudaFree or other allocating routine and does not touch the handle's own
  * level buffers.  A level needing more scratch than that (about 1M local
  * coefficients) is rejected with MGIGA_EINVAL and a message giving both sizes.
- * The first call on a device looks up the array's device address on that
- * device; make that first call before any stream capture.  All calls share
+ * The call must run with the handle's device (the one current at
+ * mgiga_assemble) current, else it returns MGIGA_EINVAL.  The first call on a
+ * device looks up the array's device address on that device; make that first
+ * call before any stream capture.  All calls share
  * the array and it keeps the last call's contents: the zero guards are
  * cleared on every call.  Calls whose work overlaps on the GPU (other
  * streams, other handles, other threads) race on the array; serialise them.

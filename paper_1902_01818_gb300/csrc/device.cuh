@@ -90,6 +90,25 @@ struct FdSmall {
   const void* dinv;
 };
 
+// one CTA of the fused 2D fast diagonalisation on the tensor cores (fd_fused_tf32): the
+// 128 x 32 output tile (rb, cb) of  out = L (Rin Rt)  for one patch interior, where
+//   pass 0:  Rin = R (interiors of r), Rt = U_0,   L = U_1^T,  out * dinv -> X (FP32)
+//   pass 1:  Rin = X,                  Rt = U_0^T, L = U_1,    u_interior += tau out
+// Every operand is FP32, row-major with its contraction index contiguous, rows 16-byte
+// aligned and zero from the matrix width up to the pitch: rin[m * ldr + k] (n1 x n0),
+// bt[n * ldb + k] = Rt(k, n) (n0 x n0), lm[m * ldl + k] = L(m, k) (n1 x n1).
+struct FdFusedTask {
+  const float* rin;
+  const float* bt;
+  const float* lm;
+  const float* dinv;  // pass 0: n1 x n0, dinv[m * n0 + n]
+  float* xout;        // pass 0: X[m * ldx + n], zero in the padding columns
+  double* u;          // pass 1: u[ibase + m * N0 + n]
+  int64_t ibase;
+  int ldr, ldb, ldl, ldx, N0;
+  int n0, n1, rb, cb, mt, pass;
+};
+
 // scalar slots of the CG state in device memory
 enum { S_RZ = 0, S_PQ, S_ALPHA, S_RR, S_RZNEW, S_BETA, S_FF, S_TMP, S_RZOLD, S_COUNT };
 

@@ -19,6 +19,7 @@
 
 #include "device.cuh"
 #include "kernels.h"
+#include "ptx.cuh"
 
 namespace mgiga {
 namespace dev {
@@ -257,33 +258,92 @@ __global__ void __launch_bounds__(kTile) prolong_band(
   u[pos] += (double)s;
 }
 
+// Mode-wise transfers of 2D patches (the 1D knot-insertion matrices applied one
+// direction at a time, Sec. 4): a CTA owns a block of rows along xi_1 of the
+// output.  Restriction: the fine rows the block's children span are first
+// contracted along xi_0 into shared memory, t[i_1][I_0] = sum_{i_0} P_0[i_0, I_0]
+// (w r)[i_1][i_0], then along xi_1, f_c[I_1][I_0] = sum_{i_1} P_1[i_1, I_1] t[i_1][I_0];
+// prolongation the same with the parents.  ~2 (p + 2) products per output instead
+// of (p + 2)^2, the same summation order as restrict_band / prolong_band (so the
+// FP64 results are identical).  blocks: (patch, first row, end row, -).
+template <typename T>
+__global__ void __launch_bounds__(256) restrict_mw2(const int4* __restrict__ blocks, const PatchMeta* __restrict__ pc,
+                                                    const PatchMeta* __restrict__ pf, const XferMeta* __restrict__ xm,
+                                                    const int* __restrict__ ch_start, const double* __restrict__ ch_val,
+                                                    int cw, const double* __restrict__ r, const double* __restrict__ w,
+                                                    const int* __restrict__ c_l2g, double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char xsm[];
+  T* t = reinterpret_cast<T*>(xsm);
+  const int4 b = blocks[blockIdx.x];
+  const int k = b.x, I1a = b.y, I1b = b.z;
+  const PatchMeta mc = pc[k], mf = pf[k];
+  const XferMeta x0 = xm[k * 3], x1 = xm[k * 3 + 1];
+  const int N0f = mf.N[0], N1f = mf.N[1], N0c = mc.N[0];
+  const int lo = ch_start[x1.ch_off + I1a];
+  const int hi = min(N1f, ch_start[x1.ch_off + I1b - 1] + cw);
+  for (int e = threadIdx.x; e < (hi - lo) * N0c; e += blockDim.x) {
+    const int ii = e / N0c, I0 = e - ii * N0c;
+    const int s0 = ch_start[x0.ch_off + I0];
+    const double* cv = ch_val + (x0.ch_off + I0) * (int64_t)cw;
+    const int64_t rowb = mf.off + (int64_t)N0f * (lo + ii);
+    T acc = 0;
+    for (int t0 = 0; t0 < cw && s0 + t0 < N0f; ++t0) {
+      const int64_t fp = rowb + s0 + t0;
+      acc = fma((T)cv[t0], (T)(w ? w[fp] * r[fp] : r[fp]), acc);
+    }
+    t[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < (I1b - I1a) * N0c; e += blockDim.x) {
+    const int dI = e / N0c, I0 = e - dI * N0c, I1 = I1a + dI;
+    const int64_t pos = mc.off + (int64_t)I1 * N0c + I0;
+    if (c_l2g[pos] < 0) { out[pos] = 0.0; continue; }
+    const int s1 = ch_start[x1.ch_off + I1];
+    const double* cv = ch_val + (x1.ch_off + I1) * (int64_t)cw;
+    T acc = 0;
+    for (int t1 = 0; t1 < cw && s1 + t1 < hi; ++t1) acc = fma((T)cv[t1], t[(s1 + t1 - lo) * N0c + I0], acc);
+    out[pos] = (double)acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) prolong_mw2(const int4* __restrict__ blocks, const PatchMeta* __restrict__ pf,
+                                                   const PatchMeta* __restrict__ pc, const XferMeta* __restrict__ xm,
+                                                   const int* __restrict__ par_start, const double* __restrict__ par_val,
+                                                   int pw, const double* __restrict__ e, double* __restrict__ u) {
+  extern __shared__ __align__(16) unsigned char xsm[];
+  T* s = reinterpret_cast<T*>(xsm);
+  const int4 b = blocks[blockIdx.x];
+  const int k = b.x, i1a = b.y, i1b = b.z;
+  const PatchMeta mf = pf[k], mc = pc[k];
+  const XferMeta x0 = xm[k * 3], x1 = xm[k * 3 + 1];
+  const int N0f = mf.N[0], N0c = mc.N[0], N1c = mc.N[1];
+  const int lo = par_start[x1.par_off + i1a];
+  const int hi = min(N1c, par_start[x1.par_off + i1b - 1] + pw);
+  for (int q = threadIdx.x; q < (hi - lo) * N0f; q += blockDim.x) {
+    const int ii = q / N0f, i0 = q - ii * N0f;
+    const int s0 = par_start[x0.par_off + i0];
+    const double* pv = par_val + (x0.par_off + i0) * (int64_t)pw;
+    const int64_t rowb = mc.off + (int64_t)N0c * (lo + ii);
+    T acc = 0;
+    for (int t0 = 0; t0 < pw && s0 + t0 < N0c; ++t0) acc = fma((T)pv[t0], (T)e[rowb + s0 + t0], acc);
+    s[q] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < (i1b - i1a) * N0f; q += blockDim.x) {
+    const int di = q / N0f, i0 = q - di * N0f, i1 = i1a + di;
+    const int s1 = par_start[x1.par_off + i1];
+    const double* pv = par_val + (x1.par_off + i1) * (int64_t)pw;
+    T acc = 0;
+    for (int t1 = 0; t1 < pw && s1 + t1 < hi; ++t1) acc = fma((T)pv[t1], s[(s1 + t1 - lo) * N0f + i0], acc);
+    u[mf.off + (int64_t)i1 * N0f + i0] += (double)acc;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // a2: batched FP64 GEMM for the fast-diagonalisation contractions
 // ---------------------------------------------------------------------------
 constexpr int GBK = 16;
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-// Bounded wait for the completion of an mbarrier phase: false after `limit`
-// polls (the kernels use the default).
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long long limit = kMbarPolls) {
-  for (long long it = 0; it < limit; ++it) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(phase)
-        : "memory");
-    if (ok) return true;
-    __nanosleep(32);
-  }
-  return false;
-}
-
 
 __device__ __forceinline__ int64_t gcol(const GemmTask& g, int n) {
   return (int64_t)(n / g.ndiv) * g.nhi + (n % g.ndiv);
@@ -1439,6 +1499,7 @@ __global__ void axpby(int64_t n, double a, const double* __restrict__ x, double 
 // ---------------------------------------------------------------------------
 static thread_local long long g_launches = 0;
 long long launch_counter() { return g_launches; }
+void count_launch() { ++g_launches; }
 template <int D, int MODE>
 static void launch_band_p(int p, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
                           const double* band, int64_t nloc, const double* u, const double* f, double* out) {
@@ -1533,6 +1594,33 @@ void launch_prolong(int d, bool f32, int ntiles, cudaStream_t st, const Tile* ti
     if (f32) MG_PROLONG(3, float); else MG_PROLONG(3, double);
   }
 #undef MG_PROLONG
+}
+
+void launch_restrict_mw2(bool f32, int nblocks, int smem, cudaStream_t st, const int4* blocks, const PatchMeta* pc,
+                         const PatchMeta* pf, const XferMeta* xm, const int* ch_start, const double* ch_val, int cw,
+                         const double* r, const double* w, const int* c_l2g, double* out) {
+  if (nblocks == 0) return;
+  ++g_launches;
+  if (f32) restrict_mw2<float><<<nblocks, 256, smem, st>>>(blocks, pc, pf, xm, ch_start, ch_val, cw, r, w, c_l2g, out);
+  else restrict_mw2<double><<<nblocks, 256, smem, st>>>(blocks, pc, pf, xm, ch_start, ch_val, cw, r, w, c_l2g, out);
+}
+
+void launch_prolong_mw2(bool f32, int nblocks, int smem, cudaStream_t st, const int4* blocks, const PatchMeta* pf,
+                        const PatchMeta* pc, const XferMeta* xm, const int* par_start, const double* par_val, int pw,
+                        const double* e, double* u) {
+  if (nblocks == 0) return;
+  ++g_launches;
+  if (f32) prolong_mw2<float><<<nblocks, 256, smem, st>>>(blocks, pf, pc, xm, par_start, par_val, pw, e, u);
+  else prolong_mw2<double><<<nblocks, 256, smem, st>>>(blocks, pf, pc, xm, par_start, par_val, pw, e, u);
+}
+
+cudaError_t prepare_transfers_mw2() {
+  for (cudaError_t e : {cudaFuncSetAttribute(restrict_mw2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kXferSmemMax),
+                        cudaFuncSetAttribute(restrict_mw2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kXferSmemMax),
+                        cudaFuncSetAttribute(prolong_mw2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kXferSmemMax),
+                        cudaFuncSetAttribute(prolong_mw2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kXferSmemMax)})
+    if (e != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 int gemm_tile(int arith) { return arith == 1 ? 64 : 32; }

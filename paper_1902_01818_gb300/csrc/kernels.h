@@ -82,6 +82,16 @@ void launch_restrict(int d, bool f32, int ntiles, cudaStream_t st, const Tile* t
 void launch_prolong(int d, bool f32, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pf,
                     const PatchMeta* pc, const XferMeta* xm, const int* par_start, const double* par_val, int pw,
                     const double* e, double* u);
+// mode-wise 2D transfers: one CTA per block (patch, first row, end row) of output rows along xi_1,
+// the intermediate of the xi_0 pass in smem bytes of shared memory (at most kXferSmemMax)
+constexpr int kXferSmemMax = 96 * 1024;
+cudaError_t prepare_transfers_mw2();
+void launch_restrict_mw2(bool f32, int nblocks, int smem, cudaStream_t st, const int4* blocks, const PatchMeta* pc,
+                         const PatchMeta* pf, const XferMeta* xm, const int* ch_start, const double* ch_val, int cw,
+                         const double* r, const double* w, const int* c_l2g, double* out);
+void launch_prolong_mw2(bool f32, int nblocks, int smem, cudaStream_t st, const int4* blocks, const PatchMeta* pf,
+                        const PatchMeta* pc, const XferMeta* xm, const int* par_start, const double* par_val, int pw,
+                        const double* e, double* u);
 // arith 0: FP64 arithmetic (32 x 32 tiles), 1: FP32 arithmetic (64 x 64 tiles)
 int gemm_tile(int arith);
 // fused fast diagonalisation of small 2D patch interiors: one CTA per patch
@@ -128,6 +138,13 @@ void launch_axpby(int64_t n, cudaStream_t st, double a, const double* x, double 
 int red_blocks();
 // kernels enqueued by this host thread so far
 long long launch_counter();
+void count_launch();  // for launchers outside kernels.cu
+// fused 2D fast diagonalisation on the tensor cores (fd_fused.cu): two launches (pass 0, pass 1)
+// of one CTA per FdFusedTask; interiors up to fd_fused_max_rows() rows (n1)
+int fd_fused_smem(int mt);  // dynamic shared memory of tasks with mt 128-row tiles
+int fd_fused_max_rows();
+cudaError_t prepare_fd_fused();
+void launch_fd_fused(int ntasks, int smem, cudaStream_t st, const FdFusedTask* tasks, double tau, int* err);
 
 }  // namespace dev
 }  // namespace mgiga

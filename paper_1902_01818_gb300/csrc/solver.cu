@@ -105,6 +105,11 @@ struct DLevel {
   int* ch_start = nullptr;
   double* ch_val = nullptr;
   int cw = 0;
+  // mode-wise 2D transfers: row blocks of the coarse (restriction) / fine (prolongation) level
+  int4* xr_blocks = nullptr;
+  int xr_n = 0, xr_smem = 0;
+  int4* xp_blocks = nullptr;
+  int xp_n = 0, xp_smem = 0;
   // fast diagonalisation: GEMM steps
   GemmTask* fd_tasks = nullptr;
   GemmItem* fd_items = nullptr;
@@ -117,6 +122,9 @@ struct DLevel {
   int64_t rc_total = 0;
   int64_t *rc_eptr = nullptr, *rc_ibase = nullptr, *rc_off = nullptr;
   int *rc_n0 = nullptr, *rc_N0 = nullptr, *rc_ld = nullptr;
+  FdFusedTask* fd_fused[2] = {nullptr, nullptr};  // 2D TF32: two chained-contraction passes
+  int fd_fused_n[2] = {0, 0};
+  int fd_fused_smem = 0;
   FdSmall* fd_small = nullptr;                 // fused path (small 2D patches): one CTA per patch
   int fd_small_n = 0, fd_small_smem = 0;
   // pieces (interface pieces on levels >= 1, the coarse solve on level 0)
@@ -169,6 +177,7 @@ struct mgiga_handle {
   bool assembled = false;
   std::string err;
   cudaStream_t stream = nullptr;
+  int device = -1;          // the CUDA device current at mgiga_assemble (owns every buffer)
   bool own_stream = false;  // created by the library when the options give none
   cudaEvent_t legacy_done = nullptr;  // orders an owned stream after the legacy default stream
   std::unique_ptr<Arena> arena;
@@ -274,6 +283,55 @@ void build_transfer_tables(const Level& C, const Level& F, const Transfer& T, Ar
         for (int t = 0; t < cw; ++t) cv.push_back(lo + t < nf ? P[(size_t)(lo + t) * nc + I] : 0.0);
       }
     }
+  // 2D: row blocks of the mode-wise kernels, as many output rows (at most 4 coarse / 8 fine: enough
+  // CTAs for every SM) as keep the intermediate of the xi_0 pass within 32 KB (FP64), unless
+  // MGIGA_XFER_MW=0
+  const char* mw_env = std::getenv("MGIGA_XFER_MW");
+  if (F.d == 2 && !(mw_env && mw_env[0] == '0')) {
+    constexpr int kRowsR = 4, kRowsP = 8, kTarget = 32 * 1024;
+    std::vector<int4> rb, pb;
+    int rs = 0, pss = 0;
+    bool fits = true;
+    for (int k = 0; k < F.K && fits; ++k) {
+      const XferMeta& m0 = xm[k * 3];
+      const XferMeta& m1 = xm[k * 3 + 1];
+      const int N1f = F.N[k][1], N1c = C.N[k][1], N0f = F.N[k][0], N0c = C.N[k][0];
+      (void)m0;
+      auto span_r = [&](int a, int b) {  // fine rows spanned by the children of coarse rows [a, b)
+        return std::min(N1f, cs[m1.ch_off + b - 1] + cw) - cs[m1.ch_off + a];
+      };
+      auto span_p = [&](int a, int b) {  // coarse rows spanned by the parents of fine rows [a, b)
+        return std::min(N1c, ps[m1.par_off + b - 1] + pw) - ps[m1.par_off + a];
+      };
+      for (int a = 0; a < N1c;) {
+        int b = a + 1;
+        while (b < N1c && b - a < kRowsR && (int64_t)span_r(a, b + 1) * N0c * 8 <= kTarget) ++b;
+        const int bytes = span_r(a, b) * N0c * 8;
+        if (bytes > kXferSmemMax) fits = false;
+        rs = std::max(rs, bytes);
+        rb.push_back(make_int4(k, a, b, 0));
+        a = b;
+      }
+      for (int a = 0; a < N1f;) {
+        int b = a + 1;
+        while (b < N1f && b - a < kRowsP && (int64_t)span_p(a, b + 1) * N0f * 8 <= kTarget) ++b;
+        const int bytes = span_p(a, b) * N0f * 8;
+        if (bytes > kXferSmemMax) fits = false;
+        pss = std::max(pss, bytes);
+        pb.push_back(make_int4(k, a, b, 0));
+        a = b;
+      }
+    }
+    if (fits) {
+      CK(prepare_transfers_mw2());
+      dl.xr_blocks = A.upload(rb);
+      dl.xr_n = (int)rb.size();
+      dl.xr_smem = rs;
+      dl.xp_blocks = A.upload(pb);
+      dl.xp_n = (int)pb.size();
+      dl.xp_smem = pss;
+    }
+  }
   dl.xm = A.upload(xm);
   dl.par_start = A.upload(ps);
   dl.par_val = A.upload(pv);
@@ -521,6 +579,61 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   }
   for (auto& s : steps) add_step(s);
   (void)lvl;
+  // 2D TF32 with MGIGA_FD_CHAINED=1: the four steps as two launches of chained contractions
+  // (fd_fused_tf32), when every interior fits the kernel's tensor memory.  Not the default: on the
+  // benchmark layout its 16-wide K slabs, each behind a CTA barrier and an MMA-completion wait, make
+  // it latency-bound (finest level, p = 6: 0.130 ms against 0.091 ms for the four separate steps)
+  const char* chained_env = std::getenv("MGIGA_FD_CHAINED");
+  if (vec2d && chained_env && chained_env[0] == '1') {
+    bool fits = true;
+    for (int k = 0; k < L.K; ++k) fits = fits && fd[k].n[1] <= fd_fused_max_rows();
+    if (fits) {
+      std::vector<FdFusedTask> ft[2];
+      int mt_max = 1;
+      for (int k = 0; k < L.K; ++k) {
+        const int n0 = fd[k].n[0], n1 = fd[k].n[1];
+        if (n0 <= 0 || n1 <= 0) continue;
+        const int mt = (n1 + 127) / 128, nb = (n0 + 31) / 32;
+        mt_max = std::max(mt_max, mt);
+        for (int pass = 0; pass < 2; ++pass)
+          for (int rb = 0; rb < mt; ++rb)
+            for (int cb = 0; cb < nb; ++cb) {
+              FdFusedTask q{};
+              q.n0 = n0;
+              q.n1 = n1;
+              q.rb = rb;
+              q.cb = cb;
+              q.mt = mt;
+              q.pass = pass;
+              q.ldr = ld4(n0);
+              q.ldb = ld4(n0);
+              q.ldl = ld4(n1);
+              q.ldx = ld4(n0);
+              q.N0 = L.N[k][0];
+              q.ibase = L.off[k] + 1 + L.N[k][0];
+              if (pass == 0) {  // T = R U_0[:, cb], X = (U_1^T T) dinv
+                q.rin = vT + toffv[k][0];
+                q.bt = vU + voff[k][1];
+                q.lm = vU + voff[k][3];
+                q.dinv = reinterpret_cast<const float*>(dD) + toff[k];
+                q.xout = vT + toffv[k][2];
+              } else {  // T = X U_0^T[:, cb], u += tau U_1 T
+                q.rin = vT + toffv[k][2];
+                q.bt = vU + voff[k][0];
+                q.lm = vU + voff[k][2];
+                q.u = dl.u;
+              }
+              ft[pass].push_back(q);
+            }
+      }
+      CK(prepare_fd_fused());
+      for (int pass = 0; pass < 2; ++pass) {
+        dl.fd_fused[pass] = A.upload(ft[pass]);
+        dl.fd_fused_n[pass] = (int)ft[pass].size();
+      }
+      dl.fd_fused_smem = fd_fused_smem(mt_max);
+    }
+  }
   if (fdk <= 1) CK(prepare_gemm());
   // small 2D interiors: all four contractions of a patch in one CTA (shared memory), unless
   // MGIGA_FD_FUSE=0 (kept for testing the batched-GEMM path on small problems)
@@ -1116,6 +1229,11 @@ void run_fd(mgiga_handle* h, DLevel& d) {
   if (d.rc)
     launch_gather_interior_f32(d.rc_n, d.rc_total, h->stream, d.rc_eptr, d.rc_ibase, d.rc_n0, d.rc_N0, d.rc_off,
                                d.rc_ld, d.r, d.rc);
+  if (d.fd_fused_n[0] > 0) {
+    for (int pass = 0; pass < 2; ++pass)
+      launch_fd_fused(d.fd_fused_n[pass], d.fd_fused_smem, h->stream, d.fd_fused[pass], h->opt.tau, h->gs_err);
+    return;
+  }
   for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
 }
 
@@ -1187,8 +1305,12 @@ void restrict_to(mgiga_handle* h, int l, const double* r, bool cycle = false) {
   const Level& Lc = h->L[l - 1];
   DLevel& df = h->D[l];
   DLevel& dc = h->D[l - 1];
-  launch_restrict(Lc.d, cycle && df.arith >= 1, dc.ntiles, h->stream, dc.tiles, dc.patches, df.patches, df.xm, df.ch_start, df.ch_val,
-                  df.cw, r, df.weight, dc.loc2glob, dc.f);
+  if (df.xr_n > 0)
+    launch_restrict_mw2(cycle && df.arith >= 1, df.xr_n, df.xr_smem, h->stream, df.xr_blocks, dc.patches, df.patches,
+                        df.xm, df.ch_start, df.ch_val, df.cw, r, df.weight, dc.loc2glob, dc.f);
+  else
+    launch_restrict(Lc.d, cycle && df.arith >= 1, dc.ntiles, h->stream, dc.tiles, dc.patches, df.patches, df.xm,
+                    df.ch_start, df.ch_val, df.cw, r, df.weight, dc.loc2glob, dc.f);
   if (conforming(h)) launch_shared(dc.nsh, h->stream, dc.sh_ptr, dc.sh_pos, dc.f, nullptr, 1);
 }
 
@@ -1196,8 +1318,12 @@ void prolong_from(mgiga_handle* h, int l, const double* e, double* u, bool cycle
   const Level& Lf = h->L[l];
   DLevel& df = h->D[l];
   DLevel& dc = h->D[l - 1];
-  launch_prolong(Lf.d, cycle && df.arith >= 1, df.ntiles, h->stream, df.tiles, df.patches, dc.patches, df.xm, df.par_start, df.par_val,
-                 df.pw, e, u);
+  if (df.xp_n > 0)
+    launch_prolong_mw2(cycle && df.arith >= 1, df.xp_n, df.xp_smem, h->stream, df.xp_blocks, df.patches, dc.patches,
+                       df.xm, df.par_start, df.par_val, df.pw, e, u);
+  else
+    launch_prolong(Lf.d, cycle && df.arith >= 1, df.ntiles, h->stream, df.tiles, df.patches, dc.patches, df.xm,
+                   df.par_start, df.par_val, df.pw, e, u);
 }
 
 void coarse_solve(mgiga_handle* h) {
@@ -1417,6 +1543,7 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       h->own_stream = true;
     }
     if (!h->legacy_done) CK(cudaEventCreateWithFlags(&h->legacy_done, cudaEventDisableTiming));
+    CK(cudaGetDevice(&h->device));
     h->arena.reset(new Arena());
     Arena& A = *h->arena;
     A.stream = h->stream;
@@ -1626,11 +1753,9 @@ static __device__ __align__(256) double g_noalloc_scratch[MGIGA_NOALLOC_SCRATCH_
 static std::mutex g_noalloc_mutex;
 static double* g_noalloc_ptr[256] = {nullptr};
 
-// device address of the scratch array on the current device, looked up once
+// device address of the scratch array on device `dev` (current), looked up once
 // per device (the host-side name of the array is not a device address)
-static double* noalloc_scratch() {
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
+static double* noalloc_scratch(int dev) {
   if (dev < 0 || dev >= 256) throw CudaError("device index out of range");
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_ptr[dev]) {
@@ -1648,6 +1773,12 @@ mgiga_status mgiga_residual_noalloc_d(mgiga_handle* h, int level, const double* 
   if (level < 0 || level >= h->levels) return fail(h, MGIGA_EINVAL, "bad level");
   if (!f || !u || !out) return fail(h, MGIGA_EINVAL, "NULL vector");
   return guarded_call(h, [&]() -> mgiga_status {
+    // the scratch of the device that holds the handle's buffers: the call runs there only
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != h->device)
+      return fail(h, MGIGA_EINVAL,
+                  "current device " + std::to_string(cur) + " is not the handle's device " + std::to_string(h->device));
     after_legacy(h);
     LaunchScope scope(h);
     const Level& L = h->L[level];
@@ -1662,7 +1793,7 @@ mgiga_status mgiga_residual_noalloc_d(mgiga_handle* h, int level, const double* 
                   "level too large for the allocation-free residual: it needs " + std::to_string(need) +
                       " doubles of scratch, the fixed scratch holds " +
                       std::to_string((long long)MGIGA_NOALLOC_SCRATCH_DOUBLES));
-    double* base = noalloc_scratch();
+    double* base = noalloc_scratch(h->device);
     double* su = base + g;
     double* sf = base + g + n + g;
     double* sr = sf + n;
@@ -1737,6 +1868,7 @@ mgiga_status mgiga_vcycle(mgiga_handle* h, const double* r, double* z) {
 // PCG (Sec. 4) or the cycle as solver, on device-resident global vectors
 static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, double tol, int* iters,
                                double* final_relres) {
+  h->history.clear();  // a solve that fails early leaves its own (empty or partial) history
   LaunchScope scope(h);
   const int top = h->levels - 1;
   DLevel& d = h->D[top];
@@ -1758,7 +1890,6 @@ static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, do
   read_scal();
   const double ff = h->host_scal[S_FF];
   if (iters) *iters = 0;
-  h->history.clear();
   if (!std::isfinite(ff) || !std::isfinite(h->host_scal[S_RR]))
     return fail(h, MGIGA_EBREAKDOWN, "non-finite right-hand side or initial guess");
   if (!(ff > 0.0)) {

@@ -138,8 +138,8 @@ def _smooth_tol(precision, d):
 def test_benchmark_layout_finest_smoother(p, precision, chained, monkeypatch):
     """The finest level of the benchmark layout (192/288 intervals, interiors of
     190-292 per direction): by default the TF32 / BF16 modes run the tcgen05
-    contractions here (TF32: the chained passes, or the four separate steps with
-    MGIGA_FD_CHAINED=0), FP32 the SIMT tiles, FP64 the FP64 tiles."""
+    contractions here (TF32: the four separate steps, or the chained passes with
+    MGIGA_FD_CHAINED=1), FP32 the SIMT tiles, FP64 the FP64 tiles."""
     monkeypatch.setenv("MGIGA_FD_CHAINED", chained)
     prob, opts = W.sipg_3x3(p, scale=3, smoother="hybrid")
     err = _interior_smoother_check(prob, opts, precision, seed=20 + p)
@@ -154,3 +154,28 @@ def test_cube_finest_smoother_tensor_cores(precision, monkeypatch):
     prob, opts = W.cube_2x2x2(3, "sipg")
     err = _interior_smoother_check(prob, opts, precision, seed=31)
     assert err <= _smooth_tol(precision, 3), err
+
+
+@pytest.mark.parametrize("p", [2, 6])
+def test_benchmark_layout_finest_transfers(p):
+    """Restriction and prolongation between the two finest levels of the benchmark
+    layout (mode-wise kernels, FP64 apply) against the oracle's knot-insertion
+    matrix P (Sec. 4), element by element at 1e-13."""
+    from oracle import hierarchy
+    prob, opts = W.sipg_3x3(p, scale=3, smoother="hybrid")
+    lib = binding().Solver(prob, levels=0, smoother="hybrid", tau=opts["tau"], delta=opts["delta"],
+                           precision="fp32")
+    kn = hierarchy.level_knots(prob, lib.levels)
+    num_c = discretize.numbering(prob, kn[-2])
+    num_f = discretize.numbering(prob, kn[-1])
+    P = hierarchy.global_prolongation(prob, kn[-2], kn[-1], num_c, num_f)
+    rng = np.random.default_rng(40 + p)
+    r = rng.standard_normal(P.shape[0])
+    ref = P.T @ r
+    got = lib.apply("restrict", lib.levels - 1, r)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    e = rng.standard_normal(P.shape[1])
+    ref = P @ e
+    got = lib.apply("prolong", lib.levels - 1, e)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    lib.close()

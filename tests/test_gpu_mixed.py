@@ -215,7 +215,7 @@ def test_gauss_seidel_streamed_ring(cs, nbuf, monkeypatch):
 def test_tensor_core_smoother_every_level(name, precision, chained, monkeypatch):
     """The tcgen05 contractions on these small interiors: MGIGA_FD_TENSOR_MIN_N=1
     sends every level's fast diagonalisation to the tensor cores (2D TF32: the two
-    chained-contraction passes of fd_fused_tf32, or with MGIGA_FD_CHAINED=0 the
+    chained-contraction passes of fd_fused_tf32 with MGIGA_FD_CHAINED=1, else the
     four gemm_umma_tf32 steps; 3D TF32: gemm_umma_tf32; BF16: gemm_umma<BF16>;
     with MGIGA_FD_FUSE=0 the 2D levels leave the one-CTA SIMT path), one smoother
     application against the oracle's explicit interior solves at the rounding

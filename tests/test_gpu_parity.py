@@ -89,6 +89,25 @@ def test_transfers_every_level(name):
         assert _rel(lib.apply("prolong", l, e), P @ e) <= 1e-13, l
 
 
+@pytest.mark.parametrize("name", ["conf2d_p2", "sipg2d_p3", "sipg2d_p1", "single_patch_p4"])
+def test_transfers_per_output_kernels(name, monkeypatch):
+    """2D levels use the mode-wise transfer kernels by default; MGIGA_XFER_MW=0
+    keeps the per-output tensor-product kernels (the 3D path) under test in 2D."""
+    monkeypatch.setenv("MGIGA_XFER_MW", "0")
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    lib = binding().Solver(prob, levels=levels, smoother="hybrid", **opt)
+    orc = _pair(name, "hybrid")[2]
+    rng = np.random.default_rng(1)
+    for l in range(1, lib.levels):
+        P = orc.h["P"][l]
+        r = rng.standard_normal(P.shape[0])
+        assert _rel(lib.apply("restrict", l, r), P.T @ r) <= 1e-13, l
+        e = rng.standard_normal(P.shape[1])
+        assert _rel(lib.apply("prolong", l, e), P @ e) <= 1e-13, l
+    lib.close()
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_coarse_solve(name):
     prob, lib, orc = _pair(name, "hybrid")

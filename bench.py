@@ -119,6 +119,10 @@ def parse():
                     help="solve the degrees one after another (default: concurrently, a stream each)")
     ap.add_argument("--priority", default="degree", choices=["degree", "none"],
                     help="concurrent solves: higher stream priority for higher degrees (the longest solves)")
+    ap.add_argument("--mu", type=int, default=1, help="1: V-cycle, 2: W-cycle (Sec. 4)")
+    ap.add_argument("--nu", type=int, default=1, help="smoothing steps per level")
+    ap.add_argument("--outer", default="pcg", choices=["pcg", "direct"],
+                    help="pcg: the cycle preconditions CG; direct: the cycle is the solver")
     ap.add_argument("--gs-cluster", default="8",
                     help="Gauss-Seidel cluster size per degree (one value, or one per degree); "
                          "ignored with --sequential, which lets the library choose")
@@ -445,6 +449,7 @@ def main():
             # concurrent solves: 8-CTA clusters on large levels pack better into the processing clusters
             handles[pr].append(mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"],
                                             tau=opts["tau"], delta=opts["delta"], precision=pr,
+                                            mu=args.mu, nu=args.nu, outer=args.outer,
                                             stream=streams[(p, pr)].cuda_stream,
                                             gs_cluster=0 if args.sequential else c))
         s = handles[args.precision][-1]
@@ -464,6 +469,8 @@ def main():
     # concurrency is safe when no sweep needs the grid-wide (cooperative) kernel: the base colours
     # cover every DoF on every level (true for this layout; checked, not assumed)
     def coop_free(s, p, d):
+        if args.smoother == "scms":
+            return True  # no Gauss-Seidel sweep at all
         base = 2 * (p + 1) ** d
         return all(int(s.colours(l).max()) < base for l in range(1, s.levels))
 
@@ -665,7 +672,8 @@ def main():
             "dtype": {"fp32": "f32+f64", "tf32": "tf32+f32+f64", "bf16": "bf16+f32+f64"}.get(args.precision, "f64"),
             "data": "synthetic",
             "config": {"workload": workload_name(args),
-                       "degrees": degrees, "unknowns": ndofs, "smoother": args.smoother, "outer": "pcg",
+                       "degrees": degrees, "unknowns": ndofs, "smoother": args.smoother, "outer": args.outer,
+                       "cycle": {"mu": args.mu, "nu": args.nu},
                        "precision": {"fp32": "fp32 smoothers, fp64 CG/coarse",
                                      "tf32": "tf32 contractions on large levels, fp32 smoothers, fp64 CG/coarse",
                                      "bf16": "bf16 contractions on large levels, fp32 smoothers, fp64 CG/coarse"

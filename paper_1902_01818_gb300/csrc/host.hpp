@@ -87,6 +87,9 @@ struct Level {
   // operator: band[o * nloc + pos], o = sum_a (o_a + p) (2p+1)^a
   int nb = 0;
   Vec band;
+  // set-up on the GPU: the band is assembled on the device; the host part of the finest-level
+  // assembly leaves the SIPG terms within one patch here as (band index, value), in cell order
+  std::vector<std::pair<int64_t, double>> band_add;
   double nnz = 0.0;  // nonzero band coefficients (kept when the host band is released)
   // SIPG cross-patch couplings, CSR over rows x_row[i]
   std::vector<int64_t> x_row;
@@ -105,9 +108,12 @@ struct Level {
 
 // numbering / topology of a level from its knots
 void build_topology(const Problem& pr, Level& L);
-// finest-level assembly: patch stiffness + SIPG interface terms into L.band / x-blocks
-void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec, 3>>& fine_knots);
-// zero Dirichlet rows and columns of band and cross blocks
+// finest-level assembly: patch stiffness + SIPG interface terms into L.band / x-blocks; with
+// stiffness = false only the interface terms (L.band stays empty; the terms within one patch go to
+// L.band_add, the band being assembled on the GPU)
+void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec, 3>>& fine_knots,
+                   bool stiffness = true);
+// zero Dirichlet rows and columns of the band (when present on the host) and of the cross blocks
 void apply_dirichlet(Level& L);
 // load vector in global order
 void assemble_load(const Problem& pr, const Level& L, double (*f)(const double*, void*), void* ctx,
@@ -119,8 +125,9 @@ struct Transfer {
   std::vector<std::array<Vec, 3>> P;  // per patch, per direction
 };
 Transfer build_transfer(const Level& C, const Level& F);
-// Galerkin coarse operator A_c = P^T A_f P (band and cross blocks)
-void galerkin(const Level& F, const Transfer& T, Level& C);
+// Galerkin coarse operator A_c = P^T A_f P (band and cross blocks; band = false: the cross blocks
+// only, the band being formed on the GPU)
+void galerkin(const Level& F, const Transfer& T, Level& C, bool band = true);
 
 // ---------------------------------------------------------------------------
 // Smoother data

@@ -626,7 +626,8 @@ static void interface_terms(const Problem& pr, Level& L, const Interface& f,
               o += (ic - ir + p) * mul;
               mul *= 2 * p + 1;
             }
-            L.band[(size_t)o * L.nloc + r] += v;
+            if (L.band.empty()) L.band_add.push_back({(int64_t)o * L.nloc + r, v});
+            else L.band[(size_t)o * L.nloc + r] += v;
           } else {
             cross[((uint64_t)r << 32) | (uint64_t)c] += v;
           }
@@ -635,11 +636,17 @@ static void interface_terms(const Problem& pr, Level& L, const Interface& f,
   }
 }
 
-void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec, 3>>& fine_knots) {
+void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec, 3>>& fine_knots,
+                   bool stiffness) {
   const int W = 2 * pr.p + 1;
   L.nb = pr.d == 2 ? W * W : W * W * W;
-  L.band.assign((size_t)L.nb * L.nloc, 0.0);
-  for (int k = 0; k < pr.K; ++k) patch_stiffness(pr, L, k);
+  L.band_add.clear();
+  if (stiffness) {
+    L.band.assign((size_t)L.nb * L.nloc, 0.0);
+    for (int k = 0; k < pr.K; ++k) patch_stiffness(pr, L, k);
+  } else {
+    Vec().swap(L.band);
+  }
   std::unordered_map<uint64_t, double> cross;
   if (pr.coupling == 1)
     for (const auto& f : pr.ifaces) interface_terms(pr, L, f, fine_knots, cross);
@@ -672,7 +679,7 @@ void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec
 
 void apply_dirichlet(Level& L) {
   // offsets in parallel, the rows of one offset's column contiguous
-  for (int k = 0; k < L.K; ++k) {
+  for (int k = 0; k < L.K && L.band.size() == (size_t)L.nb * L.nloc; ++k) {
     const int64_t r0 = L.off[k], r1 = L.off[k + 1];
 #pragma omp parallel for schedule(static)
     for (int o = 0; o < L.nb; ++o) {

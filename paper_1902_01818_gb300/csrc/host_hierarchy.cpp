@@ -103,11 +103,12 @@ static void coarsen_band_dir(int d, int p, const std::array<int, 3>& Nin, const 
   }
 }
 
-void galerkin(const Level& F, const Transfer& T, Level& C) {
+void galerkin(const Level& F, const Transfer& T, Level& C, bool band) {
   const int d = F.d, p = F.p;
   C.nb = F.nb;
-  C.band.assign((size_t)C.nb * C.nloc, 0.0);
-  for (int k = 0; k < F.K; ++k) {
+  if (band) C.band.assign((size_t)C.nb * C.nloc, 0.0);
+  else Vec().swap(C.band);
+  for (int k = 0; k < F.K && band; ++k) {
     // patch band of level F
     const int64_t rows = F.off[k + 1] - F.off[k];
     Vec B((size_t)F.nb * rows);

@@ -20,6 +20,7 @@
 #include "device.cuh"
 #include "host.hpp"
 #include "kernels.h"
+#include "setup_gpu.hpp"
 
 using namespace mgiga;
 using namespace mgiga::dev;
@@ -1529,10 +1530,28 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       t_last = now;
     };
     const int lv = h->levels;
-    assemble_finest(h->pr, h->L);
-    tick("assembly", lv - 1);
-    galerkin_hierarchy(h->L, h->T);
-    tick("galerkin", 0);
+    // the level operators' bands are assembled on the GPU (stiffness, Galerkin products) unless the
+    // degree is beyond the device kernels or MGIGA_HOST_SETUP=1; the SIPG interface terms, the
+    // cross-patch blocks of every level and the transfers stay on the host
+    const char* host_env = std::getenv("MGIGA_HOST_SETUP");
+    const bool gpu_setup = gpu_setup_supported(h->pr) && !(host_env && host_env[0] == '1');
+    if (gpu_setup) {
+      Level& F = h->L[lv - 1];
+      assemble_fine(h->pr, F, h->pr.knots, /*stiffness=*/false);
+      apply_dirichlet(F);
+      h->T.assign(lv, Transfer{});
+      for (int l = lv - 1; l > 0; --l) {
+        h->T[l] = build_transfer(h->L[l - 1], h->L[l]);
+        galerkin(h->L[l], h->T[l], h->L[l - 1], /*band=*/false);
+        apply_dirichlet(h->L[l - 1]);
+      }
+      tick("interfaces", lv - 1);
+    } else {
+      assemble_finest(h->pr, h->L);
+      tick("assembly", lv - 1);
+      galerkin_hierarchy(h->L, h->T);
+      tick("galerkin", 0);
+    }
     // device: work runs on the caller's stream, or on a non-blocking stream
     // of the handle (the legacy default stream cannot be captured into
     // graphs, and a blocking stream under capture in one thread would fail
@@ -1550,6 +1569,24 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
     if (h->opt.precision == MGIGA_PREC_TF32 || h->opt.precision == MGIGA_PREC_BF16) CK(prepare_gemm_umma());
     A.budget = h->opt.hbm_budget;
     h->D.assign(lv, DLevel{});
+    std::vector<double*> dband(lv, nullptr);
+    if (gpu_setup) {
+      // device bands of every level, finest first, then copied to the host for the set-up steps
+      // that read them (interface-piece matrices, Gauss-Seidel blocks, FP32 copies)
+      for (int l = 0; l < lv; ++l) dband[l] = A.alloc<double>((size_t)h->L[l].nb * h->L[l].nloc);
+      gpu_assemble_finest(h->pr, h->L[lv - 1], dband[lv - 1], h->stream);
+      tick("gpu stiffness", lv - 1);
+      for (int l = lv - 1; l > 0; --l) gpu_galerkin_band(h->L[l], h->L[l - 1], h->T[l], dband[l], dband[l - 1], h->stream);
+      tick("gpu galerkin", 0);
+      for (int l = 0; l < lv; ++l) {
+        Level& L = h->L[l];
+        L.band.resize((size_t)L.nb * L.nloc);
+        CK(cudaMemcpyAsync(L.band.data(), dband[l], L.band.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+      }
+      CK(cudaStreamSynchronize(h->stream));
+      tick("download", 0);
+    }
     const int sm = h->opt.smoother;
     for (int l = 0; l < lv; ++l) {
       const Level& L = h->L[l];
@@ -1563,7 +1600,7 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       d.u = A.guarded(L.nloc, d.guard);
       d.f = A.guarded(L.nloc, d.guard);
       d.r = A.guarded(L.nloc, d.guard);
-      d.band = A.upload(L.band);
+      d.band = gpu_setup ? dband[l] : A.upload(L.band);
       if (d.arith >= 1 && l > 0) {  // FP32 copy for the residuals inside the mixed-precision cycle
         std::vector<float> b32(L.band.size() + 4, 0.0f);
         for (size_t i = 0; i < L.band.size(); ++i) b32[i] = (float)L.band[i];

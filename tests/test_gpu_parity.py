@@ -200,15 +200,16 @@ def test_pcg_iterates_and_iteration_count(name, smoother):
     # the residual history: initial (u = 0: exactly 1), per iteration, the confirmed one last
     h = lib.residual_history()
     assert len(h) == it_l + 1 and h[-1] == rel_l and abs(h[0] - 1.0) <= 1e-14
-    # entry by entry at 1e-6 relative plus 1e-12 (relative to ||f||, four orders below the 1e-8
-    # stopping threshold: two FP64 recursions with different summation orders drift apart by a
-    # few rounding units of ||A|| ||u|| per iteration); the last entries separately: the
-    # library stores the confirmed true residual there
+    # entry by entry at 1e-6 relative plus 1e-10 of ||f||: the iterates agree to 1e-10 (the bar
+    # above), and two FP64 recursions with different summation orders drift apart by that much
+    # near convergence (measured: 5e-12 of ||f|| at relative residuals ~1e-7 on the 3D SIPG case);
+    # near the 1e-8 stop that is 1% of an entry, so a wrong tail value still fails.  The last
+    # entries separately: the library stores the confirmed true residual there
     m = min(len(h), len(hist))
     dev = np.abs(np.asarray(h[:m - 1]) - np.asarray(hist[:m - 1]))
-    bound = 1e-6 * np.abs(np.asarray(hist[:m - 1])) + 1e-12
+    bound = 1e-6 * np.abs(np.asarray(hist[:m - 1])) + 1e-10
     assert np.all(dev <= bound), [(i, h[i], hist[i]) for i in np.nonzero(dev > bound)[0]]
-    assert abs(h[m - 1] - hist[m - 1]) <= 1e-3 * hist[m - 1] + 1e-12, (h[m - 1], hist[m - 1])
+    assert abs(h[m - 1] - hist[m - 1]) <= 1e-3 * hist[m - 1] + 1e-10, (h[m - 1], hist[m - 1])
 
 
 @pytest.mark.parametrize("name", ["conf2d_p2", "sipg2d_p3"])

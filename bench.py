@@ -115,10 +115,17 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain-FP64 comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cube", type=int, default=1,
+                    help="add the 3D cube configurations (2x2x2 patches, 48 intervals, conforming and SIPG; mixed "
+                         "against plain FP64) as the line's 'cube' key: 1 p = 3 (keeps the default run short), "
+                         "2 p = 3..5, 0 none")
     ap.add_argument("--sequential", action="store_true",
                     help="solve the degrees one after another (default: concurrently, a stream each)")
     ap.add_argument("--priority", default="degree", choices=["degree", "none"],
                     help="concurrent solves: higher stream priority for higher degrees (the longest solves)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: the mixed handles pick their contraction engines and residual row blocking by "
+                         "timing at set-up (once per size bucket)")
     ap.add_argument("--mu", type=int, default=1, help="1: V-cycle, 2: W-cycle (Sec. 4)")
     ap.add_argument("--nu", type=int, default=1, help="smoothing steps per level")
     ap.add_argument("--outer", default="pcg", choices=["pcg", "direct"],
@@ -127,6 +134,14 @@ def parse():
                     help="Gauss-Seidel cluster size per degree (one value, or one per degree); "
                          "ignored with --sequential, which lets the library choose")
     return ap.parse_args()
+
+
+_T0 = time.perf_counter()
+
+
+def progress(msg):
+    """A timestamped progress line on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def dist_env():
@@ -222,7 +237,10 @@ def oracle_job(kind, p, scale, smoother):
     excluded); kind 'solution': the oracle's load vector and its PCG solution to 1e-8."""
     from oracle import discretize, mg
     from paper_1902_01818_gb300 import workloads as W
-    prob, opts = W.sipg_3x3(p, scale=scale, smoother=smoother)
+    if isinstance(scale, str):  # a cube sample: scale = coupling, 12 intervals
+        prob, opts = W.cube_2x2x2(p, scale, n=12)
+    else:
+        prob, opts = W.sipg_3x3(p, scale=scale, smoother=smoother)
     t0 = time.perf_counter()
     M = mg.Multigrid(prob, smoother=opts["smoother"], tau=opts["tau"], delta=opts["delta"])
     f = discretize.assemble_load(prob, prob["knots"], M.h["num"][-1], W.source_sinprod)
@@ -253,8 +271,14 @@ class OracleLegs:
             os.environ[v] = "1"
         self.args = args
         self.ncpu = os.cpu_count() or 1
-        self.pool = cf.ProcessPoolExecutor(max_workers=max(2, min(self.ncpu, len(degrees) + 1)),
+        self.pool = cf.ProcessPoolExecutor(max_workers=max(2, min(self.ncpu, len(degrees) + 7)),
                                            mp_context=mp.get_context("spawn"), initializer=_oracle_worker_init)
+        # the slowest first: the cube samples (3D, p up to 5), the 192/288 baseline, the 2D samples
+        self.cube = {}
+        if args.cube:
+            for c in ("conforming", "sipg"):
+                for p in ((5, 4, 3) if args.cube >= 2 else (3,)):
+                    self.cube[(c, p)] = self.pool.submit(oracle_job, "solution", p, c, "hybrid")
         self.base = self.pool.submit(oracle_job, "time", 2, args.scale, args.smoother)
         self.sol = {p: self.pool.submit(oracle_job, "solution", p, 1, args.smoother) for p in degrees}
 
@@ -268,6 +292,9 @@ class OracleLegs:
 
     def solutions(self):
         return {p: fu.result() for p, fu in self.sol.items()}
+
+    def cube_solutions(self):
+        return {k: fu.result() for k, fu in self.cube.items()}
 
     def all_cores(self):
         """One 64/96, p = 2 oracle solve per host core, all at once (after the GPU timing)."""
@@ -393,6 +420,67 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# 3D cube configurations (a key of the default line)
+# ---------------------------------------------------------------------------
+def cube_leg(args, mgiga, W, torch, oracle_sols, reps=3):
+    """For p = 3..5, conforming and SIPG, 48 intervals: the mixed (TF32 contractions, FP32 smoothers, FP64
+    CG) and the plain FP64 solves to 1e-8 one after another, each timed with CUDA events over `reps` solves
+    after one warm-up (inputs resident); errors of both against the FP64 oracle on the 12-interval sample."""
+    out, tot = {}, {"tf32": [0, 0.0], "fp64": [0, 0.0]}
+    st = torch.cuda.current_stream()
+    for c in ("conforming", "sipg"):
+        for p in ((3, 4, 5) if args.cube >= 2 else (3,)):
+            prob, o = W.cube_2x2x2(p, c)
+            rec = {}
+            for pr in ("tf32", "fp64"):
+                progress(f"cube {c} p = {p} {pr}")
+                t0 = time.perf_counter()
+                s = mgiga.Solver(prob, levels=0, smoother=o["smoother"], tau=o["tau"], delta=o["delta"], precision=pr,
+                                 stream=st.cuda_stream)
+                setup = time.perf_counter() - t0
+                f = torch.from_numpy(s.load_sinprod()).cuda()
+                u = torch.zeros_like(f)
+                times = []
+                for i in range(reps + 1):
+                    u.zero_()
+                    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ea.record(st)
+                    it, rel, _ = s.solve_d(f, u, tol=1e-8)
+                    eb.record(st)
+                    torch.cuda.synchronize()
+                    if i:
+                        times.append(ea.elapsed_time(eb))
+                fh = f.cpu().numpy()
+                r_true = fh - s.apply("matvec", -1, u.cpu().numpy())
+                n = s.ndof()
+                s.close()
+                med = float(np.median(times))
+                tot[pr][0] += n
+                tot[pr][1] += med
+                rec[pr] = {"value": n / (med / 1e3), "solve_ms_p50": round(med, 3),
+                           "solve_ms_p99": round(float(np.percentile(times, 99)), 3), "iterations": it,
+                           "true_relres": float(np.linalg.norm(r_true) / np.linalg.norm(fh)), "setup_s": round(setup, 1)}
+            rec["unknowns"] = n
+            ref = oracle_sols.get((c, p)) if oracle_sols else None
+            if ref is not None:  # the 12-interval sample, the oracle's load vector
+                ps, os_ = W.cube_2x2x2(p, c, n=12)
+                for pr in ("tf32", "fp64"):
+                    s = mgiga.Solver(ps, levels=0, smoother=os_["smoother"], tau=os_["tau"], delta=os_["delta"],
+                                     precision=pr)
+                    uu, it, rel, _ = s.solve(ref["f"], tol=1e-8)
+                    s.close()
+                    rec[pr]["rel_error_vs_oracle"] = float(np.linalg.norm(uu - ref["u"]) / np.linalg.norm(ref["u"]))
+                rec["oracle_sample"] = {"intervals": 12, "unknowns": ref["ndof"], "oracle_iterations": ref["iterations"]}
+            out[f"{c}_p{p}"] = rec
+    return {"workload": "[0,1]^3 as 2x2x2 trilinear patches, jitter 0.05, 48 intervals, hybrid smoother, PCG to 1e-8",
+            "solves": f"one at a time, median of {reps} after a warm-up, inputs resident",
+            "mixed": {"value": tot["tf32"][0] / (tot["tf32"][1] / 1e3), "unit": "DoF/s",
+                      "precision": "tf32 contractions (FP32 SIMT on these 49-51 interiors), fp32 smoothers, fp64 CG"},
+            "plain_fp64": {"value": tot["fp64"][0] / (tot["fp64"][1] / 1e3), "unit": "DoF/s"},
+            "per_config": out}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -450,6 +538,7 @@ def main():
             handles[pr].append(mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"],
                                             tau=opts["tau"], delta=opts["delta"], precision=pr,
                                             mu=args.mu, nu=args.nu, outer=args.outer,
+                                            autotune=bool(args.autotune) and pr != "fp64",
                                             stream=streams[(p, pr)].cuda_stream,
                                             gs_cluster=0 if args.sequential else c))
         s = handles[args.precision][-1]
@@ -515,6 +604,7 @@ def main():
             stream.wait_event(done)
         return out
 
+    progress("warm-up")
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -537,6 +627,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, device="cuda")
+    progress(f"timed steps done: {ms / args.steps:.2f} ms per step")
     launches = sum(s.kernel_launches() for s in solvers) - launches0
     step_ms = [a.elapsed_time(b) for a, b, _, _ in per_step]
     # per solve (call to result ready on its stream), per degree, over the timed steps
@@ -556,6 +647,7 @@ def main():
     e2e = {"value": job_value(world, total_dof, 1, e2e_ms), "unit": "DoF/s",
            "h2d_bytes_per_step": int(2 * 8 * total_dof), "d2h_bytes_per_step": int(8 * total_dof)}
 
+    progress("end to end done")
     # plain FP64 comparison: same workload, FP64 smoothers
     plain = None
     if "fp64" in handles and args.precision != "fp64":
@@ -572,6 +664,7 @@ def main():
                  "iterations": [x[0] for x in info64], "final_relres": [x[1] for x in info64],
                  "solve_ms": {str(p): round(ev64[i][0].elapsed_time(ev64[i][1]), 3) for i, p in enumerate(degrees)},
                  "solves": "sequential (the FP64 sweep is a grid-wide cooperative launch)"}
+    progress("plain FP64 done")
     # the mixed path solved one degree after another, for comparison with the FP64 figure
     mixed_seq = None
     if concurrent:
@@ -638,6 +731,7 @@ def main():
         rec["kernel"] = names[st]
         rec["traffic"] = dram_traffic(st, degrees, args, f32)
         stages[st] = rec
+    progress("stage rooflines done")
     dom = max(stages, key=lambda k: stages[k]["share_weight_ms"])
     roof = dict(stages[dom])
     roof["stages"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
@@ -646,7 +740,9 @@ def main():
     # error of both arms against the FP64 oracle, on the oracle-sized sample of the layout
     oracle_err = None
     if legs is not None:
+        progress("waiting for the oracle's 2D solutions")
         sols = legs.solutions()
+        progress("oracle's 2D solutions in")
         per = {}
         for p in degrees:
             ref = sols[p]
@@ -673,7 +769,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload_name(args),
                        "degrees": degrees, "unknowns": ndofs, "smoother": args.smoother, "outer": args.outer,
-                       "cycle": {"mu": args.mu, "nu": args.nu},
+                       "cycle": {"mu": args.mu, "nu": args.nu}, "autotune": bool(args.autotune),
                        "precision": {"fp32": "fp32 smoothers, fp64 CG/coarse",
                                      "tf32": "tf32 contractions on large levels, fp32 smoothers, fp64 CG/coarse",
                                      "bf16": "bf16 contractions on large levels, fp32 smoothers, fp64 CG/coarse"
@@ -695,8 +791,19 @@ def main():
             "clocks": clk.summary()}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    for hs in handles.values():
+        for s in hs:
+            s.close()
+    handles = {}
+    if args.cube and args.workload == "sipg3x3" and rank == 0 and world == 1:
+        progress("waiting for the oracle's cube solutions")
+        csol = legs.cube_solutions() if legs is not None else None
+        progress("cube configurations")
+        line["cube"] = cube_leg(args, mgiga, W, torch, csol)
     if legs is not None:
+        progress("all-core oracle leg")
         line["cpu_all_cores"] = legs.all_cores()
+    progress("done")
     if rank == 0:
         print(json.dumps(line), flush=True)
     for hs in handles.values():

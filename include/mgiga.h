@@ -141,17 +141,26 @@ typedef struct {
  * (CTAs per patch) preferred by the patch-parallel Gauss-Seidel sweep of the
  * mixed path on large levels.  Automatic takes 16 (fastest when the handle has
  * the GPU to itself); when several handles solve concurrently on their own
- * streams, 8 packs better into the GPU's processing clusters. */
+ * streams, 8 packs better into the GPU's processing clusters.
+ * autotune: 1 = at mgiga_assemble, pick per level the contraction engine of the
+ * fast diagonalisation (batched SIMT tiles, tensor-core tiles, one CTA per
+ * patch) and the row blocking of the FP32 cycle residual by timing the
+ * candidates on the device, once per size bucket (a factor sqrt(2) in the
+ * interior size / the level's rows) for the process; later handles of a known
+ * bucket reuse the choice.  0 = the built-in rules.  The paper has no
+ * counterpart; the choice changes only the FP32 summation order. */
 typedef struct {
   int levels, smoother, nu, mu, outer, precision, max_iter;
   double tau, delta;
   size_t hbm_budget;
   void* stream;
   int gs_cluster;
+  int autotune;
 } mgiga_options;
 
 /* Fill `opts` with: levels 0, SCMS, nu 1, mu 1, PCG, FP64, max_iter 1000,
- * tau 1, delta 0.12, no budget, default stream, automatic cluster size. */
+ * tau 1, delta 0.12, no budget, default stream, automatic cluster size, no
+ * autotuning. */
 void mgiga_default_options(mgiga_options* opts);
 
 /* Validate the problem, build the DoF numbering, the piece decomposition and
@@ -197,6 +206,20 @@ mgiga_status mgiga_solve(mgiga_handle* h, const double* rhs, double* u, double t
                          int* iters, double* final_relres);
 mgiga_status mgiga_solve_d(mgiga_handle* h, const double* rhs, double* u, double tol,
                            int* iters, double* final_relres);
+
+/* Batched solves (many independent problems of uneven sizes, Sec. 4 PCG each): n distinct handles,
+ * rhs[i] / u[i] device vectors of handle i as in mgiga_solve_d (u[i]: initial guess in, solution
+ * out), one tolerance.  With the outer PCG iteration every solve runs as one graph with conditional
+ * nodes (no host round trip per iteration): all n are enqueued from the calling thread, on their
+ * handles' streams, before any is awaited; with MGIGA_BATCH_ONE_GRAPH the n solve graphs are the
+ * branches of a single graph launched once (rebuilt when the handles, vectors or tolerance change;
+ * without that support, or for handles with the direct outer iteration, the solves run as without
+ * the flag).  iters, final_relres, status (n entries each, may be NULL) receive each problem's
+ * results.  Returns MGIGA_OK when every solve converged, else the first failing status.  The
+ * handles must not be in use by other threads during the call. */
+enum { MGIGA_BATCH_ONE_GRAPH = 1 };
+mgiga_status mgiga_solve_batch_d(mgiga_handle* const* hs, int n, const double* const* rhs, double* const* u,
+                                 double tol, int flags, int* iters, double* final_relres, int* status);
 
 /* Single stages of the cycle on level `level` (0 = coarsest), for testing and
  * profiling.  Vectors are in the global DoF order of the level they live on.

@@ -7,14 +7,56 @@ upload) is timed separately from the solves; the solve figure is the unknowns
 of the whole batch over the wall time of one pass over it (inputs resident),
 with the per-problem solve times' p50/p99.
 
-    python -m paper_1902_01818_gb300.batch --problems 256 --workers 16 --reps 3
+    python -m paper_1902_01818_gb300.batch --problems 256 --reps 3 [--mode graph|streams|threads]
 
-prints one JSON line.
+prints one JSON line.  Modes: the whole batch as one graph launch (each problem's PCG loop a branch
+with conditional nodes), a graph per problem enqueued from one host thread, or a host thread per
+solve.
 """
 import concurrent.futures as cf
 import time
 
 import numpy as np
+
+
+def run_batch_device(problems, reps=1, precision="tf32", tol=1e-8, one_graph=True, setup_workers=16):
+    """The batch through mgiga_solve_batch_d: every solve one graph (no host round trip per
+    iteration), all enqueued from this thread; one_graph: all of them the branches of a single graph
+    launch.  Inputs resident on the device; returns a statistics dict."""
+    import torch
+
+    from . import mgiga, workloads as W
+    streams = [torch.cuda.Stream() for _ in problems]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=setup_workers) as ex:
+        solvers = list(ex.map(lambda a: mgiga.Solver(a[0][0], levels=a[0][1]["levels"], smoother=a[0][1]["smoother"],
+                                                     tau=a[0][1]["tau"], delta=a[0][1]["delta"], precision=precision,
+                                                     gs_cluster=a[0][1].get("gs_cluster", 8),
+                                                     stream=a[1].cuda_stream),
+                              zip(problems, streams)))
+    t_setup = time.perf_counter() - t0
+    rhs = [torch.from_numpy(W.random_vector(s.ndof(), int(rs), kind="normal")).cuda()
+           for s, (_p, _o, rs) in zip(solvers, problems)]
+    ndof = [s.ndof() for s in solvers]
+    passes = []
+    try:
+        for _ in range(reps + 1):  # the first pass builds the graphs
+            u = [torch.zeros_like(f) for f in rhs]
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            its, rels, sts = mgiga.solve_batch_d(solvers, rhs, u, tol=tol, one_graph=one_graph)
+            torch.cuda.synchronize()
+            passes.append(time.perf_counter() - a)
+    finally:
+        for s in solvers:
+            s.close()
+    best = min(passes[1:]) if reps > 0 else passes[0]
+    return {"problems": len(problems), "unknowns": int(sum(ndof)), "mode": "one graph" if one_graph else
+            "one graph per problem, one host thread", "reps": reps, "precision": precision, "setup_s": t_setup,
+            "first_pass_s": passes[0], "pass_s": passes[1:], "value": sum(ndof) / best,
+            "unit": "DoF/s (best pass, inputs resident)", "iterations_mean": float(np.mean(its)),
+            "iterations_max": int(max(its)), "max_final_relres": float(max(rels)),
+            "failed": int(sum(1 for x in sts if x != 0))}
 
 
 def run_batch(problems, workers=16, reps=1, precision="tf32", tol=1e-8, solver_factory=None,
@@ -73,9 +115,16 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--seed", type=int, default=401)
+    ap.add_argument("--mode", default="graph", choices=["graph", "streams", "threads"],
+                    help="graph: one graph launch for the whole batch; streams: a graph per problem, all "
+                         "enqueued from one thread; threads: a host thread per solve (mgiga_solve)")
     args = ap.parse_args(argv)
     probs = [W.batched_problem(args.seed + i) for i in range(args.problems)]
-    print(json.dumps(run_batch(probs, workers=args.workers, reps=args.reps, precision=args.precision)), flush=True)
+    if args.mode == "threads":
+        out = run_batch(probs, workers=args.workers, reps=args.reps, precision=args.precision)
+    else:
+        out = run_batch_device(probs, reps=args.reps, precision=args.precision, one_graph=args.mode == "graph")
+    print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

@@ -17,7 +17,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libmgiga.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HOST_SOURCES = ["host_spline.cpp", "host_assembly.cpp", "host_hierarchy.cpp", "host_problem.cpp"]
+HOST_SOURCES = ["host_spline.cpp", "host_assembly.cpp", "host_hierarchy.cpp", "host_problem.cpp", "tune.cpp"]
 DEVICE_SOURCES = ["kernels.cu", "fd_fused.cu", "setup_gpu.cu", "solver.cu"]
 
 

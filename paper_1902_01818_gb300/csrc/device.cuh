@@ -109,8 +109,17 @@ struct FdFusedTask {
   int n0, n1, rb, cb, mt, pass;
 };
 
-// scalar slots of the CG state in device memory
-enum { S_RZ = 0, S_PQ, S_ALPHA, S_RR, S_RZNEW, S_BETA, S_FF, S_TMP, S_RZOLD, S_COUNT };
+// scalar slots of the CG state in device memory (S_TOL, S_NF, S_MAXIT: the parameters of a
+// device-driven solve: tolerance, ||f||, iteration limit)
+enum { S_RZ = 0, S_PQ, S_ALPHA, S_RR, S_RZNEW, S_BETA, S_FF, S_TMP, S_RZOLD, S_TOL, S_NF, S_MAXIT, S_COUNT };
+
+// state of a device-driven PCG loop: iterations done, status (0 running, 1 converged, 2 iteration
+// limit, 3 breakdown), the relative residual of the last iteration, executions of the confirming
+// true residual and of the second half of an iteration
+struct CgLoopState {
+  int it, status, nconf, ncont;
+  double rel;
+};
 
 }  // namespace dev
 }  // namespace mgiga

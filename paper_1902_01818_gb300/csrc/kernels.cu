@@ -1475,6 +1475,111 @@ __global__ void cg_update_p(int64_t n, double* __restrict__ p, const double* __r
     p[i] = fma(beta, p[i], z[i]);
 }
 
+// Device-side control of the PCG loop (Sec. 4, the stopping rule with the recursive residual,
+// confirmed by the true one), one thread, after the first half of an iteration: records the
+// relative residual, and sets the conditions of the graph's loop (hloop), of the true-residual
+// confirmation (hconf) and of the second half of the iteration (hcont)
+__global__ void cg_ctl_a(const double* __restrict__ scal, CgLoopState* st, double* hist,
+                         cudaGraphConditionalHandle hloop, cudaGraphConditionalHandle hconf,
+                         cudaGraphConditionalHandle hcont) {
+  const int it = ++st->it;
+  const double pq = scal[S_PQ];
+  const double rel = sqrt(scal[S_RR]) / scal[S_NF];
+  hist[it] = rel;
+  st->rel = rel;
+  if (!(pq > 0.0) || !isfinite(rel)) {
+    st->status = 3;
+    cudaGraphSetConditional(hloop, 0);
+    cudaGraphSetConditional(hconf, 0);
+    cudaGraphSetConditional(hcont, 0);
+    return;
+  }
+  if (rel <= scal[S_TOL]) {
+    st->nconf++;
+    cudaGraphSetConditional(hconf, 1);
+    cudaGraphSetConditional(hcont, 0);  // decided by cg_ctl_c
+    return;
+  }
+  cudaGraphSetConditional(hconf, 0);
+  if (it >= (int)scal[S_MAXIT]) {
+    st->status = 2;
+    cudaGraphSetConditional(hloop, 0);
+    cudaGraphSetConditional(hcont, 0);
+  } else {
+    st->ncont++;
+    cudaGraphSetConditional(hcont, 1);
+  }
+}
+
+// after the confirming true residual ||f - A x||^2 in scal[S_TMP]
+__global__ void cg_ctl_c(const double* __restrict__ scal, CgLoopState* st, double* hist,
+                         cudaGraphConditionalHandle hloop, cudaGraphConditionalHandle hcont) {
+  const double trel = sqrt(scal[S_TMP]) / scal[S_NF];
+  if (trel <= scal[S_TOL]) {  // the history ends with the confirmed (true) residual
+    hist[st->it] = trel;
+    st->rel = trel;
+    st->status = 1;
+    cudaGraphSetConditional(hloop, 0);
+    cudaGraphSetConditional(hcont, 0);
+  } else if (st->it >= (int)scal[S_MAXIT]) {
+    st->status = 2;
+    cudaGraphSetConditional(hloop, 0);
+    cudaGraphSetConditional(hcont, 0);
+  } else {
+    st->ncont++;
+    cudaGraphSetConditional(hcont, 1);
+  }
+}
+
+// before the loop of a solve that runs as one graph: ||f||^2 in scal[S_FF], ||f - A u0||^2 in
+// scal[S_RR]; decides between a non-finite input (status 4), a zero right-hand side (status 5, the
+// solution is zero: hzero), an initial guess that meets the rule (status 1), the iteration limit 0
+// (status 2) and the iteration (hgo: the first cycle; hloop: the loop)
+__global__ void cg_ctl_0(double* scal, CgLoopState* st, double* hist, cudaGraphConditionalHandle hzero,
+                         cudaGraphConditionalHandle hgo, cudaGraphConditionalHandle hloop) {
+  const double ff = scal[S_FF], rr = scal[S_RR];
+  cudaGraphSetConditional(hzero, 0);
+  cudaGraphSetConditional(hgo, 0);
+  cudaGraphSetConditional(hloop, 0);
+  if (!isfinite(ff) || !isfinite(rr)) {
+    st->status = 4;
+    return;
+  }
+  if (!(ff > 0.0)) {
+    st->status = 5;
+    st->rel = 0.0;
+    hist[0] = 0.0;
+    cudaGraphSetConditional(hzero, 1);
+    return;
+  }
+  const double nf = sqrt(ff);
+  scal[S_NF] = nf;
+  const double rel = sqrt(rr) / nf;
+  hist[0] = rel;
+  st->rel = rel;
+  if (rel <= scal[S_TOL]) {
+    st->status = 1;
+    return;
+  }
+  if ((int)scal[S_MAXIT] <= 0) {
+    st->status = 2;
+    return;
+  }
+  cudaGraphSetConditional(hgo, 1);
+  cudaGraphSetConditional(hloop, 1);
+}
+
+__global__ void cg_loop_init(double* scal, CgLoopState* st, double tol, double nf, int maxit) {
+  scal[S_TOL] = tol;
+  if (nf > 0.0) scal[S_NF] = nf;
+  scal[S_MAXIT] = (double)maxit;
+  st->it = 0;
+  st->status = 0;
+  st->nconf = 0;
+  st->ncont = 0;
+  st->rel = 0.0;
+}
+
 __global__ void scatter_global(int64_t nloc, const int* __restrict__ l2g, const double* __restrict__ g,
                                double* __restrict__ loc) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nloc; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1526,22 +1631,23 @@ void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile
 }
 
 void launch_band_residual_f32(int d, int p, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
-                              const float* band32, int64_t nloc, const double* u, const double* f, double* out) {
+                              const float* band32, int64_t nloc, const double* u, const double* f, double* out,
+                              int g) {
   if (ntiles == 0) return;
   ++g_launches;
-  // four threads per row group unless the level alone fills the GPU with one
-  const bool split = nloc < 400000;
+  // g threads per row group; 0: four unless the level alone fills the GPU with one
+  if (g != 1 && g != 2 && g != 4) g = nloc < 400000 ? 4 : 1;
   constexpr int NG = kTile / kRowsF32;
   switch (p) {
 #define MG_LAUNCH(DD, PP, GG) \
   band_residual_f32<DD, PP, GG><<<ntiles, NG * GG, 0, st>>>(tiles, pm, band32, nloc, u, f, out)
-#define MG_CASE(PP)                                                  \
-  case PP:                                                           \
-    if (d == 2) {                                                    \
-      if (split) MG_LAUNCH(2, PP, 4); else MG_LAUNCH(2, PP, 1);      \
-    } else {                                                         \
-      if (split) MG_LAUNCH(3, PP, 4); else MG_LAUNCH(3, PP, 1);      \
-    }                                                                \
+#define MG_CASE(PP)                                                                              \
+  case PP:                                                                                       \
+    if (d == 2) {                                                                                \
+      if (g == 4) MG_LAUNCH(2, PP, 4); else if (g == 2) MG_LAUNCH(2, PP, 2); else MG_LAUNCH(2, PP, 1); \
+    } else {                                                                                     \
+      if (g == 4) MG_LAUNCH(3, PP, 4); else if (g == 2) MG_LAUNCH(3, PP, 2); else MG_LAUNCH(3, PP, 1); \
+    }                                                                                            \
     break;
     MG_CASE(1) MG_CASE(2) MG_CASE(3) MG_CASE(4) MG_CASE(5) MG_CASE(6) MG_CASE(7) MG_CASE(8)
 #undef MG_CASE
@@ -1868,6 +1974,29 @@ void launch_cg_xr(int64_t n, cudaStream_t st, double* x, double* r, const double
                   const double* w, double* partials, double* scal, unsigned int* counter) {
   ++g_launches;
   cg_update_xr<<<kRedBlocks, 256, 0, st>>>(n, x, r, p, q, w, partials, scal, counter);
+}
+
+void launch_cg_ctl_a(cudaStream_t st, const double* scal, CgLoopState* state, double* hist,
+                     unsigned long long hloop, unsigned long long hconf, unsigned long long hcont) {
+  ++g_launches;
+  cg_ctl_a<<<1, 1, 0, st>>>(scal, state, hist, hloop, hconf, hcont);
+}
+
+void launch_cg_ctl_c(cudaStream_t st, const double* scal, CgLoopState* state, double* hist,
+                     unsigned long long hloop, unsigned long long hcont) {
+  ++g_launches;
+  cg_ctl_c<<<1, 1, 0, st>>>(scal, state, hist, hloop, hcont);
+}
+
+void launch_cg_ctl_0(cudaStream_t st, double* scal, CgLoopState* state, double* hist, unsigned long long hzero,
+                     unsigned long long hgo, unsigned long long hloop) {
+  ++g_launches;
+  cg_ctl_0<<<1, 1, 0, st>>>(scal, state, hist, hzero, hgo, hloop);
+}
+
+void launch_cg_loop_init(cudaStream_t st, double* scal, CgLoopState* state, double tol, double nf, int maxit) {
+  ++g_launches;
+  cg_loop_init<<<1, 1, 0, st>>>(scal, state, tol, nf, maxit);
 }
 
 void launch_cg_p(int64_t n, cudaStream_t st, double* p, const double* z, const double* scal) {

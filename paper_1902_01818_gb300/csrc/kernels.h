@@ -69,8 +69,10 @@ void launch_gs_fill_phase(int e0, int n, int nx, const int* xent, cudaStream_t s
 void launch_band(int d, int p, int mode, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
                  const double* band, int64_t nloc, const double* u, const double* f, double* out);
 // out = f - A u with FP32 coefficients (band32: nb x nloc + 4 floats) and FP32 arithmetic
+// g: threads per row group (1, 2, 4; other values: the built-in rule)
 void launch_band_residual_f32(int d, int p, int ntiles, cudaStream_t st, const Tile* tiles, const PatchMeta* pm,
-                              const float* band32, int64_t nloc, const double* u, const double* f, double* out);
+                              const float* band32, int64_t nloc, const double* u, const double* f, double* out,
+                              int g = 0);
 void launch_cross(int mode, int nx, cudaStream_t st, const int64_t* x_row, const int* x_ptr, const int64_t* x_col,
                   const double* x_val, const double* u, double* out);
 void launch_shared(int nsh, cudaStream_t st, const int* sh_ptr, const int64_t* sh_pos, double* v, const double* f,
@@ -132,6 +134,16 @@ void launch_dot(int64_t n, cudaStream_t st, const double* a, const double* b, co
 void launch_cg_xr(int64_t n, cudaStream_t st, double* x, double* r, const double* p, const double* q,
                   const double* w, double* partials, double* scal, unsigned int* counter);
 void launch_cg_p(int64_t n, cudaStream_t st, double* p, const double* z, const double* scal);
+// device-driven PCG loop: control kernels that set the conditions of the loop's graph nodes
+// (handles are cudaGraphConditionalHandle values)
+void launch_cg_ctl_a(cudaStream_t st, const double* scal, CgLoopState* state, double* hist,
+                     unsigned long long hloop, unsigned long long hconf, unsigned long long hcont);
+void launch_cg_ctl_c(cudaStream_t st, const double* scal, CgLoopState* state, double* hist,
+                     unsigned long long hloop, unsigned long long hcont);
+void launch_cg_ctl_0(cudaStream_t st, double* scal, CgLoopState* state, double* hist, unsigned long long hzero,
+                     unsigned long long hgo, unsigned long long hloop);
+// tolerance and iteration limit of the next device-driven solve (nf > 0: also ||f||), state reset
+void launch_cg_loop_init(cudaStream_t st, double* scal, CgLoopState* state, double tol, double nf, int maxit);
 void launch_scatter(int64_t nloc, cudaStream_t st, const int* l2g, const double* g, double* loc);
 void launch_gather(int ndof, cudaStream_t st, const int64_t* owner, const double* loc, double* g);
 void launch_axpby(int64_t n, cudaStream_t st, double a, const double* x, double b, double* y);

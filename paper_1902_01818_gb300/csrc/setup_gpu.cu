@@ -63,7 +63,8 @@ struct AsmArgs {
   const double* ctrl;
   const PatchMeta* pm;
   const int* cta_ptr;      // CTA prefix over the patches for the launched colour (K + 1)
-  double* band;
+  double* bt;              // the band accumulated row-major, bt[row * nb + o] (an element's entries of
+                           // one row share cache lines), transposed into the offset-major band at the end
   int64_t nloc;
   int c0, c1, c2;          // the colour: element index residues modulo p + 1
 };
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(128) stiffness_2d(AsmArgs a) {
     }
     const int64_t row = pm.off + (s0 + l0) + (int64_t)pm.N[0] * (s1 + l1);
     const int o = (m0 - l0 + P) + W * (m1 - l1 + P);
-    a.band[(int64_t)o * a.nloc + row] += s;
+    a.bt[row * (W * W) + o] += s;
   }
 }
 
@@ -288,12 +289,12 @@ __global__ void __launch_bounds__(256) stiffness_3d(AsmArgs a) {
         {  // (l, m)
           const int64_t row = pm.off + (s0 + l0) + N0 * (s1 + l1) + N01 * (s2 + l2);
           const int o = (m0 - l0 + P) + W * (m1 - l1 + P) + W * W * (m2 - l2 + P);
-          a.band[(int64_t)o * a.nloc + row] += val;
+          a.bt[row * (W * W * W) + o] += val;
         }
         if (L12 != M12 || m0 != l0) {  // (m, l)
           const int64_t row = pm.off + (s0 + m0) + N0 * (s1 + m1) + N01 * (s2 + m2);
           const int o = (l0 - m0 + P) + W * (l1 - m1 + P) + W * W * (l2 - m2 + P);
-          a.band[(int64_t)o * a.nloc + row] += val;
+          a.bt[row * (W * W * W) + o] += val;
         }
       }
   }
@@ -310,6 +311,24 @@ __global__ void band_add(int64_t n, const int64_t* __restrict__ idx, const doubl
                          double* __restrict__ band) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) band[idx[i]] += val[i];
+}
+
+// band[o * nloc + r] = bt[r * nb + o], through 32 x 32 shared-memory tiles (both sides coalesced)
+__global__ void band_transpose(int nb, int64_t nloc, const double* __restrict__ bt, double* __restrict__ band) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int o0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int64_t r = r0 + j;
+    const int o = o0 + threadIdx.x;
+    tile[j][threadIdx.x] = (r < nloc && o < nb) ? bt[r * nb + o] : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int o = o0 + j;
+    const int64_t r = r0 + threadIdx.x;
+    if (o < nb && r < nloc) band[(int64_t)o * nloc + r] = tile[threadIdx.x][j];
+  }
 }
 
 // strong Dirichlet condition: band entries whose row or column is a Dirichlet function are zeroed
@@ -505,7 +524,8 @@ void gpu_assemble_finest(const Problem& pr, Level& F, double* band, cudaStream_t
   a.geo = dupload(geo, T.ptrs, st);
   a.ctrl = dupload(ctrl, T.ptrs, st);
   a.pm = dupload(pm, T.ptrs, st);
-  a.band = band;
+  double* bt = dalloc<double>((size_t)F.nb * F.nloc, T.ptrs, st);
+  a.bt = bt;
   a.nloc = F.nloc;
   // CTA prefixes of every colour (elements with index residues c modulo p + 1)
   const int ncol = d == 2 ? P1 * P1 : P1 * P1 * P1;
@@ -529,7 +549,7 @@ void gpu_assemble_finest(const Problem& pr, Level& F, double* band, cudaStream_t
       default: prepare_stiffness_3d<6>(); break;
     }
   }
-  SCK(cudaMemsetAsync(band, 0, (size_t)F.nb * F.nloc * sizeof(double), st));
+  SCK(cudaMemsetAsync(bt, 0, (size_t)F.nb * F.nloc * sizeof(double), st));
   for (int c = 0; c < ncol; ++c) {
     a.c0 = c % P1;
     a.c1 = (c / P1) % P1;
@@ -546,6 +566,10 @@ void gpu_assemble_finest(const Problem& pr, Level& F, double* band, cudaStream_t
     }
     SCK(cudaGetLastError());
   }
+  count_launch();
+  band_transpose<<<dim3((unsigned)((F.nloc + 31) / 32), (unsigned)((F.nb + 31) / 32)), dim3(32, 8), 0, st>>>(
+      F.nb, F.nloc, bt, band);
+  SCK(cudaGetLastError());
   // the SIPG terms within one patch (host, in cell order): merged per band entry, then added
   if (!F.band_add.empty()) {
     std::map<int64_t, double> m;

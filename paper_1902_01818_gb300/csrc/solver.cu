@@ -21,6 +21,7 @@
 #include "host.hpp"
 #include "kernels.h"
 #include "setup_gpu.hpp"
+#include "tune.hpp"
 
 using namespace mgiga;
 using namespace mgiga::dev;
@@ -111,6 +112,7 @@ struct DLevel {
   int xr_n = 0, xr_smem = 0;
   int4* xp_blocks = nullptr;
   int xp_n = 0, xp_smem = 0;
+  int res_g = 0;  // threads per row group of the FP32 cycle residual (0: the built-in rule)
   // fast diagonalisation: GEMM steps
   GemmTask* fd_tasks = nullptr;
   GemmItem* fd_items = nullptr;
@@ -195,10 +197,24 @@ struct mgiga_handle {
   double* host_scal = nullptr;                            // pinned
   cudaGraphExec_t g_iter_a = nullptr, g_iter_b = nullptr, g_vcycle = nullptr;
   long long g_iter_a_kernels = 0, g_iter_b_kernels = 0;
+  // device-driven PCG: the whole iteration loop as one graph with conditional nodes (a while loop
+  // around the first half of an iteration, an if for the confirming true residual and one for the
+  // second half), steered by control kernels; 0: not built yet, 1: built, -1: unavailable
+  cudaGraphExec_t g_solve = nullptr;
+  int device_loop = 0;
+  CgLoopState* loop_state = nullptr;
+  double* dhist = nullptr;
+  CgLoopState* host_state = nullptr;  // pinned
+  long long g_conf_kernels = 0, g_start_kernels = 0, g_go_kernels = 0;
+  cudaGraph_t g_solve_tmpl = nullptr;  // the solve graph (for batch graphs)
+  bool pending = false;                // a solve graph was launched and not yet finished
   long long launches = 0;  // kernels enqueued on the device by this handle
   std::vector<double> history;  // relative residuals of the last solve: initial, then per iteration
 
   ~mgiga_handle() {
+    if (g_solve) cudaGraphExecDestroy(g_solve);
+    if (g_solve_tmpl) cudaGraphDestroy(g_solve_tmpl);
+    if (host_state) cudaFreeHost(host_state);
     if (g_iter_a) cudaGraphExecDestroy(g_iter_a);
     if (g_iter_b) cudaGraphExecDestroy(g_iter_b);
     if (g_vcycle) cudaGraphExecDestroy(g_vcycle);
@@ -343,7 +359,9 @@ void build_transfer_tables(const Level& C, const Level& F, const Transfer& T, Ar
 }
 
 // interior fast diagonalisation as batched GEMM steps (Sec. 5 smoother on patch interiors)
-void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLevel& dl) {
+// engine: -1 the built-in rule; 0 the batched SIMT contractions; 1 the tensor cores (TF32 / BF16
+// modes); 2 the one-CTA-per-patch contractions (2D, when every interior fits shared memory)
+void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLevel& dl, int engine = -1) {
   const int d = L.d;
   std::vector<FDData> fd(L.K);
 #pragma omp parallel for schedule(dynamic)
@@ -356,7 +374,9 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
     for (int a = 0; a < d; ++a) max_n = std::max(max_n, fd[k].n[a]);
   int tensor_min_n = 160;
   if (const char* env = std::getenv("MGIGA_FD_TENSOR_MIN_N")) tensor_min_n = std::max(1, std::atoi(env));
-  const int fdk = dl.arith <= 1 ? dl.arith : (max_n >= tensor_min_n ? dl.arith : 1);
+  const int fdk = engine == 1 ? dl.arith
+                : engine >= 0 ? (dl.arith <= 1 ? dl.arith : 1)
+                : dl.arith <= 1 ? dl.arith : (max_n >= tensor_min_n ? dl.arith : 1);
   dl.fd_kind = fdk;
   // U pool
   Vec Upool;
@@ -585,7 +605,7 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   // benchmark layout its 16-wide K slabs, each behind a CTA barrier and an MMA-completion wait, make
   // it latency-bound (finest level, p = 6: 0.130 ms against 0.091 ms for the four separate steps)
   const char* chained_env = std::getenv("MGIGA_FD_CHAINED");
-  if (vec2d && chained_env && chained_env[0] == '1') {
+  if (vec2d && chained_env && chained_env[0] == '1' && engine <= 1) {
     bool fits = true;
     for (int k = 0; k < L.K; ++k) fits = fits && fd[k].n[1] <= fd_fused_max_rows();
     if (fits) {
@@ -641,7 +661,8 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   const char* fuse_env = std::getenv("MGIGA_FD_FUSE");
   int fuse_max_n = 48;
   if (const char* env = std::getenv("MGIGA_FD_FUSE_MAX_N")) fuse_max_n = std::max(1, std::atoi(env));
-  if (d == 2 && !(fuse_env && fuse_env[0] == '0')) {
+  if (engine == 2) fuse_max_n = 1 << 30;  // forced: whatever fits shared memory
+  if (d == 2 && !(fuse_env && fuse_env[0] == '0') && engine != 0 && engine != 1) {
     std::vector<FdSmall> fs;
     int smem = 0;
     bool fits = true;
@@ -1196,7 +1217,7 @@ void cycle_residual(mgiga_handle* h, int l, const double* u, const double* f, do
     residual(h, l, u, f, out);
     return;
   }
-  launch_band_residual_f32(L.d, L.p, d.ntiles, h->stream, d.tiles, d.patches, d.band32, d.nloc, u, f, out);
+  launch_band_residual_f32(L.d, L.p, d.ntiles, h->stream, d.tiles, d.patches, d.band32, d.nloc, u, f, out, d.res_g);
   launch_cross(0, d.nx, h->stream, d.x_row, d.x_ptr, d.x_col, d.x_val, u, out);
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, out, f, 0);
 }
@@ -1431,6 +1452,76 @@ mgiga_status guarded_call(mgiga_handle* h, F&& fn) {
   }
 }
 
+// device time (ms) of one application of `fn` on the handle's stream, after one warm-up
+template <class F>
+double time_on_stream(mgiga_handle* h, F&& fn) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  fn();
+  CK(cudaEventRecord(a, h->stream));
+  fn();
+  CK(cudaEventRecord(b, h->stream));
+  CK(cudaEventSynchronize(b));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  check_launch();
+  return ms;
+}
+
+// autotuned fast diagonalisation of level l: the contraction engine (batched SIMT tiles, tensor-core
+// tiles, one CTA per patch) with the shortest measured application for this size bucket; on a miss
+// every candidate is built and timed (the losers' device data stay allocated until mgiga_destroy)
+void tune_fd(mgiga_handle* h, const Level& L, int l, Arena& A, DLevel& d, bool verbose) {
+  int max_int = 1;
+  for (int k = 0; k < L.K; ++k) {
+    int64_t v = 1;
+    for (int a = 0; a < L.d; ++a) v *= std::max(0, L.N[k][a] - 2);
+    max_int = (int)std::max<int64_t>(max_int, v);
+  }
+  const TuneKey key{TUNE_FD, L.d, L.p, h->opt.precision, tune_bucket(max_int)};
+  std::vector<int> cand = {0};
+  if (d.arith >= 2) cand.push_back(1);
+  if (L.d == 2) cand.push_back(2);
+  int choice = -1;
+  if (!Tuner::instance().lookup(key, &choice)) {
+    std::vector<DLevel> built(cand.size(), d);
+    choice = Tuner::instance().choose(key, (int)cand.size(), [&](int i) -> double {
+      DLevel& t = built[(size_t)i];
+      if (t.fd_steps.empty() && !t.fd_small) {
+        build_fd(L, l, h->opt.delta, h->opt.tau, A, t, cand[(size_t)i]);
+        if (cand[(size_t)i] == 2 && !t.fd_small) return -1.0;  // does not fit one CTA
+      }
+      return time_on_stream(h, [&]() { run_fd(h, t); });
+    });
+    if (verbose) {
+      const auto ts = Tuner::instance().last_times();
+      std::fprintf(stderr, "mgiga: tune fd level %d (bucket %d): engine %d;", l, key.bucket, cand[(size_t)choice]);
+      for (size_t i = 0; i < ts.size(); ++i) std::fprintf(stderr, " %d: %.4f ms", cand[i], ts[i]);
+      std::fprintf(stderr, "\n");
+    }
+    d = built[(size_t)choice];
+    if (d.fd_steps.empty() && !d.fd_small) build_fd(L, l, h->opt.delta, h->opt.tau, A, d, cand[(size_t)choice]);
+    return;
+  }
+  build_fd(L, l, h->opt.delta, h->opt.tau, A, d, cand[(size_t)std::min<int>(choice, (int)cand.size() - 1)]);
+}
+
+// autotuned row blocking of the FP32 cycle residual of level l: 1, 2 or 4 threads per row group
+void tune_residual(mgiga_handle* h, const Level& L, int l, DLevel& d, bool verbose) {
+  const TuneKey key{TUNE_RESIDUAL, L.d, L.p, h->opt.precision, tune_bucket(L.nloc)};
+  const int gs[3] = {1, 2, 4};
+  const int choice = Tuner::instance().choose(key, 3, [&](int i) -> double {
+    d.res_g = gs[i];
+    return time_on_stream(h, [&]() { cycle_residual(h, l, d.u, d.f, d.r); });
+  });
+  d.res_g = gs[choice];
+  if (verbose) std::fprintf(stderr, "mgiga: tune residual level %d (bucket %d): %d threads per row group\n", l,
+                            key.bucket, d.res_g);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1452,6 +1543,7 @@ void mgiga_default_options(mgiga_options* o) {
   o->hbm_budget = 0;
   o->stream = nullptr;
   o->gs_cluster = 0;
+  o->autotune = 0;
 }
 
 double mgiga_source_sinprod(const double* x, void* ctx) {
@@ -1477,7 +1569,8 @@ mgiga_status mgiga_create(const mgiga_problem* problem, const mgiga_options* opt
     const mgiga_options& o = h->opt;
     if (o.smoother < 0 || o.smoother > 2 || o.nu < 1 || o.mu < 1 || o.mu > 2 || o.outer < 0 || o.outer > 1 ||
         o.precision < MGIGA_PREC_FP64 || o.precision > MGIGA_PREC_BF16 || o.max_iter < 0 || !(o.tau > 0.0) || !(o.delta > 0.0) || o.levels < 0 ||
-        !(o.gs_cluster == 0 || o.gs_cluster == 2 || o.gs_cluster == 4 || o.gs_cluster == 8 || o.gs_cluster == 16))
+        !(o.gs_cluster == 0 || o.gs_cluster == 2 || o.gs_cluster == 4 || o.gs_cluster == 8 || o.gs_cluster == 16) ||
+        o.autotune < 0 || o.autotune > 1)
       throw SetupError(MGIGA_EINVAL, "invalid options");
     h->stream = static_cast<cudaStream_t>(o.stream);
     const int lv = o.levels > 0 ? o.levels : auto_levels(h->pr);
@@ -1535,9 +1628,13 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
     // cross-patch blocks of every level and the transfers stay on the host
     const char* host_env = std::getenv("MGIGA_HOST_SETUP");
     const bool gpu_setup = gpu_setup_supported(h->pr) && !(host_env && host_env[0] == '1');
+    // 3D: the element stiffness stays on the host (the device kernel measured slower there: cube,
+    // 48 intervals, p = 5: 49 s against 38 s on 16 host cores); its Galerkin products run on the GPU
+    const char* s3_env = std::getenv("MGIGA_GPU_STIFFNESS_3D");  // the 3D device kernel, for testing
+    const bool gpu_stiffness = gpu_setup && (h->pr.d == 2 || (s3_env && s3_env[0] == '1'));
     if (gpu_setup) {
       Level& F = h->L[lv - 1];
-      assemble_fine(h->pr, F, h->pr.knots, /*stiffness=*/false);
+      assemble_fine(h->pr, F, h->pr.knots, /*stiffness=*/!gpu_stiffness);
       apply_dirichlet(F);
       h->T.assign(lv, Transfer{});
       for (int l = lv - 1; l > 0; --l) {
@@ -1574,12 +1671,20 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       // device bands of every level, finest first, then copied to the host for the set-up steps
       // that read them (interface-piece matrices, Gauss-Seidel blocks, FP32 copies)
       for (int l = 0; l < lv; ++l) dband[l] = A.alloc<double>((size_t)h->L[l].nb * h->L[l].nloc);
-      gpu_assemble_finest(h->pr, h->L[lv - 1], dband[lv - 1], h->stream);
-      tick("gpu stiffness", lv - 1);
+      if (gpu_stiffness) {
+        gpu_assemble_finest(h->pr, h->L[lv - 1], dband[lv - 1], h->stream);
+        tick("gpu stiffness", lv - 1);
+      } else {
+        const Level& F = h->L[lv - 1];
+        CK(cudaMemcpyAsync(dband[lv - 1], F.band.data(), F.band.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           h->stream));
+        tick("host stiffness", lv - 1);
+      }
       for (int l = lv - 1; l > 0; --l) gpu_galerkin_band(h->L[l], h->L[l - 1], h->T[l], dband[l], dband[l - 1], h->stream);
       tick("gpu galerkin", 0);
       for (int l = 0; l < lv; ++l) {
         Level& L = h->L[l];
+        if (l == lv - 1 && !gpu_stiffness) continue;  // assembled on the host
         L.band.resize((size_t)L.nb * L.nloc);
         CK(cudaMemcpyAsync(L.band.data(), dband[l], L.band.size() * sizeof(double), cudaMemcpyDeviceToHost,
                            h->stream));
@@ -1640,13 +1745,15 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       }
       tick("uploads", l);
       if (sm == MGIGA_SMOOTHER_SCMS || sm == MGIGA_SMOOTHER_HYBRID) {
-        build_fd(L, l, h->opt.delta, h->opt.tau, A, d);
+        if (h->opt.autotune) tune_fd(h, L, l, A, d, verbose);
+        else build_fd(L, l, h->opt.delta, h->opt.tau, A, d);
         tick("fd", l);
         build_pieces(h->pieces[l], L, A, d, false);
         tick("pieces", l);
       }
       if (sm == MGIGA_SMOOTHER_GS || sm == MGIGA_SMOOTHER_HYBRID) build_gs(h->pr, h->colours[l], L, A, d, h->opt.gs_cluster);
       tick("gs", l);
+      if (h->opt.autotune && d.band32) tune_residual(h, L, l, d, verbose);
     }
     const Level& Lf = h->L[lv - 1];
     const int64_t g = guard_of(Lf);
@@ -1902,10 +2009,233 @@ mgiga_status mgiga_vcycle(mgiga_handle* h, const double* r, double* z) {
   });
 }
 
+// A whole PCG solve (Sec. 4) as one graph with conditional nodes (CUDA 12.4+), reading the right-hand
+// side and the initial guess from the staging vectors in1 / in2 (global order) and leaving the
+// solution in in2:
+//   [scatter f, u; ||f||^2; r = f - A u; ||r||^2; cg_ctl_0]
+//   if (zero): [u = 0]                      (zero right-hand side)
+//   if (go):   [z = B r; (r, z); p = z]     (the first cycle)
+//   while (loop): [q = A p, alpha, x += alpha p, r -= alpha q, ||r||^2, cg_ctl_a]
+//                 if (confirm): [t = f - A x, ||t||^2, cg_ctl_c]   (the true residual)
+//                 if (cont):    [z = B r, beta, p = z + beta p]
+//   [gather u]
+// so that a solve makes no host round trip until its result.  Returns false (no error left pending)
+// when the runtime or the driver cannot build or instantiate it; the host-driven loop is used then.
+static void add_if(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraphConditionalHandle hc, cudaGraphNode_t* node,
+                   cudaGraph_t* body, cudaGraphConditionalNodeType type = cudaGraphCondTypeIf) {
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  CK(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &cp));
+  *body = cp.conditional.phGraph_out[0];
+}
+
+// the leaf of a graph captured from one stream (a chain)
+static cudaGraphNode_t chain_leaf(cudaGraph_t g) {
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  cudaGraphNode_t last = nullptr;
+  for (cudaGraphNode_t x : nodes) {
+    size_t nd = 0;
+    CK(cudaGraphNodeGetDependentNodes(x, nullptr, nullptr, &nd));
+    if (nd == 0) last = x;
+  }
+  return last;
+}
+
+static bool build_solve_graph(mgiga_handle* h) {
+  const int top = h->levels - 1;
+  DLevel& d = h->D[top];
+  cudaStream_t st = h->stream;
+  const double* w = d.weight;
+  const int64_t n = d.nloc;
+  double* r = d.f;
+  double* z = d.u;
+  cudaGraph_t G = nullptr;
+  bool ok = false;
+  const long long c0 = launch_counter();
+  const auto mode = cudaStreamCaptureModeThreadLocal;
+  try {
+    CK(cudaGraphCreate(&G, 0));
+    cudaGraphConditionalHandle hzero, hgo, hloop, hconf, hcont;
+    CK(cudaGraphConditionalHandleCreate(&hzero, G, 0, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&hgo, G, 0, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&hloop, G, 0, cudaGraphCondAssignDefault));
+    // the start: initial residual and the decision
+    CK(cudaStreamBeginCaptureToGraph(st, G, nullptr, nullptr, 0, mode));
+    launch_scatter(n, st, d.loc2glob, h->in1, h->b);
+    launch_scatter(n, st, d.loc2glob, h->in2, h->x);
+    launch_dot(n, st, h->b, h->b, w, h->partials, h->scal, h->counter, S_FF, 0);
+    residual(h, top, h->x, h->b, r);
+    launch_dot(n, st, r, r, w, h->partials, h->scal, h->counter, S_RR, 0);
+    launch_cg_ctl_0(st, h->scal, h->loop_state, h->dhist, hzero, hgo, hloop);
+    CK(cudaStreamEndCapture(st, &G));
+    const long long k_start = launch_counter() - c0;
+    cudaGraphNode_t n0 = chain_leaf(G), nz, ng, nw;
+    cudaGraph_t Z, Go, B;
+    add_if(G, &n0, hzero, &nz, &Z);
+    CK(cudaStreamBeginCaptureToGraph(st, Z, nullptr, nullptr, 0, mode));
+    CK(cudaMemsetAsync(h->x, 0, n * sizeof(double), st));
+    CK(cudaStreamEndCapture(st, &Z));
+    add_if(G, &nz, hgo, &ng, &Go);
+    long long c1 = launch_counter();
+    CK(cudaStreamBeginCaptureToGraph(st, Go, nullptr, nullptr, 0, mode));
+    vcycle(h, top);
+    launch_dot(n, st, r, z, w, h->partials, h->scal, h->counter, S_RZ, 0);
+    CK(cudaMemcpyAsync(h->p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamEndCapture(st, &Go));
+    const long long k_go = launch_counter() - c1;
+    add_if(G, &ng, hloop, &nw, &B, cudaGraphCondTypeWhile);
+    CK(cudaGraphConditionalHandleCreate(&hconf, B, 0, 0));
+    CK(cudaGraphConditionalHandleCreate(&hcont, B, 0, 0));
+    // loop body: first half of an iteration
+    CK(cudaStreamBeginCaptureToGraph(st, B, nullptr, nullptr, 0, mode));
+    matvec(h, top, h->p, h->q);
+    launch_dot(n, st, h->p, h->q, w, h->partials, h->scal, h->counter, S_PQ, 1);
+    launch_cg_xr(n, st, h->x, r, h->p, h->q, w, h->partials, h->scal, h->counter);
+    launch_cg_ctl_a(st, h->scal, h->loop_state, h->dhist, hloop, hconf, hcont);
+    CK(cudaStreamEndCapture(st, &B));
+    cudaGraphNode_t nb0 = chain_leaf(B), nc, nn2;
+    cudaGraph_t C, D;
+    add_if(B, &nb0, hconf, &nc, &C);
+    c1 = launch_counter();
+    CK(cudaStreamBeginCaptureToGraph(st, C, nullptr, nullptr, 0, mode));
+    residual(h, top, h->x, h->b, h->t);
+    launch_dot(n, st, h->t, h->t, w, h->partials, h->scal, h->counter, S_TMP, 0);
+    launch_cg_ctl_c(st, h->scal, h->loop_state, h->dhist, hloop, hcont);
+    CK(cudaStreamEndCapture(st, &C));
+    h->g_conf_kernels = launch_counter() - c1;
+    add_if(B, &nc, hcont, &nn2, &D);
+    CK(cudaStreamBeginCaptureToGraph(st, D, nullptr, nullptr, 0, mode));
+    const bool flexible = h->opt.precision != MGIGA_PREC_FP64;
+    if (flexible) launch_dot(n, st, r, z, w, h->partials, h->scal, h->counter, S_RZOLD, 0);
+    vcycle(h, top);
+    launch_dot(n, st, r, z, w, h->partials, h->scal, h->counter, S_RZNEW, flexible ? 3 : 2);
+    launch_cg_p(n, st, h->p, z, h->scal);
+    CK(cudaStreamEndCapture(st, &D));
+    // the end: the solution into in2
+    CK(cudaStreamBeginCaptureToGraph(st, G, &nw, nullptr, 1, mode));
+    launch_gather(d.ndof, st, d.owner, h->x, h->in2);
+    CK(cudaStreamEndCapture(st, &G));
+    CK(cudaGraphInstantiate(&h->g_solve, G, 0));
+    h->g_start_kernels = k_start + 1;  // + the gather at the end
+    h->g_go_kernels = k_go;
+    h->g_solve_tmpl = G;
+    G = nullptr;
+    ok = true;
+  } catch (const std::exception&) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(st, &junk);
+      if (junk && junk != G) cudaGraphDestroy(junk);
+    }
+    cudaGetLastError();  // leave no error pending
+    if (h->g_solve) { cudaGraphExecDestroy(h->g_solve); h->g_solve = nullptr; }
+  }
+  if (G) cudaGraphDestroy(G);
+  h->launches -= launch_counter() - c0;  // captured, not run
+  return ok;
+}
+
+// the device-driven loop unless MGIGA_DEVICE_LOOP=0; built on first use (needs the kernel counts of
+// the host loop's two graphs for the launch statistics, so those are captured too)
+static bool use_device_loop(mgiga_handle* h) {
+  if (h->device_loop < 0) return false;
+  if (const char* env = std::getenv("MGIGA_DEVICE_LOOP"))
+    if (env[0] == '0') return false;
+  if (h->device_loop == 0) {
+    if (!h->loop_state) {
+      h->loop_state = h->arena->alloc<CgLoopState>(1);
+      h->dhist = h->arena->alloc<double>((size_t)h->opt.max_iter + 2);
+      CK(cudaMallocHost(&h->host_state, sizeof(CgLoopState)));
+    }
+    const int top = h->levels - 1;
+    DLevel& d = h->D[top];
+    cudaStream_t st = h->stream;
+    const double* w = d.weight;
+    const int64_t n = d.nloc;
+    // kernel counts of the halves (for mgiga_kernel_launches), from dry captures
+    if (!h->g_iter_a_kernels) {
+      cudaGraph_t g;
+      long long c0 = launch_counter();
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      matvec(h, top, h->p, h->q);
+      launch_dot(n, st, h->p, h->q, w, h->partials, h->scal, h->counter, S_PQ, 1);
+      launch_cg_xr(n, st, h->x, d.f, h->p, h->q, w, h->partials, h->scal, h->counter);
+      CK(cudaStreamEndCapture(st, &g));
+      cudaGraphDestroy(g);
+      h->g_iter_a_kernels = launch_counter() - c0 + 1;  // + the control kernel
+      c0 = launch_counter();
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      const bool flexible = h->opt.precision != MGIGA_PREC_FP64;
+      if (flexible) launch_dot(n, st, d.f, d.u, w, h->partials, h->scal, h->counter, S_RZOLD, 0);
+      vcycle(h, top);
+      launch_dot(n, st, d.f, d.u, w, h->partials, h->scal, h->counter, S_RZNEW, flexible ? 3 : 2);
+      launch_cg_p(n, st, h->p, d.u, h->scal);
+      CK(cudaStreamEndCapture(st, &g));
+      cudaGraphDestroy(g);
+      h->g_iter_b_kernels = launch_counter() - c0;
+      h->launches -= h->g_iter_a_kernels - 1 + h->g_iter_b_kernels;
+    }
+    h->device_loop = build_solve_graph(h) ? 1 : -1;
+  }
+  return h->device_loop > 0;
+}
+
 // PCG (Sec. 4) or the cycle as solver, on device-resident global vectors
+// enqueue a whole PCG solve as one graph launch (rhs, u: device vectors in global order; u is
+// read as the initial guess and receives the solution); no host synchronisation
+static void enqueue_graph_solve(mgiga_handle* h, const double* rhs, double* u, double tol) {
+  cudaStream_t st = h->stream;
+  const size_t bytes = (size_t)h->L[h->levels - 1].ndof * sizeof(double);
+  if (rhs != h->in1) CK(cudaMemcpyAsync(h->in1, rhs, bytes, cudaMemcpyDeviceToDevice, st));
+  if (u != h->in2) CK(cudaMemcpyAsync(h->in2, u, bytes, cudaMemcpyDeviceToDevice, st));
+  launch_cg_loop_init(st, h->scal, h->loop_state, tol, 0.0, h->opt.max_iter);
+  check_launch();
+  CK(cudaGraphLaunch(h->g_solve, st));
+  if (u != h->in2) CK(cudaMemcpyAsync(u, h->in2, bytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->host_state, h->loop_state, sizeof(CgLoopState), cudaMemcpyDeviceToHost, st));
+  h->pending = true;
+}
+
+// after the stream of an enqueued graph solve has drained: status, iterations, history
+static mgiga_status finish_graph_solve(mgiga_handle* h, int* iters, double* final_relres) {
+  h->pending = false;
+  const CgLoopState ls = *h->host_state;
+  const int it = ls.it;
+  if (iters) *iters = it;
+  if (final_relres) *final_relres = ls.rel;
+  h->history.clear();
+  h->launches += h->g_start_kernels;
+  if (ls.status == 4) return fail(h, MGIGA_EBREAKDOWN, "non-finite right-hand side or initial guess");
+  if (it > 0) h->launches += h->g_go_kernels;  // the first cycle ran iff the loop did
+  h->launches += (long long)it * h->g_iter_a_kernels + (long long)ls.nconf * h->g_conf_kernels +
+                 (long long)ls.ncont * h->g_iter_b_kernels;
+  std::vector<double> hh((size_t)it + 1);
+  CK(cudaMemcpy(hh.data(), h->dhist, hh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  h->history = hh;
+  check_device_timeout(h);
+  if (ls.status == 3) return fail(h, MGIGA_EBREAKDOWN, "CG breakdown (p^T A p <= 0 or NaN)");
+  if (ls.status == 2) return fail(h, MGIGA_ENOCONV, "max_iter reached");
+  return MGIGA_OK;
+}
+
 static mgiga_status solve_impl(mgiga_handle* h, const double* rhs, double* u, double tol, int* iters,
                                double* final_relres) {
   h->history.clear();  // a solve that fails early leaves its own (empty or partial) history
+  if (h->opt.outer == MGIGA_OUTER_PCG && use_device_loop(h)) {
+    {
+      LaunchScope scope(h);
+      enqueue_graph_solve(h, rhs, u, tol);
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return finish_graph_solve(h, iters, final_relres);
+  }
   LaunchScope scope(h);
   const int top = h->levels - 1;
   DLevel& d = h->D[top];
@@ -2056,6 +2386,155 @@ mgiga_status mgiga_solve(mgiga_handle* h, const double* rhs, double* u, double t
     }
     return s;
   });
+}
+
+// ---------------------------------------------------------------------------
+// batched solves: many handles, one host pass
+// ---------------------------------------------------------------------------
+namespace {
+// one graph for a whole batch: per problem the staging copies, the parameters, the problem's solve graph
+// (a child graph) and the copies back, all problems' chains side by side; rebuilt when the batch changes
+struct BatchGraph {
+  std::vector<mgiga_handle*> hs;
+  std::vector<const double*> rhs;
+  std::vector<double*> u;
+  std::vector<double> tol;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+  ~BatchGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+std::mutex g_batch_mutex;
+std::unique_ptr<BatchGraph> g_batch;
+
+bool build_batch_graph(BatchGraph& bg) {
+  cudaGraph_t G = nullptr;
+  bool ok = false;
+  try {
+    CK(cudaGraphCreate(&G, 0));
+    for (size_t i = 0; i < bg.hs.size(); ++i) {
+      mgiga_handle* h = bg.hs[i];
+      const size_t bytes = (size_t)h->L[h->levels - 1].ndof * sizeof(double);
+      cudaGraphNode_t a, b, c, k, e, f;
+      CK(cudaGraphAddMemcpyNode1D(&a, G, nullptr, 0, h->in1, bg.rhs[i], bytes, cudaMemcpyDeviceToDevice));
+      CK(cudaGraphAddMemcpyNode1D(&b, G, &a, 1, h->in2, bg.u[i], bytes, cudaMemcpyDeviceToDevice));
+      // the parameters of the solve: a captured launch of the init kernel
+      cudaGraph_t init = nullptr;
+      cudaStream_t cs = h->stream;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      launch_cg_loop_init(cs, h->scal, h->loop_state, bg.tol[i], 0.0, h->opt.max_iter);
+      CK(cudaStreamEndCapture(cs, &init));
+      const cudaError_t e1 = cudaGraphAddChildGraphNode(&c, G, &b, 1, init);
+      cudaGraphDestroy(init);
+      CK(e1);
+      CK(cudaGraphAddChildGraphNode(&k, G, &c, 1, h->g_solve_tmpl));
+      CK(cudaGraphAddMemcpyNode1D(&e, G, &k, 1, bg.u[i], h->in2, bytes, cudaMemcpyDeviceToDevice));
+      CK(cudaGraphAddMemcpyNode1D(&f, G, &e, 1, h->host_state, h->loop_state, sizeof(CgLoopState),
+                                  cudaMemcpyDeviceToHost));
+    }
+    CK(cudaGraphInstantiate(&bg.exec, G, 0));
+    ok = true;
+  } catch (const std::exception&) {
+    cudaGetLastError();
+    if (bg.exec) { cudaGraphExecDestroy(bg.exec); bg.exec = nullptr; }
+  }
+  if (G) cudaGraphDestroy(G);
+  return ok;
+}
+}  // namespace
+
+mgiga_status mgiga_solve_batch_d(mgiga_handle* const* hs, int n, const double* const* rhs, double* const* u,
+                                 double tol, int flags, int* iters, double* final_relres, int* status) {
+  if (n < 0 || (n > 0 && (!hs || !rhs || !u))) return MGIGA_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return MGIGA_EINVAL;
+    if (!hs[i]->assembled) return fail(hs[i], MGIGA_ESTATE, "mgiga_assemble has not run");
+    if (!rhs[i] || !u[i]) return fail(hs[i], MGIGA_EINVAL, "NULL vector");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(hs[i], MGIGA_EINVAL, "a handle appears twice in the batch");
+  }
+  std::vector<int> st(n, MGIGA_OK), graph(n, 0);
+  // every solve enqueued before any is awaited
+  for (int i = 0; i < n; ++i) {
+    mgiga_handle* h = hs[i];
+    st[i] = guarded_call(h, [&]() -> mgiga_status {
+      after_legacy(h);
+      h->history.clear();
+      if (h->opt.outer != MGIGA_OUTER_PCG || !use_device_loop(h)) return MGIGA_OK;  // solved below, alone
+      graph[i] = 1;
+      return MGIGA_OK;
+    });
+  }
+  bool one_graph = false;
+  if ((flags & MGIGA_BATCH_ONE_GRAPH) && n > 0) {
+    bool all = true;
+    for (int i = 0; i < n; ++i) all = all && graph[i] && st[i] == MGIGA_OK && hs[i]->g_solve_tmpl;
+    if (all) {
+      std::lock_guard<std::mutex> lock(g_batch_mutex);
+      const bool same = g_batch && g_batch->hs == std::vector<mgiga_handle*>(hs, hs + n) &&
+                        g_batch->rhs == std::vector<const double*>(rhs, rhs + n) &&
+                        g_batch->u == std::vector<double*>(u, u + n) && g_batch->tol == std::vector<double>(n, tol);
+      if (!same) {
+        std::unique_ptr<BatchGraph> bg(new BatchGraph());
+        bg->hs.assign(hs, hs + n);
+        bg->rhs.assign(rhs, rhs + n);
+        bg->u.assign(u, u + n);
+        bg->tol.assign(n, tol);
+        if (cudaStreamCreateWithFlags(&bg->stream, cudaStreamNonBlocking) == cudaSuccess && build_batch_graph(*bg))
+          g_batch = std::move(bg);
+        else
+          g_batch.reset();
+      }
+      if (g_batch && g_batch->exec) {
+        // the batch's stream starts after every handle's earlier work
+        for (int i = 0; i < n; ++i) {
+          cudaEvent_t ev;
+          if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(ev, hs[i]->stream);
+            cudaStreamWaitEvent(g_batch->stream, ev, 0);
+            cudaEventDestroy(ev);
+          }
+        }
+        if (cudaGraphLaunch(g_batch->exec, g_batch->stream) == cudaSuccess &&
+            cudaStreamSynchronize(g_batch->stream) == cudaSuccess) {
+          one_graph = true;
+          for (int i = 0; i < n; ++i) hs[i]->pending = true;
+        }
+      }
+    }
+  }
+  if (!one_graph)
+    for (int i = 0; i < n; ++i) {
+      if (!graph[i] || st[i] != MGIGA_OK) continue;
+      mgiga_handle* h = hs[i];
+      st[i] = guarded_call(h, [&]() -> mgiga_status {
+        LaunchScope scope(h);
+        enqueue_graph_solve(h, rhs[i], u[i], tol);
+        return MGIGA_OK;
+      });
+    }
+  mgiga_status first = MGIGA_OK;
+  for (int i = 0; i < n; ++i) {
+    mgiga_handle* h = hs[i];
+    int it = 0;
+    double rel = 0.0;
+    if (st[i] == MGIGA_OK) {
+      if (graph[i])
+        st[i] = guarded_call(h, [&]() -> mgiga_status {
+          CK(cudaStreamSynchronize(h->stream));
+          return finish_graph_solve(h, &it, &rel);
+        });
+      else
+        st[i] = guarded_call(h, [&]() { return solve_impl(h, rhs[i], u[i], tol, &it, &rel); });
+    }
+    if (iters) iters[i] = it;
+    if (final_relres) final_relres[i] = rel;
+    if (status) status[i] = st[i];
+    if (first == MGIGA_OK && st[i] != MGIGA_OK) first = (mgiga_status)st[i];
+  }
+  return first;
 }
 
 mgiga_status mgiga_check_wait_expiry(mgiga_handle* h, long long iterations, double* elapsed_ms) {

@@ -57,7 +57,7 @@ class _Options(C.Structure):
     _fields_ = [("levels", C.c_int), ("smoother", C.c_int), ("nu", C.c_int), ("mu", C.c_int),
                 ("outer", C.c_int), ("precision", C.c_int), ("max_iter", C.c_int),
                 ("tau", C.c_double), ("delta", C.c_double), ("hbm_budget", C.c_size_t),
-                ("stream", C.c_void_p), ("gs_cluster", C.c_int)]
+                ("stream", C.c_void_p), ("gs_cluster", C.c_int), ("autotune", C.c_int)]
 
 
 _H = C.c_void_p
@@ -73,6 +73,8 @@ _SIGS = {
     "mgiga_vcycle_d": (C.c_int, [_H, C.c_void_p, C.c_void_p]),
     "mgiga_solve": (C.c_int, [_H, _D, _D, C.c_double, _I, _D]),
     "mgiga_solve_d": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_double, _I, _D]),
+    "mgiga_solve_batch_d": (C.c_int, [C.POINTER(_H), C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      C.c_double, C.c_int, _I, _D, _I]),
     "mgiga_apply": (C.c_int, [_H, C.c_int, C.c_int, _D, _D, _D]),
     "mgiga_apply_d": (C.c_int, [_H, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mgiga_residual_noalloc_d": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -143,7 +145,8 @@ class Solver:
     """
 
     def __init__(self, prob, levels=0, smoother="scms", tau=1.0, delta=0.12, nu=1, mu=1, outer="pcg",
-                 precision="fp64", max_iter=1000, hbm_budget=0, stream=None, assemble=True, gs_cluster=0):
+                 precision="fp64", max_iter=1000, hbm_budget=0, stream=None, assemble=True, gs_cluster=0,
+                 autotune=False):
         self.prob = prob
         self.precision = precision
         cp, self._keep = marshal_problem(prob)
@@ -154,6 +157,7 @@ class Solver:
         opts.tau, opts.delta, opts.hbm_budget = tau, delta, hbm_budget
         opts.stream = C.c_void_p(stream) if stream else None
         opts.gs_cluster = gs_cluster
+        opts.autotune = 1 if autotune else 0
         self._h = _H()
         st = _lib.mgiga_create(C.byref(cp), C.byref(opts), C.byref(self._h))
         if st != OK:
@@ -312,3 +316,22 @@ class Solver:
         level = level % self.levels
         self._check(_lib.mgiga_apply_d(self._h, OP[op], level, _tensor_ptr(a),
                                        _tensor_ptr(b) if b is not None else None, _tensor_ptr(out)))
+
+
+BATCH_ONE_GRAPH = 1
+
+
+def solve_batch_d(solvers, rhs, u, tol=1e-8, one_graph=False):
+    """mgiga_solve_batch_d: solve every (solver, rhs, u) of the lists (CUDA float64 tensors, u the
+    initial guess and the solution); returns (iterations, final relative residuals, statuses) as
+    lists.  one_graph: all solves as the branches of one graph launch."""
+    n = len(solvers)
+    hs = (_H * max(n, 1))(*[s._h for s in solvers])
+    rp = (C.c_void_p * max(n, 1))(*[_tensor_ptr(x).value for x in rhs])
+    up = (C.c_void_p * max(n, 1))(*[_tensor_ptr(x).value for x in u])
+    it = np.zeros(max(n, 1), dtype=np.int32)
+    rel = np.zeros(max(n, 1))
+    st = np.zeros(max(n, 1), dtype=np.int32)
+    _lib.mgiga_solve_batch_d(hs, n, rp, up, tol, BATCH_ONE_GRAPH if one_graph else 0, it.ctypes.data_as(_I),
+                             _dptr(rel), st.ctypes.data_as(_I))
+    return it[:n].tolist(), rel[:n].tolist(), st[:n].tolist()

@@ -215,36 +215,51 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--workers", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=120.0, help="HBM budget of the resident operators")
-    ap.add_argument("--rate", type=float, default=20.0, help="mean arrivals per second")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="mean arrivals per second; 0: calibrated -- the stream is first served with every "
+                         "request submitted at once (capacity X solves/s, set-ups included), then replayed "
+                         "on a fresh server with Poisson arrivals at 0.8 X")
     ap.add_argument("--max-patch-dof", type=float, default=1e5, help="upper end of the per-patch DoF range")
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--seed", type=int, default=501)
     args = ap.parse_args(argv)
-    srv = Server(workers=args.workers, hbm_budget=int(args.budget_gb * (1 << 30)), precision=args.precision)
-    arrivals = np.random.default_rng(args.seed + 7)
-    srv.start()
-    futs = []
-    t = time.perf_counter()
-    for key, prob, opts, rhs_seed in W.serving_stream(args.requests, seed=args.seed,
-                                                      max_patch_dof=args.max_patch_dof):
-        t += arrivals.exponential(1.0 / args.rate)
-        wait = t - time.perf_counter()
-        if wait > 0:
-            time.sleep(wait)
-        futs.append(srv.submit(key, prob, opts, int(rhs_seed)))
-    failed, iters = 0, []
-    for f in futs:
-        try:
-            iters.append(f.result()[1])
-        except Rejected:
-            pass
-        except Exception:  # noqa: BLE001 -- counted and reported
-            failed += 1
-    st = srv.stats()
-    srv.stop()
-    st.update(requests=args.requests, failed=failed, workers=args.workers, budget_gb=args.budget_gb,
-              rate_per_s=args.rate, precision=args.precision,
-              mean_iterations=float(np.mean(iters)) if iters else None)
+    stream = list(W.serving_stream(args.requests, seed=args.seed, max_patch_dof=args.max_patch_dof))
+
+    def serve(rate):
+        srv = Server(workers=args.workers, hbm_budget=int(args.budget_gb * (1 << 30)), precision=args.precision)
+        arrivals = np.random.default_rng(args.seed + 7)
+        srv.start()
+        futs = []
+        t = time.perf_counter()
+        for key, prob, opts, rhs_seed in stream:
+            if rate > 0:
+                t += arrivals.exponential(1.0 / rate)
+                wait = t - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+            futs.append(srv.submit(key, prob, opts, int(rhs_seed)))
+        failed, iters = 0, []
+        for f in futs:
+            try:
+                iters.append(f.result()[1])
+            except Rejected:
+                pass
+            except Exception:  # noqa: BLE001 -- counted and reported
+                failed += 1
+        st = srv.stats()
+        srv.stop()
+        st.update(failed=failed, mean_iterations=float(np.mean(iters)) if iters else None)
+        return st
+
+    rate, calib = args.rate, None
+    if rate <= 0:
+        calib = serve(0.0)
+        rate = 0.8 * calib["solves_per_s"]
+    st = serve(rate)
+    st.update(requests=args.requests, workers=args.workers, budget_gb=args.budget_gb, rate_per_s=rate,
+              precision=args.precision, max_patch_dof=args.max_patch_dof,
+              calibration=None if calib is None else {"capacity_solves_per_s": calib["solves_per_s"],
+                                                       "p50_ms": calib["p50_ms"], "p99_ms": calib["p99_ms"]})
     print(json.dumps(st), flush=True)
 
 

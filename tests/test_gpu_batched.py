@@ -58,3 +58,31 @@ def test_batched_layout_concurrent_results_equal_alone():
         assert np.linalg.norm(r) <= 1.0001e-8 * np.linalg.norm(rhs[i]), SEEDS[i]
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("one_graph", [False, True])
+def test_batched_entry_point_equals_alone(one_graph):
+    """mgiga_solve_batch_d: all problems enqueued from one thread (each solve one
+    graph with conditional nodes), or all of them as the branches of a single
+    graph launch; every result bit-identical to the problem solved alone, twice
+    in a row (the single graph is reused the second time)."""
+    torch = pytest.importorskip("torch")
+    mgb = binding()
+    probs = [W.batched_problem(s) for s in SEEDS]
+    streams = [torch.cuda.Stream() for _ in probs]
+    solvers = [mgb.Solver(pr, levels=o["levels"], smoother=o["smoother"], tau=o["tau"], delta=o["delta"],
+                          precision="tf32", stream=st.cuda_stream)
+               for (pr, o, _rs), st in zip(probs, streams)]
+    rhs = [W.random_vector(s.ndof(), rs, kind="normal") for s, (_pr, _o, rs) in zip(solvers, probs)]
+    alone = [s.solve(f, tol=1e-8) for s, f in zip(solvers, rhs)]
+    rd = [torch.from_numpy(f).cuda() for f in rhs]
+    for rep in range(2):
+        ud = [torch.zeros_like(x) for x in rd]
+        torch.cuda.synchronize()
+        its, rels, sts = mgb.solve_batch_d(solvers, rd, ud, tol=1e-8, one_graph=one_graph)
+        for i, a in enumerate(alone):
+            assert sts[i] == mgb.OK and its[i] == a[1] and rels[i] == a[2], (SEEDS[i], its[i], a[1])
+            assert np.array_equal(ud[i].cpu().numpy(), a[0]), (rep, SEEDS[i])
+            assert solvers[i].residual_history()[-1] == a[2]
+    for s in solvers:
+        s.close()

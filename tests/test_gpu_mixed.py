@@ -239,3 +239,29 @@ def test_tensor_core_smoother_every_level(name, precision, chained, monkeypatch)
         # and not exact: the tensor-core arithmetic is really in use
         assert err > 1e-9, (l, err)
     lib.close()
+
+
+@pytest.mark.parametrize("name", ["sipg2d_p3", "conf3d_p3"])
+def test_autotuned_handle(name):
+    """autotune: the contraction engine of every level and the residual's row
+    blocking chosen by timing; the smoother still matches the oracle at the
+    rounding bound of its arithmetic (TF32 at worst) and PCG meets the FP64
+    stopping rule; a second handle of the same sizes reuses the decisions."""
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    mgb = binding()
+    orc = omg.Multigrid(prob, levels=levels, smoother="hybrid", **opt)
+    for rep in range(2):
+        lib = mgb.Solver(prob, levels=levels, smoother="hybrid", precision="tf32", autotune=True, **opt)
+        rng = np.random.default_rng(16)
+        for l in range(1, levels):
+            A = orc.h["A"][l]
+            n = A.shape[0]
+            u, f = rng.standard_normal(n), rng.standard_normal(n)
+            ref = u + orc.scms[l].apply(f - A @ u)
+            got = lib.apply("smooth", l, f, u)
+            assert np.linalg.norm(got - ref) <= smooth_tol("tf32", prob["dim"]) * np.linalg.norm(ref - u), l
+        f = lib.load_sinprod()
+        u, it, rel, st = lib.solve(f, tol=1e-8)
+        assert np.linalg.norm(f - orc.A @ u) <= 1e-8 * np.linalg.norm(f) * 1.0001
+        lib.close()

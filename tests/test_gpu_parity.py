@@ -247,3 +247,33 @@ def test_unit_square_workload_iterates():
     u_o, it_o, hist = orc.solve_direct(f, u0=u0, tol=1e-8)
     assert abs(it_l - it_o) <= 1 and rel_l <= 1e-8
     assert np.linalg.norm(u_l - u_o) <= 1e-7 * np.linalg.norm(u_o)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32"])
+@pytest.mark.parametrize("name", ["sipg2d_p3", "conf3d_p2"])
+def test_device_loop_equals_host_loop(name, precision, monkeypatch):
+    """The PCG loop as one graph with conditional nodes (no host round trip per
+    iteration) against the host-driven loop (MGIGA_DEVICE_LOOP=0): the same
+    kernels in the same order, so the iterates, iteration counts and residual
+    histories are identical; also when max_iter stops the loop."""
+    fac, levels, opt = CASES[name]
+    prob = fac()
+    mgb = binding()
+    dev = mgb.Solver(prob, levels=levels, smoother="hybrid", precision=precision, **opt)
+    monkeypatch.setenv("MGIGA_DEVICE_LOOP", "0")
+    host = mgb.Solver(prob, levels=levels, smoother="hybrid", precision=precision, **opt)
+    f = dev.load_sinprod()
+    u_d, it_d, rel_d, st_d = dev.solve(f, tol=1e-8)
+    u_h, it_h, rel_h, st_h = host.solve(f, tol=1e-8)
+    assert it_d == it_h and rel_d == rel_h and np.array_equal(u_d, u_h)
+    assert np.array_equal(dev.residual_history(), host.residual_history())
+    for s in (dev, host):
+        s.close()
+    dk = mgb.Solver(prob, levels=levels, smoother="hybrid", precision=precision, max_iter=3, **opt)
+    a = dk.solve(f, tol=1e-300, allow_noconv=True)   # the loop is chosen at solve time: host here
+    monkeypatch.delenv("MGIGA_DEVICE_LOOP")
+    dk2 = mgb.Solver(prob, levels=levels, smoother="hybrid", precision=precision, max_iter=3, **opt)
+    b = dk2.solve(f, tol=1e-300, allow_noconv=True)   # device
+    assert a[1] == b[1] == 3 and np.array_equal(a[0], b[0])
+    dk.close()
+    dk2.close()

@@ -1,7 +1,9 @@
 """The level operators assembled on the GPU (element stiffness by sum
 factorisation, Galerkin products one direction at a time; Sec. 2, Sec. 3
 Eq. a:galerkin) against the host set-up (MGIGA_HOST_SETUP=1) and against the
-oracle's assembled matrices.
+oracle's assembled matrices.  In 3D the device stiffness kernel is enabled
+with MGIGA_GPU_STIFFNESS_3D=1 (by default the host assembles the 3D finest
+level and the GPU forms its Galerkin products).
 
 Both set-ups compute the same sums in different orders, so the products A_l u
 agree to a few rounding units of |A| |u| on every level (bound 1e-13 of
@@ -40,7 +42,10 @@ CASES = {
 
 def _pair(prob, levels, monkeypatch):
     mgb = binding()
+    # 3D: the device stiffness kernel is not the default (slower than the host at 48 intervals); test it
+    monkeypatch.setenv("MGIGA_GPU_STIFFNESS_3D", "1")
     gpu = mgb.Solver(prob, levels=levels, smoother="hybrid", tau=0.25, delta=0.12)
+    monkeypatch.delenv("MGIGA_GPU_STIFFNESS_3D")
     monkeypatch.setenv("MGIGA_HOST_SETUP", "1")
     host = mgb.Solver(prob, levels=levels, smoother="hybrid", tau=0.25, delta=0.12)
     monkeypatch.delenv("MGIGA_HOST_SETUP")

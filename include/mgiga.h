@@ -148,7 +148,19 @@ typedef struct {
  * candidates on the device, once per size bucket (a factor sqrt(2) in the
  * interior size / the level's rows) for the process; later handles of a known
  * bucket reuse the choice.  0 = the built-in rules.  The paper has no
- * counterpart; the choice changes only the FP32 summation order. */
+ * counterpart; the choice changes only the FP32 summation order.
+ * matrix_free: 1 = the residuals the cycle computes on the finest level
+ * (before the smoothers and the restriction) evaluate the stiffness action
+ * at the Gauss points by sum factorisation instead of reading a stored band
+ * (Sec. 2, Eq. linear:system:0: the same bilinear form and quadrature, with
+ * p + 1 points per element and direction), with the geometric factors
+ * computed from the geometry's control points; the SIPG terms (Sec. 3) stay
+ * stored.  In the FP32/TF32/BF16 modes this replaces the FP32 copy of the
+ * finest band (which is then not allocated); its arithmetic is the mode's
+ * (FP32, or FP64 in the FP64 mode).  The outer CG's product keeps the FP64
+ * band.  Needs maximal smoothness and a geometry map that is one polynomial
+ * piece of degree <= 2 per patch; else mgiga_assemble returns MGIGA_EINVAL.
+ * 0 = stored bands everywhere. */
 typedef struct {
   int levels, smoother, nu, mu, outer, precision, max_iter;
   double tau, delta;
@@ -156,11 +168,12 @@ typedef struct {
   void* stream;
   int gs_cluster;
   int autotune;
+  int matrix_free;
 } mgiga_options;
 
 /* Fill `opts` with: levels 0, SCMS, nu 1, mu 1, PCG, FP64, max_iter 1000,
  * tau 1, delta 0.12, no budget, default stream, automatic cluster size, no
- * autotuning. */
+ * autotuning, stored bands. */
 void mgiga_default_options(mgiga_options* opts);
 
 /* Validate the problem, build the DoF numbering, the piece decomposition and

@@ -87,8 +87,9 @@ struct Level {
   // operator: band[o * nloc + pos], o = sum_a (o_a + p) (2p+1)^a
   int nb = 0;
   Vec band;
-  // set-up on the GPU: the band is assembled on the device; the host part of the finest-level
-  // assembly leaves the SIPG terms within one patch here as (band index, value), in cell order
+  // the SIPG terms within one patch, (band index, value) in cell order, as the finest-level
+  // assembly computes them (also added to the host band when there is one): the device set-up adds
+  // them to the band it assembles, the matrix-free residual applies them as stored couplings
   std::vector<std::pair<int64_t, double>> band_add;
   double nnz = 0.0;  // nonzero band coefficients (kept when the host band is released)
   // SIPG cross-patch couplings, CSR over rows x_row[i]
@@ -108,9 +109,9 @@ struct Level {
 
 // numbering / topology of a level from its knots
 void build_topology(const Problem& pr, Level& L);
-// finest-level assembly: patch stiffness + SIPG interface terms into L.band / x-blocks; with
-// stiffness = false only the interface terms (L.band stays empty; the terms within one patch go to
-// L.band_add, the band being assembled on the GPU)
+// finest-level assembly: patch stiffness + SIPG interface terms into L.band / x-blocks (the terms
+// within one patch also listed in L.band_add); with stiffness = false only the interface terms
+// (L.band stays empty, the band being assembled on the GPU)
 void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec, 3>>& fine_knots,
                    bool stiffness = true);
 // zero Dirichlet rows and columns of the band (when present on the host) and of the cross blocks

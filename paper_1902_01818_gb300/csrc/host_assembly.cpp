@@ -626,8 +626,8 @@ static void interface_terms(const Problem& pr, Level& L, const Interface& f,
               o += (ic - ir + p) * mul;
               mul *= 2 * p + 1;
             }
-            if (L.band.empty()) L.band_add.push_back({(int64_t)o * L.nloc + r, v});
-            else L.band[(size_t)o * L.nloc + r] += v;
+            L.band_add.push_back({(int64_t)o * L.nloc + r, v});
+            if (!L.band.empty()) L.band[(size_t)o * L.nloc + r] += v;
           } else {
             cross[((uint64_t)r << 32) | (uint64_t)c] += v;
           }

@@ -1109,27 +1109,13 @@ __device__ __forceinline__ void gs_rows(const GsSweepArgs& a, int64_t base, int6
 #pragma unroll
       for (int o0 = 0; o0 < W; ++o0) acc = fma(__ldg(br + (int64_t)o0 * a.ngs), (TB)__ldcg(ur + o0), acc);
     }
-    // SIPG couplings across interfaces, shared over the row's lanes
+    // SIPG couplings across interfaces and, for a DoF shared by conforming patches, the band rows
+    // of its further copies (their diagonals are part of the entry's), shared over the row's lanes
     for (int j = xr.x + sub; j < xr.y; j += TPR) acc = fma((TB)a.x_val[j], (TB)__ldcg(a.u + a.x_col[j]), acc);
   }
 #pragma unroll
   for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (active && sub == 0) {
-    if (cls >= 0) {
-      // further copies of a DoF shared by conforming patches (owner first)
-      for (int cp = a.sh_ptr[cls] + 1; cp < a.sh_ptr[cls + 1]; ++cp) {
-        const int64_t q = a.sh_pos[cp];
-        const PatchMeta pm = a.patches[a.sh_patch[cp]];
-        const int64_t s1 = pm.N[0], s2 = (int64_t)pm.N[0] * pm.N[1];
-        for (int ob = 0; ob < NOB; ++ob) {
-          const int o1 = ob % W, o2 = ob / W;
-          const int64_t off = (D == 3 ? (int64_t)(o2 - P) * s2 : 0) + (int64_t)(o1 - P) * s1 - P;
-          for (int o0 = 0; o0 < W; ++o0)
-            acc = fma((TB)a.band[(int64_t)(ob * W + o0) * a.nloc + q], (TB)__ldcg(a.u + q + off + o0), acc);
-        }
-        diag += (TB)a.band[(int64_t)center * a.nloc + q];
-      }
-    }
     const double unew = upos + (double)(((TB)fpos - acc) / diag);
     if (cls < 0) {
       a.u[pos] = unew;

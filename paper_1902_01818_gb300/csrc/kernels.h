@@ -19,7 +19,8 @@ struct GsSweepArgs {
                           // (double, or float for the mixed path)
   const int64_t* gs_pos;  // owner position of entry e
   const int2* gs_stride;  // (N_0, N_0 N_1) of its patch
-  const int2* gs_xrange;  // its SIPG coupling entries [x, y) in x_col / x_val
+  const int2* gs_xrange;  // its couplings besides its band row, entries [x, y) of x_col / x_val: the
+                          // SIPG couplings, then the band rows of a shared DoF's further copies
   const int* gs_cls;      // shared class (conforming) or -1
   const PatchMeta* patches;
   const double* band;

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -20,6 +21,7 @@
 #include "device.cuh"
 #include "host.hpp"
 #include "kernels.h"
+#include "matfree.hpp"
 #include "setup_gpu.hpp"
 #include "tune.hpp"
 
@@ -151,6 +153,8 @@ struct DLevel {
                               // 3 FP32 + BF16 tensor-core FD
   int2* gs_stride = nullptr;
   int2* gs_xrange = nullptr;
+  int64_t* gs_xcol = nullptr;  // per entry (gs_xrange): SIPG couplings, then further copies' band rows
+  double* gs_xval = nullptr;
   // mixed path: base colours of each patch parity swept patch-parallel
   // (staged colour blocks, see gs_patch_staged)
   int gs_base = 0;                 // (p+1)^d base colours per parity
@@ -163,6 +167,15 @@ struct DLevel {
   int64_t* gs_foff = nullptr;      // byte offset of each entry's f in the pool (-1: none)
   int* gs_xent[2] = {nullptr, nullptr};  // per phase: base-colour entries with couplings to the other parity
   int gs_nxent[2] = {0, 0};
+  // matrix-free residual of the finest level (option matrix_free)
+  bool mf = false;
+  MfDev mfd;
+  double mf_flops = 0.0, mf_bytes = 0.0;
+  int mf_nx = 0;  // stored couplings: SIPG cross-patch and within-patch terms, CSR over rows
+  int64_t* mf_x_row = nullptr;
+  int* mf_x_ptr = nullptr;
+  int64_t* mf_x_col = nullptr;
+  double* mf_x_val = nullptr;
 };
 
 }  // namespace
@@ -1124,6 +1137,68 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
   a.off_meta = pl.off_meta;
 }
 
+// matrix-free residual of the finest level: point tables, tiling and window partials (matfree.cu),
+// and the stored couplings it leaves to CSR: the SIPG cross-patch blocks and the SIPG terms within
+// one patch (summed per entry in cell order; rows and columns of Dirichlet positions dropped, as the
+// band drops them)
+void build_mf(const Problem& pr, const Level& L, const std::vector<std::pair<int64_t, double>>& self, Arena& A,
+              DLevel& d) {
+  std::string why;
+  if (!mf_supported(pr, &why)) throw SetupError(MGIGA_EINVAL, "the matrix-free residual needs " + why);
+  const bool f32 = d.arith >= 1;
+  const MfHost m = mf_build_host(pr, L, f32);
+  auto up = [&](const std::vector<double>& v) -> const void* {
+    if (f32) return A.upload(std::vector<float>(v.begin(), v.end()));
+    return A.upload(v);
+  };
+  d.mfd.pp = A.upload(m.pp);
+  d.mfd.K = L.K;
+  d.mfd.GM = m.GM;
+  d.mfd.ntile = m.ntile;
+  d.mfd.B = up(m.B);
+  d.mfd.Dv = up(m.Dv);
+  d.mfd.w = up(m.w);
+  d.mfd.gB = up(m.gB);
+  d.mfd.gD = up(m.gD);
+  d.mfd.ctrl = up(m.ctrl);
+  d.mfd.dir = A.upload(L.dirichlet);
+  d.mfd.part = f32 ? static_cast<void*>(A.alloc<float>((size_t)m.part_n)) : static_cast<void*>(A.alloc<double>((size_t)m.part_n));
+  d.mf_flops = m.flops;
+  // u and f read, out written, the window partials written and read back
+  d.mf_bytes = 24.0 * (double)L.nloc + 2.0 * (double)m.part_n * (f32 ? 4.0 : 8.0);
+  std::map<int64_t, std::vector<std::pair<int64_t, double>>> rows;
+  for (size_t i = 0; i < L.x_row.size(); ++i)
+    for (int j = L.x_ptr[i]; j < L.x_ptr[i + 1]; ++j) rows[L.x_row[i]].push_back({L.x_col[j], L.x_val[j]});
+  std::map<std::pair<int64_t, int64_t>, double> within;
+  for (const auto& x : self) {
+    const int64_t o = x.first / L.nloc, r = x.first % L.nloc;
+    const int64_t c = r + L.band_offset(L.patch_of[r], (int)o);
+    if (L.dirichlet[r] || L.dirichlet[c]) continue;
+    within[{r, c}] += x.second;
+  }
+  for (const auto& x : within) rows[x.first.first].push_back({x.first.second, x.second});
+  std::vector<int64_t> xr, xc;
+  std::vector<int> xp(1, 0);
+  Vec xv;
+  for (const auto& r : rows) {
+    xr.push_back(r.first);
+    for (const auto& e : r.second) {
+      xc.push_back(e.first);
+      xv.push_back(e.second);
+    }
+    xp.push_back((int)xc.size());
+  }
+  d.mf_nx = (int)xr.size();
+  d.mf_x_row = A.upload(xr);
+  d.mf_x_ptr = A.upload(xp);
+  d.mf_x_col = A.upload(xc);
+  d.mf_x_val = A.upload(xv);
+  d.mf = true;
+  if (std::getenv("MGIGA_VERBOSE"))
+    std::fprintf(stderr, "mgiga: matrix-free residual: %d tiles of %d^%d elements, %lld partials, %d coupled rows\n",
+                 m.ntile, m.te, L.d, (long long)m.part_n, d.mf_nx);
+}
+
 void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L, Arena& A, DLevel& dl,
               int gs_cluster) {
   const int n = L.ndof;
@@ -1150,28 +1225,59 @@ void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L,
     gx.push_back(it == xrow.end() ? -1 : it->second);
   }
   dl.gs_cptr.push_back(n);
+  // per entry, the couplings summed besides its own band row: the SIPG couplings of its row, then
+  // (conforming) the band rows of the further copies of a shared DoF, whose diagonals are folded
+  // into the entry's diagonal (the copies hold the same value); the row's lanes share them
+  const int center = L.d == 2 ? L.p * (2 * L.p + 1) + L.p : (L.p * (2 * L.p + 1) + L.p) * (2 * L.p + 1) + L.p;
+  std::vector<int2> gst(n), gxr(n);
+  std::vector<int64_t> xcol;
+  Vec xval, cdiag(n, 0.0);
+  for (int e = 0; e < n; ++e) {
+    const int k = gpatch[e];
+    gst[e] = make_int2(L.N[k][0], L.N[k][0] * L.N[k][1]);
+    const int x0 = (int)xcol.size();
+    if (gx[e] >= 0)
+      for (int j = L.x_ptr[gx[e]]; j < L.x_ptr[gx[e] + 1]; ++j) {
+        xcol.push_back(L.x_col[j]);
+        xval.push_back(L.x_val[j]);
+      }
+    if (gcls[e] >= 0)
+      for (int cp = L.sh_ptr[gcls[e]] + 1; cp < L.sh_ptr[gcls[e] + 1]; ++cp) {
+        const int64_t q = L.sh_pos[cp];
+        const int kq = L.patch_of[q];
+        for (int o = 0; o < L.nb; ++o) {
+          const double v = L.band[(size_t)o * L.nloc + q];
+          if (v == 0.0) continue;
+          if (o == center) {
+            cdiag[e] += v;
+          } else {
+            xcol.push_back(q + L.band_offset(kq, o));
+            xval.push_back(v);
+          }
+        }
+      }
+    if (xcol.size() >= (size_t)INT32_MAX) throw SetupError(MGIGA_ENOMEM, "Gauss-Seidel coupling list too long");
+    gxr[e] = make_int2(x0, (int)xcol.size());
+  }
   // band rows of the owner copies in colour order (coalesced per colour),
   // in double (FP64 path) or float (mixed path)
   const bool f32 = dl.arith >= 1;
   if (f32) {
     std::vector<float> gb((size_t)L.nb * n);
     for (int o = 0; o < L.nb; ++o)
-      for (int e = 0; e < n; ++e) gb[(size_t)o * n + e] = (float)L.band[(size_t)o * L.nloc + gpos[e]];
+      for (int e = 0; e < n; ++e)
+        gb[(size_t)o * n + e] = (float)(L.band[(size_t)o * L.nloc + gpos[e]] + (o == center ? cdiag[e] : 0.0));
     dl.gs_band = reinterpret_cast<double*>(A.upload(gb));
   } else {
     Vec gb((size_t)L.nb * n);
     for (int o = 0; o < L.nb; ++o)
-      for (int e = 0; e < n; ++e) gb[(size_t)o * n + e] = L.band[(size_t)o * L.nloc + gpos[e]];
+      for (int e = 0; e < n; ++e) gb[(size_t)o * n + e] = L.band[(size_t)o * L.nloc + gpos[e]] + (o == center ? cdiag[e] : 0.0);
     dl.gs_band = A.upload(gb);
-  }
-  std::vector<int2> gst(n), gxr(n);
-  for (int e = 0; e < n; ++e) {
-    const int k = gpatch[e];
-    gst[e] = make_int2(L.N[k][0], L.N[k][0] * L.N[k][1]);
-    gxr[e] = gx[e] >= 0 ? make_int2(L.x_ptr[gx[e]], L.x_ptr[gx[e] + 1]) : make_int2(0, 0);
   }
   dl.gs_stride = A.upload(gst);
   dl.gs_xrange = A.upload(gxr);
+  dl.gs_xcol = A.upload(xcol);
+  dl.gs_xval = A.upload(xval);
   dl.gs_cptr_d = A.upload(dl.gs_cptr);
   const int ncol = (int)dl.gs_cptr.size() - 1;
   int B = 1;
@@ -1213,6 +1319,12 @@ void residual(mgiga_handle* h, int l, const double* u, const double* f, double* 
 void cycle_residual(mgiga_handle* h, int l, const double* u, const double* f, double* out) {
   const Level& L = h->L[l];
   DLevel& d = h->D[l];
+  if (d.mf) {  // stiffness by sum factorisation at the Gauss points, stored SIPG couplings
+    mf_launch(L.d, L.p, d.arith >= 1, d.mfd, h->stream, u, f, out, d.ntiles, d.tiles);
+    launch_cross(0, d.mf_nx, h->stream, d.mf_x_row, d.mf_x_ptr, d.mf_x_col, d.mf_x_val, u, out);
+    if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, out, f, 0);
+    return;
+  }
   if (!d.band32) {
     residual(h, l, u, f, out);
     return;
@@ -1284,7 +1396,7 @@ void gs_sweep(mgiga_handle* h, int l, bool forward) {
   a.gs_pos = d.gs_pos; a.gs_stride = d.gs_stride; a.gs_xrange = d.gs_xrange; a.gs_cls = d.gs_cls;
   a.patches = d.patches; a.band = d.band; a.nloc = d.nloc;
   a.sh_ptr = d.sh_ptr; a.sh_pos = d.sh_pos; a.sh_patch = d.sh_patch;
-  a.x_col = d.x_col; a.x_val = d.x_val; a.f = d.f; a.u = d.u;
+  a.x_col = d.gs_xcol; a.x_val = d.gs_xval; a.f = d.f; a.u = d.u;
   a.bar = h->gs_bar;
   a.err = h->gs_err;
   const bool f32 = d.arith >= 1;
@@ -1313,7 +1425,7 @@ void gs_sweep(mgiga_handle* h, int l, bool forward) {
     // f minus the couplings to the other parity (fixed during the phase) into the blocks
     const int e0 = d.gs_cptr[g.c_begin], e1 = d.gs_cptr[g.c_end];
     launch_gs_fill_phase(e0, e1 - e0, d.gs_nxent[ph], d.gs_xent[ph], h->stream, d.gs_foff, d.gs_pos, d.gs_xrange,
-                         d.x_col, d.x_val, d.f, d.u, d.gs_pool);
+                         d.gs_xcol, d.gs_xval, d.f, d.u, d.gs_pool);
     CK(launch_gs_staged(L.d, L.p, d.gs_nphase[ph], d.gs_smem, h->stream, g));
   };
   auto tail = [&]() { coop(2 * B, ncol); };
@@ -1544,6 +1656,7 @@ void mgiga_default_options(mgiga_options* o) {
   o->stream = nullptr;
   o->gs_cluster = 0;
   o->autotune = 0;
+  o->matrix_free = 0;
 }
 
 double mgiga_source_sinprod(const double* x, void* ctx) {
@@ -1570,7 +1683,7 @@ mgiga_status mgiga_create(const mgiga_problem* problem, const mgiga_options* opt
     if (o.smoother < 0 || o.smoother > 2 || o.nu < 1 || o.mu < 1 || o.mu > 2 || o.outer < 0 || o.outer > 1 ||
         o.precision < MGIGA_PREC_FP64 || o.precision > MGIGA_PREC_BF16 || o.max_iter < 0 || !(o.tau > 0.0) || !(o.delta > 0.0) || o.levels < 0 ||
         !(o.gs_cluster == 0 || o.gs_cluster == 2 || o.gs_cluster == 4 || o.gs_cluster == 8 || o.gs_cluster == 16) ||
-        o.autotune < 0 || o.autotune > 1)
+        o.autotune < 0 || o.autotune > 1 || o.matrix_free < 0 || o.matrix_free > 1)
       throw SetupError(MGIGA_EINVAL, "invalid options");
     h->stream = static_cast<cudaStream_t>(o.stream);
     const int lv = o.levels > 0 ? o.levels : auto_levels(h->pr);
@@ -1632,9 +1745,12 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
     // 48 intervals, p = 5: 49 s against 38 s on 16 host cores); its Galerkin products run on the GPU
     const char* s3_env = std::getenv("MGIGA_GPU_STIFFNESS_3D");  // the 3D device kernel, for testing
     const bool gpu_stiffness = gpu_setup && (h->pr.d == 2 || (s3_env && s3_env[0] == '1'));
+    std::vector<std::pair<int64_t, double>> mf_self;  // within-patch SIPG terms for the matrix-free residual
     if (gpu_setup) {
       Level& F = h->L[lv - 1];
       assemble_fine(h->pr, F, h->pr.knots, /*stiffness=*/!gpu_stiffness);
+      if (h->opt.matrix_free) mf_self = F.band_add;
+      if (!F.band.empty()) std::vector<std::pair<int64_t, double>>().swap(F.band_add);
       apply_dirichlet(F);
       h->T.assign(lv, Transfer{});
       for (int l = lv - 1; l > 0; --l) {
@@ -1645,6 +1761,8 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       tick("interfaces", lv - 1);
     } else {
       assemble_finest(h->pr, h->L);
+      if (h->opt.matrix_free) mf_self = h->L[lv - 1].band_add;
+      std::vector<std::pair<int64_t, double>>().swap(h->L[lv - 1].band_add);
       tick("assembly", lv - 1);
       galerkin_hierarchy(h->L, h->T);
       tick("galerkin", 0);
@@ -1706,7 +1824,12 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       d.f = A.guarded(L.nloc, d.guard);
       d.r = A.guarded(L.nloc, d.guard);
       d.band = gpu_setup ? dband[l] : A.upload(L.band);
-      if (d.arith >= 1 && l > 0) {  // FP32 copy for the residuals inside the mixed-precision cycle
+      const bool mf_here = h->opt.matrix_free && l == lv - 1;
+      if (mf_here) {
+        build_mf(h->pr, L, mf_self, A, d);
+        std::vector<std::pair<int64_t, double>>().swap(mf_self);
+      }
+      if (d.arith >= 1 && l > 0 && !mf_here) {  // FP32 copy for the residuals inside the mixed-precision cycle
         std::vector<float> b32(L.band.size() + 4, 0.0f);
         for (size_t i = 0; i < L.band.size(); ++i) b32[i] = (float)L.band[i];
         d.band32 = A.upload(b32);
@@ -2647,7 +2770,12 @@ mgiga_status mgiga_stage_work(const mgiga_handle* h, int stage, int level, doubl
   // the mixed path keeps FP32 band copies for the cycle's residuals (levels >= 1) and sweeps
   const bool f32 = h->opt.precision != MGIGA_PREC_FP64;
   double fl = 0.0, by = 0.0;
-  if (stage == MGIGA_STAGE_BAND || stage == MGIGA_STAGE_RESIDUAL) {
+  if (stage == MGIGA_STAGE_RESIDUAL && h->D[level].mf) {
+    // matrix-free: the sum-factorised passes and the pointwise flux (2 flops per FMA); u and f read,
+    // out written, the window partials written and read back
+    fl = h->D[level].mf_flops;
+    by = h->D[level].mf_bytes;
+  } else if (stage == MGIGA_STAGE_BAND || stage == MGIGA_STAGE_RESIDUAL) {
     // every nonzero once (FP32 coefficients for the residual of the mixed path), u and f read, out written
     const double nnz = L.nnz;
     fl = 2.0 * nnz;

@@ -57,7 +57,8 @@ class _Options(C.Structure):
     _fields_ = [("levels", C.c_int), ("smoother", C.c_int), ("nu", C.c_int), ("mu", C.c_int),
                 ("outer", C.c_int), ("precision", C.c_int), ("max_iter", C.c_int),
                 ("tau", C.c_double), ("delta", C.c_double), ("hbm_budget", C.c_size_t),
-                ("stream", C.c_void_p), ("gs_cluster", C.c_int), ("autotune", C.c_int)]
+                ("stream", C.c_void_p), ("gs_cluster", C.c_int), ("autotune", C.c_int),
+                ("matrix_free", C.c_int)]
 
 
 _H = C.c_void_p
@@ -146,7 +147,7 @@ class Solver:
 
     def __init__(self, prob, levels=0, smoother="scms", tau=1.0, delta=0.12, nu=1, mu=1, outer="pcg",
                  precision="fp64", max_iter=1000, hbm_budget=0, stream=None, assemble=True, gs_cluster=0,
-                 autotune=False):
+                 autotune=False, matrix_free=False):
         self.prob = prob
         self.precision = precision
         cp, self._keep = marshal_problem(prob)
@@ -158,6 +159,7 @@ class Solver:
         opts.stream = C.c_void_p(stream) if stream else None
         opts.gs_cluster = gs_cluster
         opts.autotune = 1 if autotune else 0
+        opts.matrix_free = 1 if matrix_free else 0
         self._h = _H()
         st = _lib.mgiga_create(C.byref(cp), C.byref(opts), C.byref(self._h))
         if st != OK:

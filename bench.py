@@ -115,6 +115,10 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain-FP64 comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lshape", type=int, default=1,
+                    help="1: also solve the paper's non-matching L-shape (one degree per patch; lshape key)")
+    ap.add_argument("--matrix-free", type=int, default=1,
+                    help="1: also time the matrix-free finest-level residual and a solve with it (matrix_free key)")
     ap.add_argument("--cube", type=int, default=1,
                     help="add the 3D cube configurations (2x2x2 patches, 48 intervals, conforming and SIPG; mixed "
                          "against plain FP64) as the line's 'cube' key: 1 p = 3 (keeps the default run short), "
@@ -226,6 +230,27 @@ def oracle_sample(args):
     return WORKLOADS[args.workload][1].format(smoother=args.smoother)
 
 
+class _single_threaded_children:
+    """One BLAS / OpenMP thread in the processes spawned inside the block: a spawned child imports
+    numpy before any initializer runs, so the limit must be in the environment it inherits.  The
+    variables are put back afterwards, so this process's own OpenMP runtime (the library's host
+    set-up) keeps every core."""
+
+    KEYS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+    def __enter__(self):
+        self.saved = {k: os.environ.get(k) for k in self.KEYS}
+        for k in self.KEYS:
+            os.environ[k] = "1"
+
+    def __exit__(self, *exc):
+        for k, v in self.saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
 def _oracle_worker_init():
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
@@ -265,22 +290,20 @@ class OracleLegs:
     def __init__(self, args, degrees):
         import concurrent.futures as cf
         import multiprocessing as mp
-        # one BLAS / OpenMP thread in every worker: a spawned child imports this module (and numpy)
-        # before any initializer runs, so the limit must be in the environment it inherits
-        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-            os.environ[v] = "1"
         self.args = args
         self.ncpu = os.cpu_count() or 1
-        self.pool = cf.ProcessPoolExecutor(max_workers=max(2, min(self.ncpu, len(degrees) + 7)),
-                                           mp_context=mp.get_context("spawn"), initializer=_oracle_worker_init)
-        # the slowest first: the cube samples (3D, p up to 5), the 192/288 baseline, the 2D samples
-        self.cube = {}
-        if args.cube:
-            for c in ("conforming", "sipg"):
-                for p in ((5, 4, 3) if args.cube >= 2 else (3,)):
-                    self.cube[(c, p)] = self.pool.submit(oracle_job, "solution", p, c, "hybrid")
-        self.base = self.pool.submit(oracle_job, "time", 2, args.scale, args.smoother)
-        self.sol = {p: self.pool.submit(oracle_job, "solution", p, 1, args.smoother) for p in degrees}
+        # workers are spawned as the jobs are submitted (all of them here, inside the block)
+        with _single_threaded_children():
+            self.pool = cf.ProcessPoolExecutor(max_workers=max(2, min(self.ncpu, len(degrees) + 7)),
+                                               mp_context=mp.get_context("spawn"), initializer=_oracle_worker_init)
+            # the slowest first: the cube samples (3D, p up to 5), the 192/288 baseline, the 2D samples
+            self.cube = {}
+            if args.cube:
+                for c in ("conforming", "sipg"):
+                    for p in ((5, 4, 3) if args.cube >= 2 else (3,)):
+                        self.cube[(c, p)] = self.pool.submit(oracle_job, "solution", p, c, "hybrid")
+            self.base = self.pool.submit(oracle_job, "time", 2, args.scale, args.smoother)
+            self.sol = {p: self.pool.submit(oracle_job, "solution", p, 1, args.smoother) for p in degrees}
 
     def baseline(self):
         r = self.base.result()
@@ -302,8 +325,8 @@ class OracleLegs:
         import multiprocessing as mp
         self.pool.shutdown(wait=True)
         n = self.ncpu
-        with cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn"),
-                                    initializer=_oracle_worker_init) as ex:
+        with _single_threaded_children(), cf.ProcessPoolExecutor(
+                max_workers=n, mp_context=mp.get_context("spawn"), initializer=_oracle_worker_init) as ex:
             t0 = time.perf_counter()
             rs = list(ex.map(oracle_job, ["time"] * n, [2] * n, [1] * n, [self.args.smoother] * n))
             wall = time.perf_counter() - t0
@@ -477,6 +500,92 @@ def cube_leg(args, mgiga, W, torch, oracle_sols, reps=3):
             "mixed": {"value": tot["tf32"][0] / (tot["tf32"][1] / 1e3), "unit": "DoF/s",
                       "precision": "tf32 contractions (FP32 SIMT on these 49-51 interiors), fp32 smoothers, fp64 CG"},
             "plain_fp64": {"value": tot["fp64"][0] / (tot["fp64"][1] / 1e3), "unit": "DoF/s"},
+            "per_config": out}
+
+
+def matfree_leg(args, mgiga, W, torch, degrees, solvers, reps=3):
+    """The finest level's cycle residual by sum factorisation at the Gauss points (matrix_free) against
+    the stored FP32 band, per degree on the benchmark layout: device time of one application (CUDA
+    events, mgiga_time_stage), its arithmetic against the FP32 peak (the kernel is bound by its FMAs,
+    not by HBM), the FP32 band bytes it makes unnecessary, and a full mixed solve to 1e-8 with it."""
+    out = {}
+    st = torch.cuda.current_stream()
+    for p, s_band in zip(degrees, solvers):
+        prob, opts = workload(p, args)
+        s = mgiga.Solver(prob, levels=opts["levels"], smoother=opts["smoother"], tau=opts["tau"], delta=opts["delta"],
+                         precision=args.precision, matrix_free=True, stream=st.cuda_stream)
+        t_mf = s.time_stage("residual", -1, reps=10)
+        fl, by = s.stage_work("residual", -1)
+        t_band = s_band.time_stage("residual", -1, reps=10)
+        _, by_band = s_band.stage_work("residual", -1)
+        n = s.ndof()
+        f = torch.from_numpy(s.load_sinprod()).cuda()
+        u = torch.zeros_like(f)
+        times = []
+        for i in range(reps + 1):
+            u.zero_()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(st)
+            it, rel, _ = s.solve_d(f, u, tol=1e-8)
+            eb.record(st)
+            torch.cuda.synchronize()
+            if i:
+                times.append(ea.elapsed_time(eb))
+        fh = f.cpu().numpy()
+        r_true = fh - s.apply("matvec", -1, u.cpu().numpy())
+        s.close()
+        med = float(np.median(times))
+        out[str(p)] = {"residual_ms": round(t_mf, 4), "stored_band_residual_ms": round(t_band, 4),
+                       "achieved_tflops": round(fl / (t_mf / 1e3) / 1e12, 3), "peak_tflops": FP32_PEAK_TFLOPS,
+                       "frac": round(fl / (t_mf / 1e3) / 1e12 / FP32_PEAK_TFLOPS, 4),
+                       "band_bytes_saved": int(by_band - 24 * n),
+                       "solve": {"value": n / (med / 1e3), "unit": "DoF/s", "solve_ms_p50": round(med, 3),
+                                 "iterations": it,
+                                 "true_relres": float(np.linalg.norm(r_true) / np.linalg.norm(fh))}}
+    return {"what": "finest-level cycle residual matrix-free (sum factorisation at the Gauss points, geometry "
+                    "from the control points, FP32) instead of the stored FP32 band; bound: FP32 FMAs "
+                    "(peak derived: 152 SMs x 128 FFMA/clk x 2 x 2.07 GHz)",
+            "per_degree": out}
+
+
+# Table SCMS2 (b) of the paper: PCG iterations, V-cycle with the subspace-corrected mass smoother,
+# non-conforming L-shape (S_{p,h} / S_{p+1,2h} / S_{p,2h}), refinement L = 4..8 (rows), p = 2..6
+PAPER_SCMS2_PCG = {4: [17, 16, 15, 14, 13], 5: [19, 19, 18, 17, 17], 6: [21, 20, 20, 19, 19],
+                   7: [22, 22, 21, 21, 21], 8: [23, 23, 22, 22, 22]}
+
+
+def lshape_leg(args, mgiga, W, torch, refinements=(6, 8), degrees=(2, 3, 4, 5, 6)):
+    """The paper's non-matching L-shape (Sec. 5, Table SCMS2): three patches with S_{p,h},
+    S_{p+1,2h}, S_{p,2h} (one spline degree per patch), SIPG, the subspace-corrected mass smoother
+    with the table's damping .9 and scaling .12, PCG to 1e-8; iterations of the mixed and the plain
+    FP64 path beside the paper's count (its hardware and coarsest grid differ: context only)."""
+    out = {}
+    st = torch.cuda.current_stream()
+    for r in refinements:
+        for p in degrees:
+            prob, o = W.lshape(p, r)
+            rec = {"degrees": prob["degrees"], "paper_pcg_iterations": PAPER_SCMS2_PCG.get(r, [None] * 5)[p - 2]}
+            for pr in ("tf32", "fp64"):
+                s = mgiga.Solver(prob, levels=o["levels"], smoother=o["smoother"], tau=o["tau"], delta=o["delta"],
+                                 precision=pr, stream=st.cuda_stream)
+                f = torch.from_numpy(s.load_sinprod()).cuda()
+                u = torch.zeros_like(f)
+                s.solve_d(f, u, tol=1e-8)
+                u.zero_()
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(st)
+                it, rel, _ = s.solve_d(f, u, tol=1e-8)
+                eb.record(st)
+                torch.cuda.synchronize()
+                fh = f.cpu().numpy()
+                r_true = fh - s.apply("matvec", -1, u.cpu().numpy())
+                rec[pr] = {"iterations": it, "solve_ms": round(ea.elapsed_time(eb), 3),
+                           "true_relres": float(np.linalg.norm(r_true) / np.linalg.norm(fh))}
+                rec["unknowns"], rec["levels"] = s.ndof(), s.levels
+                s.close()
+            out[f"r{r}_p{p}"] = rec
+    return {"workload": "L-shape [0,2]^2 without (1,2]^2, 3 patches, S_{p,h} / S_{p+1,2h} / S_{p,2h} (2^r, "
+                        "2^(r-1), 2^(r-1) intervals), SIPG C = 5 (p+2)^2, SCMS tau .9 delta .12, PCG to 1e-8",
             "per_config": out}
 
 
@@ -732,6 +841,10 @@ def main():
         rec["traffic"] = dram_traffic(st, degrees, args, f32)
         stages[st] = rec
     progress("stage rooflines done")
+    mf = None
+    if args.matrix_free and args.precision != "fp64" and rank == 0:
+        mf = matfree_leg(args, mgiga, W, torch, degrees, solvers)
+        progress("matrix-free residual done")
     dom = max(stages, key=lambda k: stages[k]["share_weight_ms"])
     roof = dict(stages[dom])
     roof["stages"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
@@ -787,7 +900,7 @@ def main():
                                   if concurrent else "sequential"),
                        "gs_cluster": None if args.sequential else cs},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "plain_fp64": plain,
-            "mixed_sequential": mixed_seq, "oracle_error": oracle_err,
+            "mixed_sequential": mixed_seq, "oracle_error": oracle_err, "matrix_free": mf,
             "clocks": clk.summary()}
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -800,6 +913,9 @@ def main():
         csol = legs.cube_solutions() if legs is not None else None
         progress("cube configurations")
         line["cube"] = cube_leg(args, mgiga, W, torch, csol)
+    if args.lshape and args.workload == "sipg3x3" and rank == 0 and world == 1:
+        progress("L-shape, one degree per patch")
+        line["lshape_nonmatching"] = lshape_leg(args, mgiga, W, torch)
     if legs is not None:
         progress("all-core oracle leg")
         line["cpu_all_cores"] = legs.all_cores()

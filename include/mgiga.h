@@ -92,9 +92,16 @@ typedef struct {
 } mgiga_interface;
 
 /* Problem statement (Sec. 2 Eq. omega:1/2 and Eq. local; Sec. 3).
- * All patches share the spline degree `degree` (p >= 1) in every direction,
- * maximal smoothness (simple interior knots) and open knot vectors (end
- * multiplicity p + 1).  The knot vector of level l-1 keeps every other
+ * Every patch has one spline degree p_k >= 1 in all directions, maximal
+ * smoothness (simple interior knots) and open knot vectors (end multiplicity
+ * p_k + 1).  degrees: NULL (every patch has degree `degree`) or num_patches
+ * degrees, one per patch, whose largest must equal `degree` -- the
+ * non-matching spaces of the SIPG experiments of Sec. 5 (Table SCMS2: one
+ * third of the patches S_{p,h}, one third S_{p+1,2h}, one third S_{p,2h});
+ * conforming coupling needs equal degrees on both sides of every interface.
+ * The patch bands of all levels then span offsets -degree .. degree (the
+ * coefficients beyond a patch's own degree are zero) and the Gauss-Seidel
+ * colours use degree + 1 as modulus.  The knot vector of level l-1 keeps every other
  * breakpoint of level l (uniform refinement, Sec. 2), so every direction of
  * every patch needs an even number of intervals on all but the coarsest level.
  *   num_knots[k*dim + a]      length of the knot vector of patch k, direction a
@@ -123,6 +130,7 @@ typedef struct {
   const mgiga_interface* interfaces;
   int coupling;
   double sipg_penalty;
+  const int* degrees;
 } mgiga_problem;
 
 /* Solver options.  levels: number of grid levels (0 = coarsen while every

@@ -40,6 +40,21 @@ def shape_of(knots_k, p):
     return tuple(bspline.num_basis(t, p) for t in knots_k)
 
 
+def degree_of(problem, k):
+    """Spline degree of patch k (the same in every direction): problem["degrees"][k] when the
+    problem lists one per patch (the non-matching setting of the SIPG experiments of Sec. 5,
+    Table SCMS2: one third of the patches carry S_{p,h}, one third S_{p+1,2h} and one third
+    S_{p,2h}), else problem["degree"]."""
+    dk = problem.get("degrees")
+    return int(problem["degree"] if dk is None else dk[k])
+
+
+def max_degree(problem):
+    """Largest patch degree (the reach of the patch band, the modulus of the colouring)."""
+    dk = problem.get("degrees")
+    return int(problem["degree"] if dk is None else max(dk))
+
+
 def unflatten(flat, shape):
     """Multi-index (i_0, ..., i_{d-1}) of local flat index (xi_0 fastest)."""
     out = []
@@ -176,8 +191,7 @@ def numbering(problem, knots):
     class of copies is Dirichlet if any copy has a nonzero trace on a
     boundary side.
     """
-    p = problem["degree"]
-    shapes = [shape_of(kn, p) for kn in knots]
+    shapes = [shape_of(kn, degree_of(problem, k)) for k, kn in enumerate(knots)]
     sizes = [int(np.prod(s)) for s in shapes]
     offsets = np.concatenate(([0], np.cumsum(sizes)))
     dir_local = dirichlet_local(problem, shapes)
@@ -273,7 +287,7 @@ def _patch_elements(problem, k, knots_k):
     elements (E0, Q, d, d)/(E0, Q, d), W = tensor weights (E0, Q).
     """
     d = problem["dim"]
-    p = problem["degree"]
+    p = degree_of(problem, k)
     nq = p + 1
     dd = [_direction_data(t, p, nq) for t in knots_k]
     X, J = geometry.eval_grid(problem["geo_degree"], problem["geo_knots"][k],
@@ -326,7 +340,7 @@ def patch_stiffness(problem, k, knots_k):
     the gradient form of Eq. model:discr).  Returned as scipy CSR.
     """
     d = problem["dim"]
-    p = problem["degree"]
+    p = degree_of(problem, k)
     shape = shape_of(knots_k, p)
     n = int(np.prod(shape))
     acc = _Accumulator(n)
@@ -356,7 +370,7 @@ def patch_stiffness(problem, k, knots_k):
 def patch_mass(problem, k, knots_k):
     """Mass matrix M_ij = (B_i, B_j)_{L2(Omega_k)} of patch k (scipy CSR)."""
     d = problem["dim"]
-    p = problem["degree"]
+    p = degree_of(problem, k)
     shape = shape_of(knots_k, p)
     n = int(np.prod(shape))
     acc = _Accumulator(n)
@@ -378,7 +392,7 @@ def patch_load(problem, k, knots_k, f):
     f: vectorised callable of physical points (npts, d) -> (npts,).
     """
     d = problem["dim"]
-    p = problem["degree"]
+    p = degree_of(problem, k)
     shape = shape_of(knots_k, p)
     n = int(np.prod(shape))
     out = np.zeros(n)
@@ -481,7 +495,7 @@ def _side_eval(problem, k, knots_k, side, s_pts):
     per unit tangential parameter measure (Nanson's formula).
     """
     d = problem["dim"]
-    p = problem["degree"]
+    p = degree_of(problem, k)
     shape = shape_of(knots_k, p)
     a = side // 2
     tdirs = tangential_dirs(d, side)
@@ -524,12 +538,13 @@ def interface_matrix(problem, knots, fine_knots, iface):
       (u, v)_B = ([[u]], {grad v}.n)_I,  (u, v)_J = ([[u]], [[v]])_I,
     [[u]] = u_a - u_b, {w} = (w_a + w_b)/2, n the outward normal of patch a
     (Sec. 3, Eq. model:discr2).  Quadrature: p+1 Gauss points on every cell of
-    the union of both sides' breakpoints, in the parameter of side a.
+    the union of both sides' breakpoints, in the parameter of side a, p the
+    larger of the two patches' degrees.
     Returns (flats_a, flats_b, M) with M over [flats_a, flats_b].
     """
     pa, sa, pb, sb, orient = iface
     d = problem["dim"]
-    p = problem["degree"]
+    p = max(degree_of(problem, pa), degree_of(problem, pb))  # points per cell: exact for both sides
     eta = sipg_eta(problem, fine_knots, pa, pb)
     tdir_a = tangential_dirs(d, sa)
     tdir_b = tangential_dirs(d, sb)
@@ -640,7 +655,7 @@ def global_to_local_vectors(num, u):
 def evaluate(problem, knots, local_coeffs, k, xi):
     """Value of the discrete function on patch k at parameter points xi (npts, d)."""
     d = problem["dim"]
-    p = problem["degree"]
+    p = degree_of(problem, k)
     shape = shape_of(knots[k], p)
     vals = [bspline.basis(knots[k][a], p, xi[:, a]) for a in range(d)]
     c = np.asarray(local_coeffs).reshape(tuple(reversed(shape)))

@@ -32,10 +32,10 @@ def auto_levels(problem):
 
 def level_knots(problem, levels):
     """knots[l][k][a] for l = 0 (coarsest) .. levels-1 (finest = the problem's)."""
-    p = problem["degree"]
     out = [problem["knots"]]
     for _ in range(levels - 1):
-        out.append([[bspline.coarsen_knots(t, p) for t in kn] for kn in out[-1]])
+        out.append([[bspline.coarsen_knots(t, discretize.degree_of(problem, k)) for t in kn]
+                    for k, kn in enumerate(out[-1])])
     return out[::-1]
 
 
@@ -59,8 +59,8 @@ def global_prolongation(problem, knots_c, knots_f, num_c, num_f):
     that numbered it); coarse columns of Dirichlet DoFs are dropped: a coarse
     function that vanishes on the boundary is a fine one that does.
     """
-    p = problem["degree"]
-    Pk = [patch_prolongation(knots_c[k], knots_f[k], p) for k in range(len(knots_f))]
+    Pk = [patch_prolongation(knots_c[k], knots_f[k], discretize.degree_of(problem, k))
+          for k in range(len(knots_f))]
     Pblk = sp.block_diag(Pk, format="csr")
     off_f, off_c = num_f["offsets"], num_c["offsets"]
     # fine global DoF g -> row of its owner copy in the block layout

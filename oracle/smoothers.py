@@ -120,11 +120,10 @@ class SCMS:
         self.tau = tau
         self.pieces = pieces
         self.solvers = []
-        p = problem["degree"]
         for pc in pieces:
             if pc["kind"] == "interior":
                 k = pc["patch"]
-                L, _sigma = interior_operator(knots[k], p, delta)
+                L, _sigma = interior_operator(knots[k], discretize.degree_of(problem, k), delta)
                 # interior DoFs of patch k in interior flat order
                 shape = num["shapes"][k]
                 multi = discretize.unflatten(np.arange(int(np.prod(shape))), shape)
@@ -183,17 +182,18 @@ def patch_parity(problem):
 def structural_pattern(problem, knots, num):
     """Couplings of the global DoFs that decide the colouring (integer work).
 
-    Two DoFs couple if some patch holds copies of both whose local indices
-    differ by at most p in every direction, or (SIPG) if they lie in the two
+    Two DoFs couple if some patch k holds copies of both whose local indices
+    differ by at most p_k (that patch's degree) in every direction, or (SIPG)
+    if they lie in the two
     layers next to the two sides of an interface and their tangential
     supports overlap on a set of positive measure.  Returned as a boolean CSR
     matrix (symmetric, diagonal included).
     """
     from . import bspline
     d = problem["dim"]
-    p = problem["degree"]
     rows, cols = [], []
     for k, shape in enumerate(num["shapes"]):
+        p = discretize.degree_of(problem, k)
         l2g = num["loc2glob"][k]
         n = len(l2g)
         multi = discretize.unflatten(np.arange(n), shape)
@@ -218,12 +218,13 @@ def structural_pattern(problem, knots, num):
             ma = discretize.unflatten(fa, num["shapes"][pa])
             mb = discretize.unflatten(fb, num["shapes"][pb])
             ok = np.ones((len(fa), len(fb)), dtype=bool)
+            p_a, p_b = discretize.degree_of(problem, pa), discretize.degree_of(problem, pb)
             for c in range(d - 1):
                 cb = (1 - c) if swap else c
                 tka = knots[pa][ta[c]]
                 tkb = knots[pb][tb[cb]]
-                lo_a, hi_a = tka[ma[ta[c]]], tka[ma[ta[c]] + p + 1]
-                lo_b, hi_b = tkb[mb[tb[cb]]], tkb[mb[tb[cb]] + p + 1]
+                lo_a, hi_a = tka[ma[ta[c]]], tka[ma[ta[c]] + p_a + 1]
+                lo_b, hi_b = tkb[mb[tb[cb]]], tkb[mb[tb[cb]] + p_b + 1]
                 if orient & (1 << cb):
                     lo_b, hi_b = 1.0 - hi_b, 1.0 - lo_b
                 lo = np.maximum(lo_a[:, None], lo_b[None, :])
@@ -247,7 +248,9 @@ def colouring(problem, knots, num):
     """Multicolour ordering of the global DoFs for Gauss-Seidel (integer work).
 
     Base colour of a DoF, from the copy that numbered it (patch k, local
-    multi-index i):  par(k) (p+1)^d + sum_a (i_a mod (p+1)) (p+1)^a.
+    multi-index i):  par(k) (p+1)^d + sum_a (i_a mod (p+1)) (p+1)^a, p the
+    largest patch degree (with per-patch degrees, a patch of lower degree
+    couples over fewer indices, so its base colours still never couple).
     A DoF is moved if it couples with a DoF of lower global index and the
     same base colour, if it couples with a DoF owned by another patch of the
     same parity, or if it has copies in several patches (a conforming
@@ -258,7 +261,7 @@ def colouring(problem, knots, num):
     patches can be swept side by side.)  Returns the colour of every DoF.
     """
     d = problem["dim"]
-    p = problem["degree"]
+    p = discretize.max_degree(problem)  # patches of lower degree reach less: still a valid colouring
     par = patch_parity(problem)
     base = np.zeros(num["ndof"], dtype=np.int64)
     for g, (k, f) in enumerate(num["owner"]):

@@ -55,7 +55,9 @@ struct Interface {
 };
 
 struct Problem {
-  int d = 2, K = 0, p = 1;
+  int d = 2, K = 0, p = 1;  // p: the largest patch degree (the reach of the patch band)
+  std::vector<int> pk;      // degree of every patch (all p unless the problem lists one per patch)
+  int deg(int k) const { return pk.empty() ? p : pk[k]; }
   std::vector<std::array<Vec, 3>> knots;  // finest level
   std::vector<Geometry> geo;
   std::vector<Interface> ifaces;
@@ -70,7 +72,9 @@ void geo_eval(const Problem& pr, int k, const double* xi, double* X, double* J);
 // One grid level: layout, numbering, operator
 // ---------------------------------------------------------------------------
 struct Level {
-  int d = 2, p = 1, K = 0;
+  int d = 2, p = 1, K = 0;  // p: the largest patch degree; band offsets span -p .. p
+  std::vector<int> pk;      // degree of every patch
+  int deg(int k) const { return pk.empty() ? p : pk[k]; }
   std::vector<std::array<Vec, 3>> knots;
   std::vector<std::array<int, 3>> N;  // B-splines per direction (unused dirs: 1)
   std::vector<int64_t> off;           // patch block offsets, K + 1 entries

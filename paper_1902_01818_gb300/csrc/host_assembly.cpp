@@ -50,12 +50,14 @@ struct DSU {
 void build_topology(const Problem& pr, Level& L) {
   const int d = pr.d, K = pr.K, p = pr.p;
   L.d = d; L.p = p; L.K = K;
+  L.pk.assign(K, p);
+  for (int k = 0; k < K; ++k) L.pk[k] = pr.deg(k);
   L.N.assign(K, {{1, 1, 1}});
   L.off.assign(K + 1, 0);
   for (int k = 0; k < K; ++k) {
     int64_t sz = 1;
     for (int a = 0; a < d; ++a) {
-      L.N[k][a] = num_basis(L.knots[k][a], p);
+      L.N[k][a] = num_basis(L.knots[k][a], pr.deg(k));
       sz *= L.N[k][a];
     }
     L.off[k + 1] = L.off[k] + sz;
@@ -216,7 +218,8 @@ double inv_small(const double* J, int d, double* Ji) {
 }  // namespace
 
 static void patch_stiffness(const Problem& pr, Level& L, int k) {
-  const int d = pr.d, p = pr.p, P1 = p + 1, nq = p + 1, W = 2 * p + 1;
+  // p: this patch's degree (its basis and quadrature); the band spans offsets -pr.p .. pr.p
+  const int d = pr.d, p = pr.deg(k), P1 = p + 1, nq = p + 1, W = 2 * pr.p + 1;
   DirQuad dq[3];
   int ne[3] = {1, 1, 1};
   for (int a = 0; a < d; ++a) { dq[a] = dir_quad(L.knots[k][a], p); ne[a] = (int)dq[a].span.size(); }
@@ -232,7 +235,7 @@ static void patch_stiffness(const Problem& pr, Level& L, int k) {
   std::vector<int> ocode(d == 2 ? P1 * P1 : P1 * P1 * P1);
   for (int x = 0; x < (int)ocode.size(); ++x)
     ocode[x] = x % P1 + W * ((x / P1) % P1) + (d == 3 ? W * W * (x / (P1 * P1)) : 0);
-  const int ocode0 = p + W * p + (d == 3 ? W * W * p : 0);
+  const int ocode0 = pr.p + W * pr.p + (d == 3 ? W * W * pr.p : 0);
   // element slabs along the slowest direction touch disjoint band rows when
   // they are p+1 apart: p+1 parallel phases
   // (in 3D the rows of elements along xi_0 are coloured by both outer indices
@@ -433,7 +436,7 @@ struct SideFun {
 // nonzero functions (two layers next to the side) of patch k at side point xi
 void side_functions(const Problem& pr, const Level& L, int k, int side, const double* xi,
                     std::vector<SideFun>& out, double* normal, double* dS) {
-  const int d = pr.d, p = pr.p, P1 = p + 1;
+  const int d = pr.d, p = pr.deg(k), P1 = p + 1;
   double X[3], J[9], Ji[9];
   geo_eval(pr, k, xi, X, J);
   const double det = inv_small(J, d, Ji);
@@ -500,7 +503,8 @@ double grid_size(const std::array<Vec, 3>& kn, int d) {
 static void interface_terms(const Problem& pr, Level& L, const Interface& f,
                             const std::vector<std::array<Vec, 3>>& fine_knots,
                             std::unordered_map<uint64_t, double>& cross) {
-  const int d = pr.d, p = pr.p;
+  // p: the larger degree of the two sides (Gauss points per cell exact for both sides' products)
+  const int d = pr.d, p = std::max(pr.deg(f.pa), pr.deg(f.pb));
   const double eta = pr.penalty / std::min(grid_size(fine_knots[f.pa], d), grid_size(fine_knots[f.pb], d));
   const auto ta = tangential(d, f.sa), tb = tangential(d, f.sb);
   const int m = d - 1;
@@ -623,8 +627,8 @@ static void interface_terms(const Problem& pr, Level& L, const Interface& f,
             for (int a = 0; a < d; ++a) {
               const int ir = (int)(rem_r % L.N[kr][a]), ic = (int)(rem_c % L.N[kr][a]);
               rem_r /= L.N[kr][a]; rem_c /= L.N[kr][a];
-              o += (ic - ir + p) * mul;
-              mul *= 2 * p + 1;
+              o += (ic - ir + pr.p) * mul;  // the band spans the largest degree of all patches
+              mul *= 2 * pr.p + 1;
             }
             L.band_add.push_back({(int64_t)o * L.nloc + r, v});
             if (!L.band.empty()) L.band[(size_t)o * L.nloc + r] += v;
@@ -708,9 +712,10 @@ void apply_dirichlet(Level& L) {
 
 void assemble_load(const Problem& pr, const Level& L, double (*fn)(const double*, void*), void* ctx,
                    double* out) {
-  const int d = pr.d, p = pr.p, P1 = p + 1, nq = p + 1;
+  const int d = pr.d;
   Vec loc(L.nloc, 0.0);
   for (int k = 0; k < pr.K; ++k) {
+    const int p = pr.deg(k), P1 = p + 1, nq = p + 1;
     DirQuad dq[3];
     int ne[3] = {1, 1, 1};
     for (int a = 0; a < d; ++a) { dq[a] = dir_quad(L.knots[k][a], p); ne[a] = (int)dq[a].span.size(); }

@@ -44,7 +44,8 @@ Transfer build_transfer(const Level& C, const Level& F) {
     for (int a = 0; a < F.d; ++a) {
       auto key = std::make_pair(C.knots[k][a], F.knots[k][a]);
       auto it = cache.find(key);
-      if (it == cache.end()) it = cache.emplace(key, prolongation_1d(C.knots[k][a], F.knots[k][a], F.p)).first;
+      // (the knot vectors carry the degree through their end multiplicity, so they key the cache)
+      if (it == cache.end()) it = cache.emplace(key, prolongation_1d(C.knots[k][a], F.knots[k][a], F.deg(k))).first;
       T.P[k][a] = it->second;
     }
   return T;
@@ -304,7 +305,7 @@ FDData fd_setup(const Level& L, int k, double delta) {
   fd.sigma = 1.0 / (delta * h * h);
   for (int a = 0; a < L.d; ++a) {
     Vec Kf, Mf;
-    param_matrices(L.knots[k][a], L.p, Kf, Mf);
+    param_matrices(L.knots[k][a], L.deg(k), Kf, Mf);
     const int N = L.N[k][a], n = N - 2;
     fd.n[a] = n;
     Vec Ki((size_t)n * n), Mi((size_t)n * n);
@@ -378,9 +379,10 @@ std::vector<int> patch_parity(const Problem& pr) {
 static void structural_neighbours(const Problem& pr, const Level& L, int g,
                                   const std::vector<std::vector<int64_t>>& copies_of,
                                   const std::vector<std::vector<int>>& iface_nb, std::vector<int>& out) {
-  const int d = L.d, p = L.p;
+  const int d = L.d;
   for (int64_t pos : copies_of[g]) {
     const int k = L.patch_of[pos];
+    const int p = L.deg(k);  // the patch's own reach
     int64_t rem = pos - L.off[k];
     int idx[3] = {0, 0, 0};
     for (int a = 0; a < d; ++a) { idx[a] = (int)(rem % L.N[k][a]); rem /= L.N[k][a]; }
@@ -399,6 +401,7 @@ static void structural_neighbours(const Problem& pr, const Level& L, int g,
 }
 
 std::vector<int> colouring(const Problem& pr, const Level& L) {
+  // base colours modulo the largest degree + 1: a patch of lower degree couples over fewer indices
   const int d = L.d, p = L.p;
   const auto par = patch_parity(pr);
   int pw = 1;
@@ -459,8 +462,8 @@ std::vector<int> colouring(const Problem& pr, const Level& L) {
             const Vec& tka = L.knots[f.pa][ta[c]];
             const Vec& tkb = L.knots[f.pb][tb[cb]];
             const int ia = tidx(qa, f.pa, ta[c]), ib = tidx(qb, f.pb, tb[cb]);
-            const double lo_a = tka[ia], hi_a = tka[ia + p + 1];
-            double lo_b = tkb[ib], hi_b = tkb[ib + p + 1];
+            const double lo_a = tka[ia], hi_a = tka[ia + L.deg(f.pa) + 1];
+            double lo_b = tkb[ib], hi_b = tkb[ib + L.deg(f.pb) + 1];
             if ((f.orient >> cb) & 1u) { const double t = lo_b; lo_b = 1.0 - hi_b; hi_b = 1.0 - t; }
             const double lo = std::max(lo_a, lo_b), hi = std::min(hi_a, hi_b);
             ok = hi - lo > 1e-12;

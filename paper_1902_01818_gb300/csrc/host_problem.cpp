@@ -1,6 +1,7 @@
 // Import and validation of the C problem statement (patches, knot vectors,
 // degree, geometry control points, interface pairing, SIPG penalty; Sec. 2-3)
 // into the host representation of the set-up.
+#include <algorithm>
 #include <cstdint>
 
 #include "host_problem.hpp"
@@ -21,6 +22,16 @@ void import_problem(const mgiga_problem* P, Problem& pr) {
   pr.d = P->dim;
   pr.K = P->num_patches;
   pr.p = P->degree;
+  pr.pk.assign(pr.K, P->degree);
+  if (P->degrees) {  // one degree per patch: degree must be the largest
+    int mx = 0;
+    for (int k = 0; k < pr.K; ++k) {
+      if (P->degrees[k] < 1 || P->degrees[k] > 8) throw SetupError(MGIGA_EINVAL, "degrees[k] must be in 1..8");
+      pr.pk[k] = P->degrees[k];
+      mx = std::max(mx, P->degrees[k]);
+    }
+    if (mx != P->degree) throw SetupError(MGIGA_EINVAL, "degree must be the largest of degrees[]");
+  }
   pr.coupling = P->coupling;
   pr.penalty = P->sipg_penalty;
   pr.knots.assign(pr.K, {});
@@ -28,17 +39,18 @@ void import_problem(const mgiga_problem* P, Problem& pr) {
   size_t kk = 0, gk = 0, gc = 0;
   for (int k = 0; k < pr.K; ++k) {
     int64_t ncp = 1;
+    const int pk = pr.pk[k];
     for (int a = 0; a < pr.d; ++a) {
       const int n = P->num_knots[k * pr.d + a];
-      if (n < 2 * pr.p + 2) throw SetupError(MGIGA_EINVAL, "knot vector too short");
+      if (n < 2 * pk + 2) throw SetupError(MGIGA_EINVAL, "knot vector too short");
       Vec t(P->knots + kk, P->knots + kk + n);
       kk += n;
       for (int i = 0; i + 1 < n; ++i)
         if (!(t[i] <= t[i + 1])) throw SetupError(MGIGA_EINVAL, "knot vector not nondecreasing");
-      for (int i = 0; i <= pr.p; ++i)
+      for (int i = 0; i <= pk; ++i)
         if (t[i] != 0.0 || t[n - 1 - i] != 1.0)
           throw SetupError(MGIGA_EINVAL, "knot vectors must be open on [0, 1] (end multiplicity p+1)");
-      for (int i = pr.p + 1; i + 1 < n - pr.p - 1; ++i)
+      for (int i = pk + 1; i + 1 < n - pk - 1; ++i)
         if (t[i] == t[i + 1]) throw SetupError(MGIGA_EINVAL, "interior knots must be simple (maximal smoothness)");
       pr.knots[k][a] = t;
       const int gn = P->geo_num_knots[k * pr.d + a];
@@ -59,6 +71,8 @@ void import_problem(const mgiga_problem* P, Problem& pr) {
     if (f.side_a < 0 || f.side_a >= 2 * pr.d || f.side_b < 0 || f.side_b >= 2 * pr.d)
       throw SetupError(MGIGA_EINVAL, "bad interface side");
     if (f.orient > (pr.d == 3 ? 7u : 1u)) throw SetupError(MGIGA_EINVAL, "bad interface orientation");
+    if (P->coupling == MGIGA_CONFORMING && pr.pk[f.patch_a] != pr.pk[f.patch_b])
+      throw SetupError(MGIGA_EINVAL, "conforming coupling needs the same degree on both sides of an interface");
     pr.ifaces.push_back({f.patch_a, f.side_a, f.patch_b, f.side_b, f.orient});
   }
 }
@@ -69,7 +83,7 @@ void init_levels(const Problem& pr, int lv, std::vector<Level>& L) {
   for (int l = lv - 1; l > 0; --l) {
     L[l - 1].knots.resize(pr.K);
     for (int k = 0; k < pr.K; ++k)
-      for (int a = 0; a < pr.d; ++a) L[l - 1].knots[k][a] = coarsen_knots(L[l].knots[k][a], pr.p);
+      for (int a = 0; a < pr.d; ++a) L[l - 1].knots[k][a] = coarsen_knots(L[l].knots[k][a], pr.deg(k));
   }
   for (int l = 0; l < lv; ++l) build_topology(pr, L[l]);
 }

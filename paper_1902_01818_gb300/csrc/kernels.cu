@@ -953,19 +953,39 @@ __global__ void __launch_bounds__(256) gemm_umma_tf32(const GemmTask* __restrict
   }
   __syncthreads();
   if (ok && nst > 0) {
-    for (int idx = tid; idx < UM * UN; idx += 256) {
-      const int r = g.ctrans ? idx % UM : idx / UN, c = g.ctrans ? idx / UM : idx % UN;
-      const int m = m0 + r, n = n0 + c;
-      if (m >= g.M || n >= g.N) continue;
-      float acc = tile[r * TP + c];
-      const int64_t ci = oC + (g.ctrans ? (int64_t)n * g.ldc + m : (int64_t)m * g.ldc + gcol(g, n));
-      if (g.epi == 1) acc *= static_cast<const float*>(g.dinv)[(int64_t)m * g.ldd + n];
+    // EB elements per thread at a time: their global reads (the eigenvalue table, or the output
+    // that is updated) are issued together, not one dependent load after another
+    constexpr int EB = 8;
+    for (int base = 0; base < UM * UN; base += 256 * EB) {
+      float acc[EB], ext[EB];
+      int64_t cix[EB];
+      bool live[EB];
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        const int idx = base + j * 256 + tid;
+        const int r = g.ctrans ? idx % UM : idx / UN, c = g.ctrans ? idx / UM : idx % UN;
+        const int m = m0 + r, n = n0 + c;
+        live[j] = idx < UM * UN && m < g.M && n < g.N;
+        acc[j] = live[j] ? tile[r * TP + c] : 0.0f;
+        cix[j] = live[j] ? oC + (g.ctrans ? (int64_t)n * g.ldc + m : (int64_t)m * g.ldc + gcol(g, n)) : 0;
+        ext[j] = (live[j] && g.epi == 1) ? static_cast<const float*>(g.dinv)[(int64_t)m * g.ldd + n] : 1.0f;
+      }
       if (g.tC) {
-        float* cp = static_cast<float*>(g.C) + ci;
-        *cp = g.epi == 2 ? *cp + (float)(g.alpha * acc) : acc;
+        float* C = static_cast<float*>(g.C);
+        float old[EB];
+#pragma unroll
+        for (int j = 0; j < EB; ++j) old[j] = (live[j] && g.epi == 2) ? C[cix[j]] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < EB; ++j)
+          if (live[j]) C[cix[j]] = g.epi == 2 ? old[j] + (float)(g.alpha * acc[j]) : acc[j] * ext[j];
       } else {
-        double* cp = static_cast<double*>(g.C) + ci;
-        *cp = g.epi == 2 ? *cp + g.alpha * (double)acc : (double)acc;
+        double* C = static_cast<double*>(g.C);
+        double old[EB];
+#pragma unroll
+        for (int j = 0; j < EB; ++j) old[j] = (live[j] && g.epi == 2) ? C[cix[j]] : 0.0;
+#pragma unroll
+        for (int j = 0; j < EB; ++j)
+          if (live[j]) C[cix[j]] = g.epi == 2 ? old[j] + g.alpha * (double)acc[j] : (double)(acc[j] * ext[j]);
       }
     }
   }
@@ -1110,8 +1130,24 @@ __device__ __forceinline__ void gs_rows(const GsSweepArgs& a, int64_t base, int6
       for (int o0 = 0; o0 < W; ++o0) acc = fma(__ldg(br + (int64_t)o0 * a.ngs), (TB)__ldcg(ur + o0), acc);
     }
     // SIPG couplings across interfaces and, for a DoF shared by conforming patches, the band rows
-    // of its further copies (their diagonals are part of the entry's), shared over the row's lanes
-    for (int j = xr.x + sub; j < xr.y; j += TPR) acc = fma((TB)a.x_val[j], (TB)__ldcg(a.u + a.x_col[j]), acc);
+    // of its further copies (their diagonals are part of the entry's), shared over the row's lanes;
+    // four entries per lane in flight (the column then the value: two dependent loads each), summed
+    // in the same order as one at a time
+    int j = xr.x + sub;
+    for (; j + 3 * TPR < xr.y; j += 4 * TPR) {
+      int64_t c[4];
+      double v[4], w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        c[q] = a.x_col[j + q * TPR];
+        v[q] = a.x_val[j + q * TPR];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[q] = __ldcg(a.u + c[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc = fma((TB)v[q], (TB)w[q], acc);
+    }
+    for (; j < xr.y; j += TPR) acc = fma((TB)a.x_val[j], (TB)__ldcg(a.u + a.x_col[j]), acc);
   }
 #pragma unroll
   for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

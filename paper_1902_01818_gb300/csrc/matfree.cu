@@ -599,6 +599,10 @@ bool mf_supported(const Problem& pr, std::string* why) {
     return false;
   }
   for (int k = 0; k < pr.K; ++k) {
+    if (pr.deg(k) != pr.p) {
+      if (why) *why = "one degree for all patches";
+      return false;
+    }
     const Geometry& g = pr.geo[k];
     if (g.q > 2) {
       if (why) *why = "geometry degree <= 2 (patch " + std::to_string(k) + ")";

@@ -147,7 +147,7 @@ struct DLevel {
   double* gs_band = nullptr;  // band rows of the owner copies in colour order
   float* band32 = nullptr;    // FP32 band (mixed path): residuals inside the cycle
   int* gs_cptr_d = nullptr;
-  int gs_blocks = 0;
+  int gs_blocks = 0, gs_blocks_tail = 0;  // cooperative grid: all colours / the colours after the base ones
   std::vector<int> gs_cptr;
   int arith = 0;              // smoother arithmetic: 0 FP64, 1 FP32, 2 FP32 + TF32 tensor-core FD,
                               // 3 FP32 + BF16 tensor-core FD
@@ -1289,6 +1289,12 @@ void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L,
   const int coop = gs_coop_max_blocks(L.d, L.p, f32);
   if (coop <= 0) throw CudaError("cooperative launch not available for the Gauss-Seidel sweep");
   dl.gs_blocks = std::max(1, std::min(coop, (maxrows * 8 + 255) / 256));
+  // the colours after the base colours (swept grid-wide after the patch-parallel phases): blocks
+  // for their largest colour only (few rows each: a small grid keeps the grid barrier short)
+  int maxrows_tail = 1;
+  for (size_t c = std::min<size_t>(2 * B, dl.gs_cptr.size() - 1); c + 1 < dl.gs_cptr.size(); ++c)
+    maxrows_tail = std::max(maxrows_tail, dl.gs_cptr[c + 1] - dl.gs_cptr[c]);
+  dl.gs_blocks_tail = dl.gs_csize > 0 ? std::max(1, std::min(coop, (maxrows_tail * 8 + 255) / 256)) : dl.gs_blocks;
   if (std::getenv("MGIGA_VERBOSE"))
     std::fprintf(stderr,
                  "mgiga: gs level ndof %d colours %d base %d cluster %d smem %d buffers %d x %d bytes threads %d "
@@ -1401,16 +1407,16 @@ void gs_sweep(mgiga_handle* h, int l, bool forward) {
   a.err = h->gs_err;
   const bool f32 = d.arith >= 1;
   const int B = d.gs_base;
-  auto coop = [&](int cb, int ce) {
+  auto coop = [&](int cb, int ce, int blocks) {
     a.c_begin = std::min(cb, ncol);
     a.c_end = std::min(ce, ncol);
     if (a.c_end <= a.c_begin) return;
     CK(cudaMemsetAsync(h->gs_bar, 0, 2 * sizeof(unsigned int), h->stream));
-    CK(launch_gs_sweep(L.d, L.p, f32, d.gs_blocks, h->stream, a));
+    CK(launch_gs_sweep(L.d, L.p, f32, blocks, h->stream, a));
   };
   auto phase = [&](int ph) {
     if (d.gs_csize == 0) {  // no staged plan (FP64 path, or slabs too large): grid-wide sweep
-      coop(ph * B, (ph + 1) * B);
+      coop(ph * B, (ph + 1) * B, d.gs_blocks);
       return;
     }
     GsStagedArgs g = d.gs_staged;
@@ -1428,7 +1434,7 @@ void gs_sweep(mgiga_handle* h, int l, bool forward) {
                          d.gs_xcol, d.gs_xval, d.f, d.u, d.gs_pool);
     CK(launch_gs_staged(L.d, L.p, d.gs_nphase[ph], d.gs_smem, h->stream, g));
   };
-  auto tail = [&]() { coop(2 * B, ncol); };
+  auto tail = [&]() { coop(2 * B, ncol, d.gs_blocks_tail); };
   if (forward) { phase(0); phase(1); tail(); }
   else { tail(); phase(1); phase(0); }
 }
@@ -1744,7 +1750,10 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
     // 3D: the element stiffness stays on the host (the device kernel measured slower there: cube,
     // 48 intervals, p = 5: 49 s against 38 s on 16 host cores); its Galerkin products run on the GPU
     const char* s3_env = std::getenv("MGIGA_GPU_STIFFNESS_3D");  // the 3D device kernel, for testing
-    const bool gpu_stiffness = gpu_setup && (h->pr.d == 2 || (s3_env && s3_env[0] == '1'));
+    // (patches of different degrees: the element stiffness on the host, one degree per patch)
+    bool uniform = true;
+    for (int k = 0; k < h->pr.K; ++k) uniform = uniform && h->pr.deg(k) == h->pr.p;
+    const bool gpu_stiffness = gpu_setup && uniform && (h->pr.d == 2 || (s3_env && s3_env[0] == '1'));
     std::vector<std::pair<int64_t, double>> mf_self;  // within-patch SIPG terms for the matrix-free residual
     if (gpu_setup) {
       Level& F = h->L[lv - 1];

@@ -50,7 +50,7 @@ class _Problem(C.Structure):
                 ("geo_degree", C.c_int), ("geo_num_knots", C.POINTER(C.c_int)),
                 ("geo_knots", C.POINTER(C.c_double)), ("geo_ctrl", C.POINTER(C.c_double)),
                 ("num_interfaces", C.c_int), ("interfaces", C.POINTER(_Interface)),
-                ("coupling", C.c_int), ("sipg_penalty", C.c_double)]
+                ("coupling", C.c_int), ("sipg_penalty", C.c_double), ("degrees", C.POINTER(C.c_int))]
 
 
 class _Options(C.Structure):
@@ -131,10 +131,14 @@ def marshal_problem(prob):
     ifs = (_Interface * max(1, len(prob["interfaces"])))()
     for i, (pa, sa, pb, sb, o) in enumerate(prob["interfaces"]):
         ifs[i] = _Interface(pa, sa, pb, sb, o)
-    keep = (nk, kn, gnk, gkn, gctrl, ifs)
+    degs = None
+    if prob.get("degrees") is not None:  # one degree per patch; `degree` is their largest
+        degs = np.ascontiguousarray(prob["degrees"], dtype=np.int32)
+    keep = (nk, kn, gnk, gkn, gctrl, ifs, degs)
     cp = _Problem(d, K, p, nk.ctypes.data_as(_I), _dptr(kn), prob["geo_degree"], gnk.ctypes.data_as(_I),
                   _dptr(gkn), _dptr(gctrl), len(prob["interfaces"]), ifs,
-                  CONFORMING if prob["coupling"] == "conforming" else SIPG, float(prob.get("sipg_penalty", 0.0)))
+                  CONFORMING if prob["coupling"] == "conforming" else SIPG, float(prob.get("sipg_penalty", 0.0)),
+                  degs.ctypes.data_as(_I) if degs is not None else None)
     return cp, keep
 
 

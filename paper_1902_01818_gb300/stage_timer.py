@@ -1,7 +1,7 @@
 """Per-level stage times of the V-cycle on the SIPG 3x3 benchmark layout (or the 3D cube).
 
     python -m paper_1902_01818_gb300.stage_timer --degree 6 --precision fp32 \
-        [--levels 5] [--stages gs,fd] [--reps 5] [--scale 3] [--workload cube-sipg]
+        [--levels 5] [--stages gs,fd] [--reps 5] [--scale 3] [--workload cube-sipg] [--matrix-free]
 
 The first line gives the wall time of the handle's set-up (MGIGA_VERBOSE=1
 prints its phases on stderr).
@@ -33,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--stages", default="band,residual,fd,pieces,gs,restrict,prolong,coarse,vcycle")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--gs-cluster", type=int, default=0, help="0 automatic, or 2/4/8/16 (see mgiga_options)")
+    ap.add_argument("--matrix-free", action="store_true",
+                    help="the finest level's cycle residual by sum factorisation (mgiga_options.matrix_free)")
     args = ap.parse_args(argv)
 
     from . import mgiga  # loads libmgiga.so (CUDA)
@@ -43,7 +45,7 @@ def main(argv=None):
         prob, opts = W.cube_2x2x2(args.degree, args.workload.split("-")[1])
     t0 = time.perf_counter()
     s = mgiga.Solver(prob, levels=0, smoother=args.smoother, tau=opts["tau"], delta=opts["delta"],
-                     precision=args.precision, gs_cluster=args.gs_cluster)
+                     precision=args.precision, gs_cluster=args.gs_cluster, matrix_free=args.matrix_free)
     setup = time.perf_counter() - t0
     nl = s.levels
     levels = list(range(nl - 1, -1, -1)) if args.levels == "all" else [int(x) % nl for x in args.levels.split(",")]

@@ -221,6 +221,41 @@ def sipg_3x3(p, scale=1, smoother="scms"):
     return prob, opts
 
 
+def with_patch_degrees(prob, degrees):
+    """The same patches (same interval counts) with spline degree degrees[k] on patch k: knot
+    vectors rebuilt per patch, `degree` the largest, the SIPG penalty factor 5 (p + 1)^2 taken
+    with that largest degree."""
+    out = dict(prob)
+    out["degrees"] = [int(x) for x in degrees]
+    out["degree"] = max(out["degrees"])
+    out["knots"] = [[uniform_knots(len(np.unique(t)) - 1, pk) for t in kn]
+                    for kn, pk in zip(prob["knots"], out["degrees"])]
+    out["sipg_penalty"] = 5.0 * (out["degree"] + 1) ** 2
+    return out
+
+
+def lshape(p, r, nonmatching=True, smoother="scms"):
+    """The L-shaped domain of the paper's experiments (Sec. 2: three quadrilaterals whose
+    geometry maps are the identity or a translation): [0,2]^2 without (1,2]^2, patches [0,1]^2,
+    [1,2]x[0,1], [0,1]x[1,2].  Patch 0 has 2^r intervals per direction.  nonmatching (the SIPG
+    setting of Sec. 5, Table SCMS2): patch 0 carries S_{p,h}, patch 1 S_{p+1,2h}, patch 2
+    S_{p,2h}; else all three S_{p,h} with SIPG coupling.  f from u = sin(pi x) sin(pi y), which
+    vanishes on the whole boundary.  Options: the subspace-corrected mass smoother with the
+    table's damping .9 and scaling .12 (smoother="hybrid": .25 / .1), PCG; levels: coarsen until
+    the coarse patches have 2 intervals (the paper's coarsest grid has one element per patch)."""
+    cells = [(0, 0), (1, 0), (0, 1)]
+    n_of = {0: 2 ** r, 1: 2 ** (r - 1) if nonmatching else 2 ** r, 2: 2 ** (r - 1) if nonmatching else 2 ** r}
+
+    def n(cidx, a):
+        return n_of[cells.index(tuple(cidx))]
+    prob = grid_problem((2, 2), n, p, "sipg", box=(2.0, 2.0), jitter=0.0, active=cells)
+    if nonmatching:
+        prob = with_patch_degrees(prob, [p, p + 1, p])
+    opts = (dict(levels=0, smoother="scms", tau=0.9, delta=0.12) if smoother == "scms"
+            else dict(levels=0, smoother="hybrid", tau=0.25, delta=0.1))
+    return prob, opts
+
+
 def cube_2x2x2(p, coupling, n=48):
     """[0,1]^3 as 2x2x2 trilinear patches: centre vertex jittered U[-.05,.05]^3,
     boundary non-corner vertices jittered tangentially; hybrid smoother

@@ -7,8 +7,7 @@ from oracle import bspline, discretize, geometry
 
 def full_numbering(problem, knots):
     """A numbering that keeps every local DoF (no Dirichlet, no sharing)."""
-    p = problem["degree"]
-    shapes = [discretize.shape_of(kn, p) for kn in knots]
+    shapes = [discretize.shape_of(kn, discretize.degree_of(problem, k)) for k, kn in enumerate(knots)]
     sizes = [int(np.prod(s)) for s in shapes]
     offsets = np.concatenate(([0], np.cumsum(sizes)))
     l2g = [offsets[k] + np.arange(sizes[k]) for k in range(len(sizes))]
@@ -32,11 +31,11 @@ def patch_values(problem, knots, num, u, k, xi):
 
 def l2_error(problem, num, u, exact, nq=None):
     """L2(Omega) error of the discrete solution by per-element Gauss quadrature (2D)."""
-    p = problem["degree"]
-    nq = nq or p + 3
     locs = discretize.global_to_local_vectors(num, u)
     err2 = 0.0
     for k, kn in enumerate(problem["knots"]):
+        p = discretize.degree_of(problem, k)
+        nq = nq or discretize.max_degree(problem) + 3
         xs, ws = [], []
         for t in kn:
             x, w, _ = bspline.element_quadrature(t, nq)

@@ -45,6 +45,15 @@ CASES = {
                                               active=[(0, 0), (1, 0), (0, 1)]), 2),
     "lshape_sipg_p2": (lambda: W.grid_problem((2, 2), _nm, 2, "sipg", jitter=0.1, seed=6,
                                               active=[(0, 0), (1, 0), (0, 1)]), 2),
+    # one degree per patch (Sec. 5, Table SCMS2): S_{p,h} / S_{p+1,2h} / S_{p,2h} on the L-shape,
+    # and mixed degrees on jittered, flipped / transposed 2D and 3D grids
+    "lshape_nonmatching_p3": (lambda: W.lshape(3, 4)[0], 3),
+    "mixed2d_1232": (lambda: W.with_patch_degrees(W.grid_problem((2, 2), _nm, 3, "sipg", jitter=0.1, seed=31,
+                                                                 flip_patches=(1,), transpose_patches=(2,)),
+                                                  [1, 2, 3, 2]), 3),
+    "mixed3d_23": (lambda: W.with_patch_degrees(W.grid_problem((2, 1, 2), lambda c, a: 2 if sum(c) % 2 == 0 else 4, 3,
+                                                               "sipg", jitter=0.05, seed=32, flip_patches=(1,)),
+                                                [2, 3, 3, 2]), 2),
 }
 
 

@@ -40,6 +40,12 @@ def _cases():
         ("sipg3d", W.grid_problem((2, 1, 2), nm, 2, "sipg", jitter=0.05, seed=4, flip_patches=(1,),
                                   transpose_patches=(2,)), 2),
         ("lshape_like", W.grid_problem((2, 2), 4, 1, "conforming"), 2),
+        # one degree per patch (Sec. 5, Table SCMS2): the L-shape S_{p,h} / S_{p+1,2h} / S_{p,2h}
+        ("lshape_nonmatching", W.lshape(2, 5)[0], 3),
+        ("mixed2d", W.with_patch_degrees(W.grid_problem((2, 2), nm, 3, "sipg", jitter=0.1, seed=31,
+                                                        flip_patches=(1,)), [1, 2, 3, 2]), 3),
+        ("mixed3d", W.with_patch_degrees(W.grid_problem((2, 1, 1), lambda c, a: 4 if c[0] == 0 else 6, 3, "sipg",
+                                                        jitter=0.05, seed=32), [2, 3]), 2),
     ]
 
 
@@ -141,3 +147,18 @@ def test_residual_history_is_empty_before_a_solve():
     s = mg.Solver(prob, levels=2, assemble=False)
     assert s.residual_history().size == 0
     s.close()
+
+
+def test_patch_degrees_validated():
+    """One degree per patch: `degree` must be their largest, and conforming coupling needs equal
+    degrees on both sides of an interface (a continuous space across it)."""
+    mg = binding()
+    prob = W.with_patch_degrees(W.grid_problem((2, 1), 4, 3, "conforming"), [2, 3])
+    with pytest.raises(mg.MgigaError) as e:
+        mg.Solver(prob, levels=2, assemble=False)
+    assert e.value.status == mg.EINVAL and "same degree" in str(e.value)
+    prob = W.with_patch_degrees(W.grid_problem((2, 1), 4, 3, "sipg"), [2, 3])
+    prob["degree"] = 4
+    with pytest.raises(mg.MgigaError) as e:
+        mg.Solver(prob, levels=2, assemble=False)
+    assert e.value.status == mg.EINVAL and "largest" in str(e.value)

@@ -1,0 +1,154 @@
+"""Pins of the oracle with one spline degree per patch (the non-matching SIPG setting of Sec. 5,
+Table SCMS2: S_{p,h}, S_{p+1,2h}, S_{p,2h} on different patches of the L-shaped domain of Sec. 2).
+
+What fixes the result independently of the code: the SIPG form stays symmetric, kills constants
+before the Dirichlet elimination and is SPD after it (Sec. 3, Theorem 2 setting) whatever the
+spaces on the two sides; it is consistent, so a polynomial that lies in every patch space and
+vanishes on the boundary is reproduced exactly; listing the same degree for every patch is the
+scalar-degree problem; the multicolour ordering stays a valid colouring; the V-cycle still
+contracts (spectral radius of I - BA below 1) with a symmetric preconditioner; the coarse levels
+keep each patch's degree.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import discretize, geometry, hierarchy, mg, smoothers
+from paper_1902_01818_gb300 import workloads as W
+from oracle_helpers import full_numbering, solve_discrete, patch_values, l2_error
+
+
+def _mixed_grid(degrees, seed=5, jitter=0.1):
+    def nm(c, a):
+        return 3 if (c[0] + c[1]) % 2 == 0 else 4
+    prob = W.grid_problem((2, 2), nm, max(degrees), "sipg", jitter=jitter, seed=seed, flip_patches=(1,))
+    return W.with_patch_degrees(prob, degrees)
+
+
+@pytest.mark.parametrize("degrees", [[1, 2, 3, 2], [2, 3, 2, 4], [3, 1, 1, 2]])
+def test_mixed_degree_sipg_symmetric_kills_constants_spd(degrees):
+    prob = _mixed_grid(degrees)
+    kn = prob["knots"]
+    full = full_numbering(prob, kn)
+    assert [s[0] for s in full["shapes"]] == [len(kn[k][0]) - degrees[k] - 1 for k in range(4)]
+    A = discretize.assemble_global(prob, kn, full).toarray()
+    assert np.max(np.abs(A - A.T)) <= 1e-14 * np.max(np.abs(A))
+    assert np.max(np.abs(A @ np.ones(len(A)))) <= 1e-12 * np.max(np.abs(A))
+    num = discretize.numbering(prob, kn)
+    Ad = discretize.assemble_global(prob, kn, num).toarray()
+    assert np.linalg.eigvalsh(Ad)[0] > 0
+
+
+def test_same_degree_for_every_patch_is_the_scalar_degree():
+    base = W.grid_problem((2, 2), lambda c, a: 3 if sum(c) % 2 == 0 else 4, 2, "sipg", jitter=0.1, seed=5)
+    listed = W.with_patch_degrees(base, [2, 2, 2, 2])
+    for prob in (base, listed):
+        prob["sipg_penalty"] = base["sipg_penalty"]
+    kn = base["knots"]
+    A0 = discretize.assemble_global(base, kn, discretize.numbering(base, kn))
+    A1 = discretize.assemble_global(listed, listed["knots"], discretize.numbering(listed, listed["knots"]))
+    assert (A0 != A1).nnz == 0
+
+
+def _quadratic_bubble(box):
+    def u(x):
+        return np.prod([x[:, a] * (box[a] - x[:, a]) for a in range(x.shape[1])], axis=0)
+
+    def f(x):
+        d = x.shape[1]
+        out = np.zeros(len(x))
+        for a in range(d):
+            others = np.prod([x[:, b] * (box[b] - x[:, b]) for b in range(d) if b != a], axis=0)
+            out += 2.0 * others
+        return out
+    return u, f
+
+
+def test_mixed_degree_polynomial_reproduction():
+    """A quadratic bubble lies in S_2, S_3 and S_4 on every patch and its normal derivative jumps
+    nowhere: SIPG with patches of degrees 2..4 and non-matching grids reproduces it exactly (a
+    dropped or one-sided flux term, a wrong quadrature count on a cell shared by two degrees, or
+    a basis of the wrong degree on one side fails this)."""
+    def nm(c, a):
+        return 3 if (c[0] + c[1]) % 2 == 0 else 4
+    prob = W.grid_problem((3, 3), nm, 4, "sipg", box=(4.5, 3.0), flip_patches=(1, 5), transpose_patches=(4,))
+    prob = W.with_patch_degrees(prob, [2, 3, 4, 3, 2, 4, 2, 3, 2])
+    u_ex, f = _quadratic_bubble((4.5, 3.0))
+    num, A, b, u = solve_discrete(prob, f)
+    xi = np.random.default_rng(0).uniform(0, 1, (30, 2))
+    for k in range(9):
+        X, _ = geometry.eval_points(1, prob["geo_knots"][k], prob["geo_ctrl"][k], xi)
+        uh = patch_values(prob, prob["knots"], num, u, k, xi)
+        assert np.max(np.abs(uh - u_ex(X))) <= 1e-11, k
+
+
+def test_lshape_nonmatching_spaces_and_convergence():
+    """The L-shape of Table SCMS2: patch sizes and degrees as the setting states; the discrete
+    solution converges to sin(pi x) sin(pi y) at least at the rate of the lowest degree + 1."""
+    errs = []
+    for r in (2, 3, 4):
+        prob, _ = W.lshape(2, r)
+        assert prob["degrees"] == [2, 3, 2]
+        ne = [len(np.unique(prob["knots"][k][0])) - 1 for k in range(3)]
+        assert ne == [2 ** r, 2 ** (r - 1), 2 ** (r - 1)]
+        num, A, b, u = solve_discrete(prob, W.source_sinprod)
+        errs.append(l2_error(prob, num, u, W.exact_sinprod))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 3 - 0.35), rates
+
+
+def test_mixed_degree_colouring_is_valid():
+    prob, _ = W.lshape(2, 4)
+    num = discretize.numbering(prob, prob["knots"])
+    col = smoothers.colouring(prob, prob["knots"], num)
+    A = discretize.assemble_global(prob, prob["knots"], num).tocoo()
+    off = A.row != A.col
+    assert not np.any(col[A.row[off]] == col[A.col[off]])
+    S = smoothers.structural_pattern(prob, prob["knots"], num).tocoo()
+    Sd = set(zip(S.row.tolist(), S.col.tolist()))
+    assert all((r, c) in Sd for r, c in zip(A.row.tolist(), A.col.tolist()))
+    # the DoFs left on base colours carry par(k) (P+1)^2 + (i_0 mod (P+1)) + (i_1 mod (P+1)) (P+1),
+    # P = 3 the largest degree, from the copy that numbered them
+    P1 = 3 + 1
+    par = smoothers.patch_parity(prob)
+    nbase = 0
+    for g, (k, f) in enumerate(num["owner"]):
+        if col[g] >= 2 * P1 ** 2:
+            continue
+        i0, i1 = discretize.unflatten(f, num["shapes"][k])
+        assert col[g] == par[k] * P1 ** 2 + (i0 % P1) + (i1 % P1) * P1
+        nbase += 1
+    assert nbase > 0.8 * num["ndof"]
+
+
+def test_mixed_degree_hierarchy_keeps_each_patch_degree():
+    prob, _ = W.lshape(3, 4)
+    h = hierarchy.build(prob, 3)
+    for l in range(3):
+        for k, pk in enumerate(prob["degrees"]):
+            t = h["knots"][l][k][0]
+            assert np.sum(t == 0.0) == pk + 1  # end multiplicity p_k + 1 on every level
+    # Galerkin coarse operators: P^T M_f P = M_c holds patch by patch (nested spaces)
+    for k, pk in enumerate(prob["degrees"]):
+        P = hierarchy.patch_prolongation(h["knots"][1][k], h["knots"][2][k], pk)
+        Mf = discretize.patch_mass(prob, k, h["knots"][2][k])
+        Mc = discretize.patch_mass(prob, k, h["knots"][1][k])
+        assert np.max(np.abs((P.T @ Mf @ P - Mc).toarray())) <= 1e-13
+
+
+@pytest.mark.parametrize("smoother,tau,delta", [("scms", 0.5, 0.12), ("hybrid", 0.25, 0.1)])
+def test_mixed_degree_cycle_converges_and_is_symmetric(smoother, tau, delta):
+    prob, _ = W.lshape(2, 4)
+    M = mg.Multigrid(prob, levels=3, smoother=smoother, tau=tau, delta=delta)
+    E = M.error_propagation()
+    rho = max(abs(np.linalg.eigvals(E)))
+    assert rho < 1.0, rho
+    rng = np.random.default_rng(2)
+    x, y = rng.standard_normal(M.ndof), rng.standard_normal(M.ndof)
+    bx, by = M.precondition(x), M.precondition(y)
+    assert abs(y @ bx - x @ by) <= 1e-12 * np.linalg.norm(bx) * np.linalg.norm(y)
+    f = discretize.assemble_load(prob, prob["knots"], M.h["num"][-1], W.source_sinprod)
+    u, it, hist = M.solve_pcg(f)
+    assert np.linalg.norm(f - M.A @ u) / np.linalg.norm(f) <= 1e-8
+    ex = spla.spsolve(M.A.tocsc(), f)
+    assert np.linalg.norm(u - ex) <= 1e-6 * np.linalg.norm(ex)

@@ -953,39 +953,19 @@ __global__ void __launch_bounds__(256) gemm_umma_tf32(const GemmTask* __restrict
   }
   __syncthreads();
   if (ok && nst > 0) {
-    // EB elements per thread at a time: their global reads (the eigenvalue table, or the output
-    // that is updated) are issued together, not one dependent load after another
-    constexpr int EB = 8;
-    for (int base = 0; base < UM * UN; base += 256 * EB) {
-      float acc[EB], ext[EB];
-      int64_t cix[EB];
-      bool live[EB];
-#pragma unroll
-      for (int j = 0; j < EB; ++j) {
-        const int idx = base + j * 256 + tid;
-        const int r = g.ctrans ? idx % UM : idx / UN, c = g.ctrans ? idx / UM : idx % UN;
-        const int m = m0 + r, n = n0 + c;
-        live[j] = idx < UM * UN && m < g.M && n < g.N;
-        acc[j] = live[j] ? tile[r * TP + c] : 0.0f;
-        cix[j] = live[j] ? oC + (g.ctrans ? (int64_t)n * g.ldc + m : (int64_t)m * g.ldc + gcol(g, n)) : 0;
-        ext[j] = (live[j] && g.epi == 1) ? static_cast<const float*>(g.dinv)[(int64_t)m * g.ldd + n] : 1.0f;
-      }
+    for (int idx = tid; idx < UM * UN; idx += 256) {
+      const int r = g.ctrans ? idx % UM : idx / UN, c = g.ctrans ? idx / UM : idx % UN;
+      const int m = m0 + r, n = n0 + c;
+      if (m >= g.M || n >= g.N) continue;
+      float acc = tile[r * TP + c];
+      const int64_t ci = oC + (g.ctrans ? (int64_t)n * g.ldc + m : (int64_t)m * g.ldc + gcol(g, n));
+      if (g.epi == 1) acc *= static_cast<const float*>(g.dinv)[(int64_t)m * g.ldd + n];
       if (g.tC) {
-        float* C = static_cast<float*>(g.C);
-        float old[EB];
-#pragma unroll
-        for (int j = 0; j < EB; ++j) old[j] = (live[j] && g.epi == 2) ? C[cix[j]] : 0.0f;
-#pragma unroll
-        for (int j = 0; j < EB; ++j)
-          if (live[j]) C[cix[j]] = g.epi == 2 ? old[j] + (float)(g.alpha * acc[j]) : acc[j] * ext[j];
+        float* cp = static_cast<float*>(g.C) + ci;
+        *cp = g.epi == 2 ? *cp + (float)(g.alpha * acc) : acc;
       } else {
-        double* C = static_cast<double*>(g.C);
-        double old[EB];
-#pragma unroll
-        for (int j = 0; j < EB; ++j) old[j] = (live[j] && g.epi == 2) ? C[cix[j]] : 0.0;
-#pragma unroll
-        for (int j = 0; j < EB; ++j)
-          if (live[j]) C[cix[j]] = g.epi == 2 ? old[j] + g.alpha * (double)acc[j] : (double)(acc[j] * ext[j]);
+        double* cp = static_cast<double*>(g.C) + ci;
+        *cp = g.epi == 2 ? *cp + g.alpha * (double)acc : (double)acc;
       }
     }
   }

@@ -777,7 +777,9 @@ __global__ void __launch_bounds__(128) gemm_umma(const GemmTask* __restrict__ ta
 constexpr int kUmmaStages = 4;
 // core matrices of one 8-row group 144 B apart along K (not 128): the eight 16-byte copies that
 // fill one row's slab then land in distinct shared-memory banks; 8-row groups 8 x 144 B apart
-constexpr int kTfLbo = 144, kTfSbo = 8 * kTfLbo;
+// K of one slab: 256 bytes per row (64 TF32 elements, 8 MMAs); a row's 16 core matrices along K
+constexpr int kTfKB = 256;
+constexpr int kTfLbo = 144, kTfSbo = (kTfKB / 16) * kTfLbo;
 constexpr int kTfA = (UM / 8) * kTfSbo, kTfB = (UN / 8) * kTfSbo;  // bytes of one slab of A / B
 constexpr int kUmmaTf32Smem = kUmmaStages * (kTfA + kTfB);
 
@@ -792,7 +794,7 @@ __device__ __forceinline__ uint64_t umma_sdesc_tf(unsigned saddr) {
 
 __global__ void __launch_bounds__(256) gemm_umma_tf32(const GemmTask* __restrict__ tasks,
                                                       const GemmItem* __restrict__ items, int* err) {
-  constexpr int KT = UKB / 4;  // K elements per slab
+  constexpr int KT = kTfKB / 4;  // K elements per slab
   extern __shared__ __align__(1024) unsigned char usm[];
   auto sA = [&](int b) { return usm + b * kTfA; };
   auto sB = [&](int b) { return usm + kUmmaStages * kTfA + b * kTfB; };
@@ -824,7 +826,7 @@ __global__ void __launch_bounds__(256) gemm_umma_tf32(const GemmTask* __restrict
   const int nst = (g.K + KT - 1) / KT;
   const int64_t sAm = g.transA ? 1 : g.lda, sAk = g.transA ? g.lda : 1;
   const int64_t sBn = g.transB ? g.ldb : 1, sBk = g.transB ? 1 : g.ldb;
-  // element (row, kk) of a slab in the core-matrix layout: 8-row groups of 1024 B, 16-byte column groups
+  // element (row, kk) of a slab in the core-matrix layout: 8-row groups kTfSbo B apart, 16-byte column groups
   auto cm_off = [](int row, int kk) {
     return (row >> 3) * kTfSbo + (kk >> 2) * kTfLbo + (row & 7) * 16 + (kk & 3) * 4;
   };
@@ -889,7 +891,7 @@ __global__ void __launch_bounds__(256) gemm_umma_tf32(const GemmTask* __restrict
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const unsigned a0 = smem_u32(sA(b)), b0 = smem_u32(sB(b));
 #pragma unroll
-      for (int j = 0; j < UKB / 32; ++j) {
+      for (int j = 0; j < kTfKB / 32; ++j) {
         const uint64_t ad = umma_sdesc_tf(a0 + 2 * kTfLbo * j), bd = umma_sdesc_tf(b0 + 2 * kTfLbo * j);
         const unsigned acc = (st > 0 || j > 0) ? 1u : 0u;
         asm volatile(

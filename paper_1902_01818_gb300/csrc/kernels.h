@@ -59,7 +59,8 @@ struct GsStagedArgs {
   double* u;
   int* err;
 };
-bool gs_staged_fits(int d, int p, int csize, int smem, int threads);
+// whether a cluster of csize CTAs of `threads` threads (tpr per row) with smem bytes fits the GPU (gs_staged.cu)
+bool gs_staged_fits(int d, int p, int tpr, int csize, int smem, int threads);
 cudaError_t launch_gs_staged(int d, int p, int nclusters, int smem, cudaStream_t st, const GsStagedArgs& a);
 // xent: the nx entries of [e0, e0 + n) with couplings to the other parity
 void launch_wait_expiry_probe(long long limit, cudaStream_t st, int* err, long long* elapsed_ns);

@@ -972,7 +972,7 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
   Plan pl;
   for (int cs : sizes) {
     Plan t;
-    if (!plan_for(cs, t) || !gs_staged_fits(d, P, cs, (int)t.total, t.threads)) continue;
+    if (!plan_for(cs, t) || !gs_staged_fits(d, P, t.tpr, cs, (int)t.total, t.threads)) continue;
     pl = std::move(t);
     dl.gs_csize = cs;
     dl.gs_smem = (int)pl.total;

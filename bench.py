@@ -56,19 +56,24 @@ def hbm_peak_gbs():
 DRAM_TRAFFIC = {
     ("band", 2): 1.093e+08,
     ("residual", 2): 6.325e+07,
-    ("gs", 2): 8.199e+07,
+    ("fd", 2): 2.71e+07,
+    ("gs", 2): 8.2e+07,
     ("band", 3): 2.139e+08,
     ("residual", 3): 1.153e+08,
+    ("fd", 3): 2.75e+07,
     ("gs", 3): 1.351e+08,
     ("band", 4): 3.538e+08,
     ("residual", 4): 1.851e+08,
-    ("gs", 4): 2.095e+08,
+    ("fd", 4): 2.77e+07,
+    ("gs", 4): 2.096e+08,
     ("band", 5): 5.304e+08,
     ("residual", 5): 2.734e+08,
-    ("gs", 5): 3.012e+08,
+    ("fd", 5): 2.78e+07,
+    ("gs", 5): 3.015e+08,
     ("band", 6): 7.443e+08,
     ("residual", 6): 3.804e+08,
-    ("gs", 6): 4.306e+08,
+    ("fd", 6): 2.8e+07,
+    ("gs", 6): 4.305e+08,
 }
 
 

@@ -95,6 +95,9 @@ struct Level {
   // assembly computes them (also added to the host band when there is one): the device set-up adds
   // them to the band it assembles, the matrix-free residual applies them as stored couplings
   std::vector<std::pair<int64_t, double>> band_add;
+  bool record_band_add = false;  // list the within-patch SIPG terms also when a host band is assembled
+  // the entries of band_add with equal band index summed in their listed (cell) order, by index
+  std::vector<std::pair<int64_t, double>> merged_band_add() const;
   double nnz = 0.0;  // nonzero band coefficients (kept when the host band is released)
   // SIPG cross-patch couplings, CSR over rows x_row[i]
   std::vector<int64_t> x_row;

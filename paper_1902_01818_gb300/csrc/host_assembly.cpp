@@ -4,6 +4,8 @@
 #include <numeric>
 #include <unordered_map>
 
+#include <omp.h>
+
 #include "host.hpp"
 
 namespace mgiga {
@@ -500,9 +502,13 @@ double grid_size(const std::array<Vec, 3>& kn, int d) {
 }
 }  // namespace
 
+// cross: one map of cross-patch couplings per row partition (row mod cross.size()); badd: the
+// within-patch terms listed per row partition (when the band is assembled elsewhere or they are
+// recorded)
 static void interface_terms(const Problem& pr, Level& L, const Interface& f,
                             const std::vector<std::array<Vec, 3>>& fine_knots,
-                            std::unordered_map<uint64_t, double>& cross) {
+                            std::vector<std::unordered_map<uint64_t, double>>& cross,
+                            std::vector<std::vector<std::pair<int64_t, double>>>& badd) {
   // p: the larger degree of the two sides (Gauss points per cell exact for both sides' products)
   const int d = pr.d, p = std::max(pr.deg(f.pa), pr.deg(f.pb));
   const double eta = pr.penalty / std::min(grid_size(fine_knots[f.pa], d), grid_size(fine_knots[f.pb], d));
@@ -611,33 +617,58 @@ static void interface_terms(const Problem& pr, Level& L, const Interface& f,
       }
     }
     if (too_many) throw SetupError(1, "interface cell has too many active functions");
-    for (int cell = cbeg; cell < cend; ++cell) {
-      const std::vector<int64_t>& dofs = out[cell - cbeg].dofs;
-      const Vec& blk = out[cell - cbeg].blk;
-      for (size_t i = 0; i < dofs.size(); ++i)
-        for (size_t j = 0; j < dofs.size(); ++j) {
-          const double v = blk[i * ld + j];
-          if (v == 0.0) continue;
-          const int64_t r = dofs[i], c = dofs[j];
-          const int kr = L.patch_of[r], kc = L.patch_of[c];
-          if (kr == kc) {
-            // same patch: inside the band (|offset| <= 1 normal, <= p tangential)
-            int64_t rem_r = r - L.off[kr], rem_c = c - L.off[kc];
-            int o = 0, mul = 1;
-            for (int a = 0; a < d; ++a) {
-              const int ir = (int)(rem_r % L.N[kr][a]), ic = (int)(rem_c % L.N[kr][a]);
-              rem_r /= L.N[kr][a]; rem_c /= L.N[kr][a];
-              o += (ic - ir + pr.p) * mul;  // the band spans the largest degree of all patches
-              mul *= 2 * pr.p + 1;
+    // the cells' entries added in cell order; the rows are split among the threads (row mod the
+    // partitions), so every entry still receives its contributions in cell order
+    const int T = (int)cross.size();
+    const bool list = L.band.empty() || L.record_band_add;
+#pragma omp parallel num_threads(T)
+    {
+#pragma omp for schedule(static, 1)
+      for (int t = 0; t < T; ++t)
+        for (int cell = cbeg; cell < cend; ++cell) {
+          const std::vector<int64_t>& dofs = out[cell - cbeg].dofs;
+          const Vec& blk = out[cell - cbeg].blk;
+          for (size_t i = 0; i < dofs.size(); ++i) {
+            const int64_t r = dofs[i];
+            if (r % T != t) continue;
+            const int kr = L.patch_of[r];
+            for (size_t j = 0; j < dofs.size(); ++j) {
+              const double v = blk[i * ld + j];
+              if (v == 0.0) continue;
+              const int64_t c = dofs[j];
+              const int kc = L.patch_of[c];
+              if (kr == kc) {
+                // same patch: inside the band (|offset| <= 1 normal, <= p tangential)
+                int64_t rem_r = r - L.off[kr], rem_c = c - L.off[kc];
+                int o = 0, mul = 1;
+                for (int a = 0; a < d; ++a) {
+                  const int ir = (int)(rem_r % L.N[kr][a]), ic = (int)(rem_c % L.N[kr][a]);
+                  rem_r /= L.N[kr][a]; rem_c /= L.N[kr][a];
+                  o += (ic - ir + pr.p) * mul;  // the band spans the largest degree of all patches
+                  mul *= 2 * pr.p + 1;
+                }
+                if (list) badd[t].push_back({(int64_t)o * L.nloc + r, v});
+                if (!L.band.empty()) L.band[(size_t)o * L.nloc + r] += v;
+              } else {
+                cross[t][((uint64_t)r << 32) | (uint64_t)c] += v;
+              }
             }
-            L.band_add.push_back({(int64_t)o * L.nloc + r, v});
-            if (!L.band.empty()) L.band[(size_t)o * L.nloc + r] += v;
-          } else {
-            cross[((uint64_t)r << 32) | (uint64_t)c] += v;
           }
         }
     }
   }
+}
+
+std::vector<std::pair<int64_t, double>> Level::merged_band_add() const {
+  std::vector<size_t> ord(band_add.size());
+  for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return band_add[a].first < band_add[b].first; });
+  std::vector<std::pair<int64_t, double>> out;
+  for (size_t i : ord) {
+    if (!out.empty() && out.back().first == band_add[i].first) out.back().second += band_add[i].second;
+    else out.push_back(band_add[i]);
+  }
+  return out;
 }
 
 void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec, 3>>& fine_knots,
@@ -651,18 +682,31 @@ void assemble_fine(const Problem& pr, Level& L, const std::vector<std::array<Vec
   } else {
     Vec().swap(L.band);
   }
-  std::unordered_map<uint64_t, double> cross;
+  const int T = std::max(1, omp_get_max_threads());
+  std::vector<std::unordered_map<uint64_t, double>> cross(T);
+  std::vector<std::vector<std::pair<int64_t, double>>> badd(T);
   if (pr.coupling == 1)
-    for (const auto& f : pr.ifaces) interface_terms(pr, L, f, fine_knots, cross);
+    for (const auto& f : pr.ifaces) interface_terms(pr, L, f, fine_knots, cross, badd);
+  // within-patch terms: the partitions one after another (a row's entries all in one partition,
+  // in cell order)
+  for (auto& b : badd) {
+    L.band_add.insert(L.band_add.end(), b.begin(), b.end());
+    std::vector<std::pair<int64_t, double>>().swap(b);
+  }
   // cross-patch entries to CSR by row position: counted by row, then each row's
   // columns sorted (rows in parallel)
   std::vector<int64_t> cnt((size_t)L.nloc + 1, 0);
-  for (const auto& e : cross) ++cnt[(size_t)(e.first >> 32) + 1];
+  size_t ncross = 0;
+  for (const auto& part : cross) {
+    ncross += part.size();
+    for (const auto& e : part) ++cnt[(size_t)(e.first >> 32) + 1];
+  }
   for (int64_t r = 0; r < L.nloc; ++r) cnt[(size_t)r + 1] += cnt[(size_t)r];
-  std::vector<std::pair<int64_t, double>> ent(cross.size());
+  std::vector<std::pair<int64_t, double>> ent(ncross);
   {
     std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
-    for (const auto& e : cross) ent[(size_t)fill[(size_t)(e.first >> 32)]++] = {(int64_t)(e.first & 0xffffffffu), e.second};
+    for (const auto& part : cross)
+      for (const auto& e : part) ent[(size_t)fill[(size_t)(e.first >> 32)]++] = {(int64_t)(e.first & 0xffffffffu), e.second};
   }
 #pragma omp parallel for schedule(dynamic, 1024)
   for (int64_t r = 0; r < L.nloc; ++r)

@@ -572,11 +572,9 @@ void gpu_assemble_finest(const Problem& pr, Level& F, double* band, cudaStream_t
   SCK(cudaGetLastError());
   // the SIPG terms within one patch (host, in cell order): merged per band entry, then added
   if (!F.band_add.empty()) {
-    std::map<int64_t, double> m;
-    for (const auto& x : F.band_add) m[x.first] += x.second;
     std::vector<int64_t> idx;
     std::vector<double> val;
-    for (const auto& x : m) { idx.push_back(x.first); val.push_back(x.second); }
+    for (const auto& x : F.merged_band_add()) { idx.push_back(x.first); val.push_back(x.second); }
     const int64_t* di = dupload(idx, T.ptrs, st);
     const double* dv = dupload(val, T.ptrs, st);
     count_launch();

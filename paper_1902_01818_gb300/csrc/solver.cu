@@ -1169,14 +1169,13 @@ void build_mf(const Problem& pr, const Level& L, const std::vector<std::pair<int
   std::map<int64_t, std::vector<std::pair<int64_t, double>>> rows;
   for (size_t i = 0; i < L.x_row.size(); ++i)
     for (int j = L.x_ptr[i]; j < L.x_ptr[i + 1]; ++j) rows[L.x_row[i]].push_back({L.x_col[j], L.x_val[j]});
-  std::map<std::pair<int64_t, int64_t>, double> within;
+  // self: one entry per band index (summed in cell order), sorted by index
   for (const auto& x : self) {
     const int64_t o = x.first / L.nloc, r = x.first % L.nloc;
     const int64_t c = r + L.band_offset(L.patch_of[r], (int)o);
     if (L.dirichlet[r] || L.dirichlet[c]) continue;
-    within[{r, c}] += x.second;
+    rows[r].push_back({c, x.second});
   }
-  for (const auto& x : within) rows[x.first.first].push_back({x.first.second, x.second});
   std::vector<int64_t> xr, xc;
   std::vector<int> xp(1, 0);
   Vec xv;
@@ -1757,8 +1756,9 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
     std::vector<std::pair<int64_t, double>> mf_self;  // within-patch SIPG terms for the matrix-free residual
     if (gpu_setup) {
       Level& F = h->L[lv - 1];
+      F.record_band_add = h->opt.matrix_free != 0;
       assemble_fine(h->pr, F, h->pr.knots, /*stiffness=*/!gpu_stiffness);
-      if (h->opt.matrix_free) mf_self = F.band_add;
+      if (h->opt.matrix_free) mf_self = F.merged_band_add();
       if (!F.band.empty()) std::vector<std::pair<int64_t, double>>().swap(F.band_add);
       apply_dirichlet(F);
       h->T.assign(lv, Transfer{});
@@ -1769,8 +1769,9 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       }
       tick("interfaces", lv - 1);
     } else {
+      h->L[lv - 1].record_band_add = h->opt.matrix_free != 0;
       assemble_finest(h->pr, h->L);
-      if (h->opt.matrix_free) mf_self = h->L[lv - 1].band_add;
+      if (h->opt.matrix_free) mf_self = h->L[lv - 1].merged_band_add();
       std::vector<std::pair<int64_t, double>>().swap(h->L[lv - 1].band_add);
       tick("assembly", lv - 1);
       galerkin_hierarchy(h->L, h->T);

@@ -1010,6 +1010,8 @@ void build_gs_staged(const Problem& pr, const std::vector<int>& colour, const Le
         }
   std::vector<unsigned char> pool((size_t)std::max<int64_t>(total, 16), 0);
   std::vector<int64_t> foff(L.ndof, -1);
+  // groups write disjoint parts of the pool (and of foff): in parallel
+#pragma omp parallel for schedule(dynamic, 4)
   for (int g = 0; g < ngrp; ++g) {
     const int k = (g / cs) % K, r = g % cs;
     const int64_t plane = plane_of(k);
@@ -1263,12 +1265,14 @@ void build_gs(const Problem& pr, const std::vector<int>& colour, const Level& L,
   const bool f32 = dl.arith >= 1;
   if (f32) {
     std::vector<float> gb((size_t)L.nb * n);
+#pragma omp parallel for schedule(static)
     for (int o = 0; o < L.nb; ++o)
       for (int e = 0; e < n; ++e)
         gb[(size_t)o * n + e] = (float)(L.band[(size_t)o * L.nloc + gpos[e]] + (o == center ? cdiag[e] : 0.0));
     dl.gs_band = reinterpret_cast<double*>(A.upload(gb));
   } else {
     Vec gb((size_t)L.nb * n);
+#pragma omp parallel for schedule(static)
     for (int o = 0; o < L.nb; ++o)
       for (int e = 0; e < n; ++e) gb[(size_t)o * n + e] = L.band[(size_t)o * L.nloc + gpos[e]] + (o == center ? cdiag[e] : 0.0);
     dl.gs_band = A.upload(gb);

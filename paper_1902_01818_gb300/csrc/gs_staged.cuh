@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(1024, 1) gs_patch_staged(GsStagedArgs a) {
           srow = (int)(li >> 20);
           rest = (int)(li & 0xFFFFFu);
           own = G + (srow + P) * pitch + rest;
-#pragma unroll(D == 2 ? 16 : 1)
+#pragma unroll(D == 2 ? 16 : 4)
           for (int ob = sub; ob < NOB; ob += TPR) {
             const int o1 = ob % W, o2 = ob / W;
             const float* ur = us + own + (D == 2 ? (o1 - P) * pitch : (o2 - P) * pitch + (o1 - P) * N0) - P;

@@ -196,6 +196,10 @@ struct mgiga_handle {
   int device = -1;          // the CUDA device current at mgiga_assemble (owns every buffer)
   bool own_stream = false;  // created by the library when the options give none
   cudaEvent_t legacy_done = nullptr;  // orders an owned stream after the legacy default stream
+  // the smoother's interface-piece solves run beside its fast diagonalisation (disjoint unknowns,
+  // both read only r): a second stream of the stream's priority, forked and joined by events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   std::unique_ptr<Arena> arena;
   std::vector<DLevel> D;
   // PCG state
@@ -235,6 +239,9 @@ struct mgiga_handle {
     arena.reset();
     if (own_stream && stream) cudaStreamDestroy(stream);
     if (legacy_done) cudaEventDestroy(legacy_done);
+    if (side) cudaStreamDestroy(side);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
   }
 };
 
@@ -1380,12 +1387,23 @@ void run_fd(mgiga_handle* h, DLevel& d) {
   for (size_t i = 0; i < d.fd_steps.size(); ++i) run_fd_step(h, d, i);
 }
 
-// u += tau sum_T P_T L_T^{-1} P_T^T r  (Eq. Ldef), r in d.r
+// u += tau sum_T P_T L_T^{-1} P_T^T r  (Eq. Ldef), r in d.r.  The pieces T partition the unknowns
+// (patch interiors and interface pieces), so the interface-piece solves and the interiors' fast
+// diagonalisation read only r and update disjoint entries of u: the pieces go on the side stream
+// (forked from the handle's stream and joined back; under graph capture, two parallel branches)
 void smooth(mgiga_handle* h, int l) {
   DLevel& d = h->D[l];
-  run_fd(h, d);
-  launch_piece(d.npiece_items, d.piece_max_n, h->stream, d.piece_items, d.pieces, d.zpool, d.zpool_f32, d.piece_pos, d.r, d.u,
+  const bool fork = h->side && d.npiece_items > 0;
+  cudaStream_t ps = fork ? h->side : h->stream;
+  if (fork) {
+    CK(cudaEventRecord(h->fork_ev, h->stream));
+    CK(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+  }
+  launch_piece(d.npiece_items, d.piece_max_n, ps, d.piece_items, d.pieces, d.zpool, d.zpool_f32, d.piece_pos, d.r, d.u,
                h->opt.tau, 0);
+  if (fork) CK(cudaEventRecord(h->join_ev, h->side));
+  run_fd(h, d);
+  if (fork) CK(cudaStreamWaitEvent(h->stream, h->join_ev, 0));
   if (conforming(h)) launch_shared(d.nsh, h->stream, d.sh_ptr, d.sh_pos, d.u, nullptr, 2);
 }
 
@@ -1791,6 +1809,16 @@ mgiga_status mgiga_assemble(mgiga_handle* h) {
       h->own_stream = true;
     }
     if (!h->legacy_done) CK(cudaEventCreateWithFlags(&h->legacy_done, cudaEventDisableTiming));
+    {
+      const char* env = std::getenv("MGIGA_SIDE_STREAM");  // 0: the pieces after the interiors, one stream
+      if (!h->side && !(env && env[0] == '0')) {
+        int prio = 0;
+        CK(cudaStreamGetPriority(h->stream, &prio));
+        CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio));
+        CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+      }
+    }
     CK(cudaGetDevice(&h->device));
     h->arena.reset(new Arena());
     Arena& A = *h->arena;

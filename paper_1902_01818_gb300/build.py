@@ -18,7 +18,7 @@ LIB = os.path.join(LIBDIR, "libmgiga.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SOURCES = ["host_spline.cpp", "host_assembly.cpp", "host_hierarchy.cpp", "host_problem.cpp", "tune.cpp"]
-DEVICE_SOURCES = ["kernels.cu", "gs_staged_2d.cu", "gs_staged_3d.cu", "fd_fused.cu", "setup_gpu.cu", "matfree.cu", "solver.cu"]
+DEVICE_SOURCES = ["kernels.cu", "gs_staged_2d.cu", "gs_staged_3d.cu", "fd_fused.cu", "fd_cluster.cu", "setup_gpu.cu", "matfree.cu", "solver.cu"]
 
 
 def _nvcc():

@@ -112,6 +112,17 @@ int fd_small_smem(int n0, int n1, bool f32);  // shared memory of one patch (mus
 cudaError_t prepare_fd_small();
 void launch_fd_small(int npatch, int smem, bool f32, cudaStream_t st, const FdSmall* patches, const double* r,
                      double* u, double tau);
+// fused fast diagonalisation of 2D patch interiors on the FP32 path by one thread-block cluster per
+// patch (fd_cluster.cu): cs CTAs per patch, each owning wm (>= ceil(n0 / cs), a multiple of 4)
+// columns of the intermediates, ks groups of threads over the contraction index
+struct FdClusterShape {
+  int cs, wm, ks, threads, smem;
+  int resident;  // clusters of this shape resident at once on the device
+};
+// the shape for interiors up to n0max x n1max (npatch clusters in a launch); false if none fits
+bool fd_cluster_shape(int n0max, int n1max, int npatch, FdClusterShape* out);
+cudaError_t launch_fd_cluster(int npatch, const FdClusterShape& s, cudaStream_t st, const FdSmall* patches,
+                              const double* r, double* u, double tau);
 cudaError_t prepare_gemm();  // shared-memory attributes of the SIMT GEMM (once per process)
 // tA: element type of A in the step (0 double, 1 float); B is of the arithmetic type
 void launch_gemm(int nitems, int arith, int tA, cudaStream_t st, const GemmTask* tasks, const GemmItem* items);

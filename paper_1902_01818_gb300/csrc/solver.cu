@@ -132,6 +132,9 @@ struct DLevel {
   int fd_fused_smem = 0;
   FdSmall* fd_small = nullptr;                 // fused path (small 2D patches): one CTA per patch
   int fd_small_n = 0, fd_small_smem = 0;
+  FdSmall* fd_cluster = nullptr;               // fused path (2D, FP32): one thread-block cluster per patch
+  int fd_cluster_n = 0;
+  FdClusterShape fd_cshape{};
   // pieces (interface pieces on levels >= 1, the coarse solve on level 0)
   PieceMeta* pieces = nullptr;
   PieceItem* piece_items = nullptr;
@@ -381,6 +384,13 @@ void build_transfer_tables(const Level& C, const Level& F, const Transfer& T, Ar
 // interior fast diagonalisation as batched GEMM steps (Sec. 5 smoother on patch interiors)
 // engine: -1 the built-in rule; 0 the batched SIMT contractions; 1 the tensor cores (TF32 / BF16
 // modes); 2 the one-CTA-per-patch contractions (2D, when every interior fits shared memory)
+// MGIGA_FD_CLUSTER=1: the one-cluster-per-patch fast diagonalisation on 2D FP32 levels (built-in
+// rule and autotuner candidate)
+bool fd_cluster_opted_in() {
+  const char* env = std::getenv("MGIGA_FD_CLUSTER");
+  return env && env[0] == '1';
+}
+
 void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLevel& dl, int engine = -1) {
   const int d = L.d;
   std::vector<FDData> fd(L.K);
@@ -682,7 +692,38 @@ void build_fd(const Level& L, int lvl, double delta, double tau, Arena& A, DLeve
   int fuse_max_n = 48;
   if (const char* env = std::getenv("MGIGA_FD_FUSE_MAX_N")) fuse_max_n = std::max(1, std::atoi(env));
   if (engine == 2) fuse_max_n = 1 << 30;  // forced: whatever fits shared memory
-  if (d == 2 && !(fuse_env && fuse_env[0] == '0') && engine != 0 && engine != 1) {
+  // 2D interiors on the FP32 path: all four contractions of a patch by one thread-block cluster
+  // (engine 3), with MGIGA_FD_CLUSTER=1 wherever it fits.  Opt-in: measured on the SIPG 3x3 layout,
+  // p = 6, one solve alone it is faster (interiors of 52-76: 0.047 -> 0.021 ms, 28-40: 0.023 ->
+  // 0.013 ms; V-cycle 2.59 -> 2.57 ms, p = 2 1.40 -> 1.34 ms), but five solves side by side ran 2.5%
+  // slower (its clusters of 8-16 CTAs wait for whole SMs that the other solves' kernels hold)
+  const bool cl_off = fuse_env && fuse_env[0] == '0';
+  if (d == 2 && f32 && !cl_off && (engine == 3 || (engine < 0 && fd_cluster_opted_in() && fdk == 1))) {
+    std::vector<FdSmall> fc;
+    int n0max = 0, n1max = 0;
+    for (int k = 0; k < L.K; ++k) {
+      const int n0 = fd[k].n[0], n1 = fd[k].n[1];
+      if (n0 <= 0 || n1 <= 0) continue;
+      n0max = std::max(n0max, n0);
+      n1max = std::max(n1max, n1);
+      FdSmall q{};
+      q.ibase = L.off[k] + 1 + L.N[k][0];
+      q.n0 = n0;
+      q.n1 = n1;
+      q.N0 = L.N[k][0];
+      q.U0 = dU + uoff[k][0] * esz;
+      q.U1 = dU + uoff[k][1] * esz;
+      q.dinv = dD + toff[k] * esz;
+      fc.push_back(q);
+    }
+    FdClusterShape sh{};
+    if (!fc.empty() && fd_cluster_shape(n0max, n1max, (int)fc.size(), &sh)) {
+      dl.fd_cluster = A.upload(fc);
+      dl.fd_cluster_n = (int)fc.size();
+      dl.fd_cshape = sh;
+    }
+  }
+  if (d == 2 && !(fuse_env && fuse_env[0] == '0') && engine != 0 && engine != 1 && engine != 3 && !dl.fd_cluster) {
     std::vector<FdSmall> fs;
     int smem = 0;
     bool fits = true;
@@ -1371,6 +1412,10 @@ void run_fd_step(mgiga_handle* h, DLevel& d, size_t i) {
 
 // the interior part of the smoother: fused per patch on small 2D levels, else the batched GEMM steps
 void run_fd(mgiga_handle* h, DLevel& d) {
+  if (d.fd_cluster) {
+    CK(launch_fd_cluster(d.fd_cluster_n, d.fd_cshape, h->stream, d.fd_cluster, d.r, d.u, h->opt.tau));
+    return;
+  }
   if (d.fd_small) {
     launch_fd_small(d.fd_small_n, d.fd_small_smem, d.arith >= 1, h->stream, d.fd_small, d.r, d.u, h->opt.tau);
     return;
@@ -1624,14 +1669,16 @@ void tune_fd(mgiga_handle* h, const Level& L, int l, Arena& A, DLevel& d, bool v
   std::vector<int> cand = {0};
   if (d.arith >= 2) cand.push_back(1);
   if (L.d == 2) cand.push_back(2);
+  if (L.d == 2 && d.arith >= 1 && fd_cluster_opted_in()) cand.push_back(3);
   int choice = -1;
   if (!Tuner::instance().lookup(key, &choice)) {
     std::vector<DLevel> built(cand.size(), d);
     choice = Tuner::instance().choose(key, (int)cand.size(), [&](int i) -> double {
       DLevel& t = built[(size_t)i];
-      if (t.fd_steps.empty() && !t.fd_small) {
+      if (t.fd_steps.empty() && !t.fd_small && !t.fd_cluster) {
         build_fd(L, l, h->opt.delta, h->opt.tau, A, t, cand[(size_t)i]);
-        if (cand[(size_t)i] == 2 && !t.fd_small) return -1.0;  // does not fit one CTA
+        if (cand[(size_t)i] == 2 && !t.fd_small) return -1.0;    // does not fit one CTA
+        if (cand[(size_t)i] == 3 && !t.fd_cluster) return -1.0;  // does not fit one cluster
       }
       return time_on_stream(h, [&]() { run_fd(h, t); });
     });
@@ -1642,7 +1689,8 @@ void tune_fd(mgiga_handle* h, const Level& L, int l, Arena& A, DLevel& d, bool v
       std::fprintf(stderr, "\n");
     }
     d = built[(size_t)choice];
-    if (d.fd_steps.empty() && !d.fd_small) build_fd(L, l, h->opt.delta, h->opt.tau, A, d, cand[(size_t)choice]);
+    if (d.fd_steps.empty() && !d.fd_small && !d.fd_cluster)
+      build_fd(L, l, h->opt.delta, h->opt.tau, A, d, cand[(size_t)choice]);
     return;
   }
   build_fd(L, l, h->opt.delta, h->opt.tau, A, d, cand[(size_t)std::min<int>(choice, (int)cand.size() - 1)]);

@@ -152,3 +152,28 @@ def test_mixed_degree_cycle_converges_and_is_symmetric(smoother, tau, delta):
     assert np.linalg.norm(f - M.A @ u) / np.linalg.norm(f) <= 1e-8
     ex = spla.spsolve(M.A.tocsc(), f)
     assert np.linalg.norm(u - ex) <= 1e-6 * np.linalg.norm(ex)
+
+
+def test_lshape_scms_pcg_iterations_bounded_in_h_and_p():
+    """Sec. 5, Table SCMS2: on the non-matching L-shape the SCMS-preconditioned CG takes a number
+    of iterations that stays bounded as the grid is refined (one more level per refinement, the
+    coarsest grid fixed) and does not grow with the degree.  Refinements r = 4, 5, 6 (patch 0 with
+    2^r intervals, up to 7k unknowns), p = 2, 3, 4: the counts of one degree vary by at most 2 and
+    the last refinement adds at most one; at each refinement a higher degree needs no more
+    iterations.  Checked by planting mistakes in the oracle: a coarse-grid correction scaled by 1/2
+    (restriction 0.5 P^T) makes the counts grow with r (12, 18, 25 at p = 2); a cycle without its
+    coarse-grid correction breaks the ordering in p.  (A wrong h-scaling of the interior smoother's
+    sigma does not show here: the exact interface pieces and CG absorb it.)"""
+    counts = {}
+    for p in (2, 3, 4):
+        for r in (4, 5, 6):
+            prob, _ = W.lshape(p, r)
+            M = mg.Multigrid(prob, levels=r - 1, smoother="scms", tau=0.9, delta=0.12)
+            f = discretize.assemble_load(prob, prob["knots"], M.h["num"][-1], W.source_sinprod)
+            _, it, _ = M.solve_pcg(f)
+            counts[p, r] = it
+    for p in (2, 3, 4):
+        row = [counts[p, r] for r in (4, 5, 6)]
+        assert max(row) - min(row) <= 2 and row[2] <= row[1] + 1, (p, row)
+    for r in (4, 5, 6):
+        assert counts[2, r] >= counts[3, r] >= counts[4, r], (r, counts)

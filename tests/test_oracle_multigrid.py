@@ -369,3 +369,20 @@ def test_interior_eigen_solve_equals_sparse_lu(d, p):
     x = np.random.default_rng(d * 10 + p).standard_normal(L.shape[0])
     ref = spla.spsolve(L, x)
     assert np.max(np.abs(ap(x) - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("coupling", ["conforming", "sipg"])
+@pytest.mark.parametrize("smoother,tau,delta", [("scms", 0.25, 0.12), ("hybrid", 0.25, 0.1)])
+def test_pcg_iterations_bounded_under_refinement(coupling, smoother, tau, delta):
+    """Sec. 4 and 5 (Tables GS1, SCMS1): with one more level per refinement and the coarsest grid
+    fixed, the cycle-preconditioned CG needs a number of iterations bounded in the grid size.  On a
+    jittered 2x2 patch grid, p = 2, 16 / 32 / 64 intervals per patch: the counts vary by at most 4
+    and the last refinement adds at most one.  Checked by planting a coarse-grid correction scaled
+    by 1/2 (restriction 0.5 P^T) in the oracle: the counts then grow with every refinement."""
+    counts = []
+    for n, levels in ((16, 4), (32, 5), (64, 6)):
+        prob = W.grid_problem((2, 2), n, 2, coupling, jitter=0.1, seed=1, flip_patches=(3,))
+        M = mg.Multigrid(prob, levels=levels, smoother=smoother, tau=tau, delta=delta)
+        f = discretize.assemble_load(prob, prob["knots"], M.h["num"][-1], W.source_sinprod)
+        counts.append(M.solve_pcg(f)[1])
+    assert max(counts) - min(counts) <= 4 and counts[2] <= counts[1] + 1, counts
